@@ -1,0 +1,208 @@
+"""Pins for the CKKS oracle (oracle/ckks.py) against exact big-integer
+mathematics, not against itself:
+
+* Conv returns x + u*B with 0 <= u < |B| (CRT lift, python big ints);
+* ModDown returns floor(X / P) - u with 0 <= u < K (CRT lift);
+* RESCALE returns round(X / q_l) exactly (CRT lift; q_l odd, so no ties);
+* the tensor product decrypts as (c0 + c1 s)(c0' + c1' s) under (1, s, s^2);
+* KeySwitch(d2) decrypts to d2 s^2 plus an error within the analytic bound;
+* the canonical embedding agrees with direct complex evaluation and is a ring
+  homomorphism for the product in R[X]/(X^N+1);
+* decrypt(HMULT(enc a, enc b)) = a*b within 1e-5 (sparse ternary secret).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ckks as C
+from oracle import params as P
+from paper_2212_14191_gb300 import inputs as I
+
+U64 = np.uint64
+
+
+def lift(res, mods):
+    """(k, N) residues -> list of python ints in [0, prod)."""
+    M = math.prod(mods)
+    out = []
+    for n in range(res.shape[1]):
+        x = 0
+        for i, m in enumerate(mods):
+            Mi = M // m
+            x += int(res[i, n]) * Mi * pow(Mi % m, -1, m)
+        out.append(x % M)
+    return out
+
+
+@pytest.fixture(scope="module")
+def small():
+    qs, ps = P.default_moduli(12, 4)
+    prm = C.Params(256, qs, ps, alpha=4)
+    s = I.ternary_secret(11, prm.N, hamming_weight=64)
+    L = len(qs)
+    arand = I.uniform_residues(12, qs + ps, prm.dnum(L), prm.N, dtype=np.uint64).transpose(1, 0, 2)
+    erand = I.gaussian_error(13, (prm.dnum(L), prm.N))
+    evk = C.keygen_evk(prm, s, arand, erand)
+    return prm, s, evk
+
+
+@pytest.mark.parametrize("nsrc,ndst", [(1, 3), (4, 6), (3, 2)])
+def test_conv_is_x_plus_uB(nsrc, ndst):
+    qs = P.ntt_primes(nsrc + ndst)
+    src, dst = qs[:nsrc], qs[nsrc:]
+    N = 64
+    x = I.uniform_residues(nsrc, src, 1, N, dtype=np.uint64)[:, 0]
+    y = C.conv(x, src, dst)
+    X = lift(x, src)
+    B = math.prod(src)
+    ybig = [0] * N
+    for i, b in enumerate(src):
+        bh = B // b
+        for n in range(N):
+            ybig[n] += (int(x[i, n]) * pow(bh % b, -1, b) % b) * bh
+    for n in range(N):
+        u, r = divmod(ybig[n] - X[n], B)
+        assert r == 0 and 0 <= u < nsrc
+        for t_i, t in enumerate(dst):
+            assert int(y[t_i, n]) == ybig[n] % t
+
+
+def test_moddown_is_floor_div_P(small):
+    prm, _, _ = small
+    nl = 5
+    mods = prm.qs[:nl] + prm.ps
+    psis = prm.psi_q[:nl] + prm.psi_p
+    ks_c = I.uniform_residues(21, mods, 1, prm.N, dtype=np.uint64)[:, 0]
+    out = C.moddown(prm, nl, C.ntt(ks_c, mods, psis))
+    out_c = C.intt(out, prm.qs[:nl], prm.psi_q[:nl])
+    X = lift(ks_c, mods)
+    Q = math.prod(prm.qs[:nl])
+    got = lift(out_c, prm.qs[:nl])
+    for n in range(prm.N):
+        u = (X[n] // prm.P - got[n]) % Q
+        assert 0 <= u < prm.K
+
+
+@pytest.mark.parametrize("nl", [2, 3, 7])
+def test_rescale_is_round_div_ql(small, nl):
+    prm, _, _ = small
+    mods, psis = prm.qs[:nl], prm.psi_q[:nl]
+    c = I.uniform_residues(30 + nl, mods, 2, prm.N, dtype=np.uint64).transpose(1, 0, 2)
+    out = C.rescale(prm, np.stack([C.ntt(c[k], mods, psis) for k in range(2)]))
+    ql = mods[-1]
+    for k in range(2):
+        X = lift(c[k], mods)
+        got = C.intt(out[k], mods[:-1], psis[:-1])
+        for n in range(prm.N):
+            want = (2 * X[n] + ql) // (2 * ql)      # round to nearest, ql odd
+            for i, q in enumerate(mods[:-1]):
+                assert int(got[i, n]) == want % q
+
+
+def test_tensor_decrypts_under_1_s_s2(small):
+    prm, s, _ = small
+    nl = 4
+    mods, psis = prm.qs[:nl], prm.psi_q[:nl]
+    ca = I.uniform_residues(40, mods, 2, prm.N, dtype=np.uint64).transpose(1, 0, 2)
+    cb = I.uniform_residues(41, mods, 2, prm.N, dtype=np.uint64).transpose(1, 0, 2)
+    d0, d1, d2 = C.tensor(ca, cb, mods)
+    sn = C.ntt(C.small_to_residues(s, mods), mods, psis)
+    lhs = C.add(C.add(d0, C.hada(d1, sn, mods), mods), C.hada(d2, C.hada(sn, sn, mods), mods), mods)
+    rhs = C.hada(C.add(ca[0], C.hada(ca[1], sn, mods), mods),
+                 C.add(cb[0], C.hada(cb[1], sn, mods), mods), mods)
+    assert (lhs == rhs).all()
+
+
+@pytest.mark.parametrize("nl", [1, 4, 6, 9, 12])
+def test_keyswitch_error_bound(small, nl):
+    """ks0 + ks1 s - d2 s^2 is small in the coefficient domain.
+
+    Bound: sum over slices of N * (alpha + 1) * (Q_j / P) * max|e|, plus the
+    ModDown rounding (1 + ||s||_1)(K + 1).
+    """
+    prm, s, evk = small
+    mods, psis = prm.qs[:nl], prm.psi_q[:nl]
+    d2 = I.uniform_residues(50 + nl, mods, 1, prm.N, dtype=np.uint64)[:, 0]
+    k0, k1 = C.keyswitch(prm, nl, d2, evk)
+    sn = C.ntt(C.small_to_residues(s, mods), mods, psis)
+    diff = C.sub(C.add(k0, C.hada(k1, sn, mods), mods), C.hada(d2, C.hada(sn, sn, mods), mods), mods)
+    err = C.crt_centered(C.intt(diff, mods, psis), mods)
+    bound = 0.0
+    for j in range(prm.dnum(nl)):
+        Qj = math.prod(prm.qs[i] for i in prm.slice_limbs(j, nl))
+        bound += prm.N * (prm.alpha + 1) * Qj / prm.P * 19
+    bound += (1 + int(np.abs(s).sum())) * (prm.K + 1)
+    assert max(abs(e) for e in err) <= bound
+    assert math.prod(mods) > 1e6 * bound   # the check is meaningful
+
+
+def test_embedding_matches_direct_evaluation():
+    N = 32
+    m = np.random.default_rng(3).normal(size=N)
+    zeta = np.exp(1j * np.pi / N)
+    direct = np.array([sum(m[n] * zeta ** ((2 * k + 1) * n) for n in range(N)) for k in range(N)])
+    assert np.allclose(C.embed(m), direct, atol=1e-9)
+    z = np.random.default_rng(4).uniform(-1, 1, N // 2) + 1j * np.random.default_rng(5).uniform(-1, 1, N // 2)
+    mm = C.encode(z, N, 2.0 ** 40)
+    assert np.abs(C.decode(np.array(mm, dtype=float), 2.0 ** 40) - z).max() < N * 2.0 ** -40
+    for j, k in enumerate(C.slot_index(N)):
+        assert np.isclose(zeta ** (2 * k + 1), zeta ** pow(5, j, 2 * N))
+
+
+def test_embedding_is_multiplicative():
+    N = 64
+    za, zb = I.uniform_reals(1, N // 2), I.uniform_reals(2, N // 2)
+    ma, mb = C.encode(za, N, 2.0 ** 20), C.encode(zb, N, 2.0 ** 20)
+    full = [0] * (2 * N)
+    for i in range(N):
+        for j in range(N):
+            full[i + j] += ma[i] * mb[j]
+    prod = np.array([full[k] - full[k + N] for k in range(N)], dtype=float)
+    assert np.abs(C.decode(prod, 2.0 ** 40) - za * zb).max() < 1e-4
+
+
+def _hmult_case(N, nq, nl, h, seed):
+    qs, ps = P.default_moduli(nq, 8)
+    prm = C.Params(N, qs, ps, alpha=8)
+    s = I.ternary_secret(seed, N, hamming_weight=h)
+    L = len(qs)
+    arand = I.uniform_residues(seed + 1, qs + ps, prm.dnum(L), N, dtype=np.uint64).transpose(1, 0, 2)
+    evk = C.keygen_evk(prm, s, arand, I.gaussian_error(seed + 2, (prm.dnum(L), N)))
+    delta = 2.0 ** 30
+    za, zb = I.uniform_reals(seed + 3, N // 2), I.uniform_reals(seed + 4, N // 2)
+    cts = []
+    for k, z in enumerate((za, zb)):
+        m = C.encode(z, N, delta)
+        a = I.uniform_residues(seed + 5 + k, qs[:nl], 1, N, dtype=np.uint64)[:, 0]
+        cts.append(C.encrypt(prm, nl, m, s, a, I.gaussian_error(seed + 7 + k, N)))
+    out = C.hmult(prm, nl, cts[0], cts[1], evk)
+    scale = delta * delta / qs[nl - 1]
+    dec = C.decode(np.array(C.decrypt_coeffs(prm, out, s), dtype=float), scale)
+    ref = za * zb
+    return np.abs(dec - ref).max() / np.abs(ref).max()
+
+
+@pytest.mark.parametrize("N,nq,nl", [(1024, 24, 24), (1024, 24, 9), (2048, 12, 3)])
+def test_hmult_decrypts_to_product(N, nq, nl):
+    assert _hmult_case(N, nq, nl, 64, 70 + nl) < 1e-5
+
+
+def test_hmult_constant():
+    """Encryptions of constants: every slot of the product equals the product constant."""
+    N, nl = 512, 5
+    qs, ps = P.default_moduli(8, 8)
+    prm = C.Params(N, qs, ps, alpha=8)
+    s = I.ternary_secret(90, N, hamming_weight=64)
+    arand = I.uniform_residues(91, qs + ps, 1, N, dtype=np.uint64).transpose(1, 0, 2)
+    evk = C.keygen_evk(prm, s, arand, I.gaussian_error(92, (1, N)))
+    delta = 2.0 ** 30
+    cts = []
+    for k, v in enumerate((0.75, -0.5)):
+        m = C.encode(np.full(N // 2, v), N, delta)
+        assert m[0] == round(v * delta) and all(c == 0 for c in m[1:])
+        a = I.uniform_residues(93 + k, qs[:nl], 1, N, dtype=np.uint64)[:, 0]
+        cts.append(C.encrypt(prm, nl, m, s, a, I.gaussian_error(95 + k, N)))
+    out = C.hmult(prm, nl, cts[0], cts[1], evk)
+    dec = C.decode(np.array(C.decrypt_coeffs(prm, out, s), dtype=float), delta * delta / qs[nl - 1])
+    assert np.abs(dec - (-0.375)).max() < 1e-6
