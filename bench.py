@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Benchmark: batched negacyclic NTT KOPS at N = 2^16 and CKKS HMULT KOPS on one GB300.
+
+Workload of `value` (one step): forward NTT + inverse NTT, in place, of 64 polynomials x 44
+RNS limbs (30-bit primes q_0..q_43) at N = 2^16 -- one fhe_ntt_fwd and one fhe_ntt_inv call
+(704 MiB resident in HBM, larger than L2, so no flush is needed between steps). One op = one
+limb transform (the #NTT/s unit of Table VIII). The JSON line also carries both NTT paths,
+the HMULT throughput (N = 2^16, 24 + 8 limbs, dnum = 3, 128 ciphertext pairs per call), the
+end-to-end number through the C ABI with host buffers, the roofline of the dominant kernel
+and the CPU oracle timed on this host.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs the same per-GPU workload on its own GPU (replicas;
+the path has no exchange step) and rank 0 prints the aggregate.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NTT KOPS and HMULT KOPS at N=2^16 (INT8-TC vs plain CUDA), % INT8/HBM roofline"
+LOGN, N = 16, 1 << 16
+NTT_LIMBS, NTT_BATCH = 44, 64
+HM_LIMBS, HM_K, HM_ALPHA, HM_BATCH = 24, 8, 8, 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--hmult-steps", type=int, default=3)
+    ap.add_argument("--no-hmult", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi every 200 ms while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_for(kernel_file, key):
+    """Per-launch DRAM bytes of a kernel from a committed ncu summary, if still current."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(key)
+        with open(os.path.join(ROOT, kernel_file), "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()[:16]
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("source_sha256_16") != h:
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+# ------------------------------------------------------------------ CPU oracle (baseline leg)
+
+
+def cpu_oracle_kops(budget_s=10.0, batch_cap=NTT_BATCH):
+    """The C oracle (oracle/ntt_oracle.c, OpenMP over rows, as it stands) on a bounded
+    sample of the same workload: all 44 limbs x b polynomials, forward + inverse."""
+    from oracle import ntt as ON
+    from oracle import params as P
+    from paper_2212_14191_gb300 import inputs as I
+    qs, _ = P.default_moduli(NTT_LIMBS, 8)
+    psis = [P.psi(q, N) for q in qs]
+    b = 1
+    while True:
+        x = I.uniform_residues(5, qs, b, N)
+        t0 = time.perf_counter()
+        y, used = ON.ntt_batch(x, qs, psis)
+        z, _ = ON.ntt_batch(y, qs, psis, inverse=True)
+        dt = time.perf_counter() - t0
+        assert (z == x).all()
+        if dt * 2 > budget_s or b * 2 > batch_cap:
+            ops = 2 * NTT_LIMBS * b
+            return {"value": ops / dt / 1e3, "unit": "KOPS", "cores": used, "kind": "oracle",
+                    "sample": "%d limbs x %d polys, fwd+inv NTT at N=2^16 (%d limb transforms, %.1f s)"
+                              % (NTT_LIMBS, b, ops, dt)}
+        b *= 2
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import ntt as ON
+    from oracle import params as P
+    from paper_2212_14191_gb300 import inputs as I
+    qs, _ = P.default_moduli(NTT_LIMBS, 8)
+    psis = [P.psi(q, N) for q in qs]
+    b = 2  # each step: 44 limbs x 2 polynomials, forward + inverse (a bounded sample)
+    x = I.uniform_residues(5, qs, b, N)
+    used = 1
+    for _ in range(args.warmup):
+        y, used = ON.ntt_batch(x, qs, psis)
+        ON.ntt_batch(y, qs, psis, inverse=True)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        y, used = ON.ntt_batch(x, qs, psis)
+        ON.ntt_batch(y, qs, psis, inverse=True)
+    dt = time.perf_counter() - t0
+    ops = 2 * NTT_LIMBS * b * args.steps
+    v = ops / dt / 1e3
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "KOPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": "batched NTT+INTT, N=2^16, 44 limbs, per step 2 polynomials (sample of 64)",
+                   "timing": "host wall clock"},
+        "cpu_baseline": {"value": v, "unit": "KOPS", "cores": used, "kind": "oracle",
+                         "sample": "44 limbs x 2 polys fwd+inv per step at N=2^16"},
+        "e2e": {"value": v, "unit": "KOPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ------------------------------------------------------------------ GPU arm
+
+
+def ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2212_14191_gb300 import fhe
+    from paper_2212_14191_gb300 import inputs as I
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if ws == 1:
+            return v
+        import torch.distributed as dist
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    allp = fhe.fhe_gen_primes(16, 30, NTT_LIMBS + 8)
+    ps, qs = allp[:8], allp[8:]
+    ctx = fhe.Context(16, qs, ps, alpha=HM_ALPHA, default_path=fhe.FHE_NTT_U32)
+    st = torch.cuda.current_stream()
+    sh = st.cuda_stream
+    x_host = I.uniform_residues(1234 + rank, qs, NTT_BATCH, N)
+    x = fhe.to_device(x_host)
+    ops_per_step = 2 * NTT_LIMBS * NTT_BATCH
+
+    def step(path, ev=None):
+        if ev is not None:
+            ev[0].record(st)
+        fhe.fhe_ntt_fwd(ctx.handle, path, LOGN, x.data_ptr(), 0, NTT_LIMBS, NTT_BATCH, sh)
+        if ev is not None:
+            ev[1].record(st)
+        fhe.fhe_ntt_inv(ctx.handle, path, LOGN, x.data_ptr(), 0, NTT_LIMBS, NTT_BATCH, sh)
+        if ev is not None:
+            ev[2].record(st)
+
+    def time_path(path, steps, warmup):
+        for _ in range(warmup):
+            step(path)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(st)
+        for i in range(steps):
+            step(path, evs[i])
+        t1.record(st)
+        barrier()
+        total = t0.elapsed_time(t1) / 1e3
+        fwd = statistics.mean(e[0].elapsed_time(e[1]) for e in evs) / 1e3
+        inv = statistics.mean(e[1].elapsed_time(e[2]) for e in evs) / 1e3
+        return max_over_ranks(total), fwd, inv
+
+    paths = {"u32": fhe.FHE_NTT_U32}
+    results = {}
+    clocks = None
+    for name, path in paths.items():
+        if name == "u32":
+            with ClockSampler(local) as cs:
+                total, fwd, inv = time_path(path, args.steps, args.warmup)
+            clocks = cs.summary()
+        else:
+            total, fwd, inv = time_path(path, args.steps, args.warmup)
+        results[name] = {"kops": ops_per_step * args.steps * ws / total / 1e3,
+                         "fwd_ms": fwd * 1e3, "inv_ms": inv * 1e3}
+    head = "u32"
+    total_head = ops_per_step * args.steps * ws / (results[head]["kops"] * 1e3)
+    # end to end through the C ABI with host buffers: H2D, fwd, inv, D2H every step
+    pinned_in = torch.from_numpy(x_host.view(np.int32)).pin_memory()
+    pinned_out = torch.empty_like(pinned_in).pin_memory()
+    e2e_steps = max(2, args.steps // 2)
+    for _ in range(2):
+        x.copy_(pinned_in, non_blocking=True)
+        step(paths[head])
+        pinned_out.copy_(x, non_blocking=True)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(e2e_steps):
+        x.copy_(pinned_in, non_blocking=True)
+        step(paths[head])
+        pinned_out.copy_(x, non_blocking=True)
+    e1.record(st)
+    barrier()
+    e2e_t = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    assert np.array_equal(pinned_out.numpy().view(np.uint32), x_host)
+    nbytes = x_host.nbytes
+
+    # HMULT (N = 2^16, 24 + 8 limbs, dnum = 3, 128 pairs): uniform ciphertexts and key
+    hm = None
+    if not args.no_hmult:
+        hctx = fhe.Context(16, qs[:HM_LIMBS], ps, alpha=HM_ALPHA, default_path=fhe.FHE_NTT_U32)
+        a = fhe.to_device(I.uniform_residues(11, qs[:HM_LIMBS], 2 * HM_BATCH, N))
+        b = fhe.to_device(I.uniform_residues(12, qs[:HM_LIMBS], 2 * HM_BATCH, N))
+        a = a.view(HM_LIMBS, 2, HM_BATCH, N).permute(1, 0, 2, 3).contiguous()
+        b = b.view(HM_LIMBS, 2, HM_BATCH, N).permute(1, 0, 2, 3).contiguous()
+        dnum = -(-HM_LIMBS // HM_ALPHA)
+        evk = fhe.to_device(I.uniform_residues(13, qs[:HM_LIMBS] + ps, 2 * dnum, N)).view(
+            HM_LIMBS + HM_K, dnum, 2, N).permute(1, 2, 0, 3).contiguous()
+        out = torch.empty((2, HM_LIMBS - 1, HM_BATCH, N), dtype=torch.int32, device="cuda")
+        hctx.hmult(a, b, evk, LOGN, out=out)
+        barrier()
+        h0 = torch.cuda.Event(enable_timing=True)
+        h1 = torch.cuda.Event(enable_timing=True)
+        h0.record(st)
+        for _ in range(args.hmult_steps):
+            hctx.hmult(a, b, evk, LOGN, out=out)
+        h1.record(st)
+        barrier()
+        ht = max_over_ranks(h0.elapsed_time(h1) / 1e3)
+        hm = {"kops": HM_BATCH * args.hmult_steps * ws / ht / 1e3,
+              "ms_per_call": ht / args.hmult_steps * 1e3,
+              "config": "N=2^16, 24 ciphertext limbs + 8 special primes, dnum=3, 128 pairs per call, "
+                        "HMULT + relinearisation + rescale"}
+        del a, b, evk, out
+        hctx.close()
+
+    if rank == 0:
+        peaks, peak_kind = measured_peaks()
+        fwd_s = results[head]["fwd_ms"] / 1e3
+        alg_bytes = 8 * N * NTT_LIMBS * NTT_BATCH   # read + write N u32 per limb transform
+        achieved = alg_bytes / fwd_s / 1e9
+        line = {
+            "metric": METRIC,
+            "value": results[head]["kops"],
+            "unit": "KOPS",
+            "n_gpus": ws,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": total_head / args.steps * 1e3,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": "batched negacyclic NTT+INTT, N=2^16, 44 RNS limbs (30-bit primes), "
+                                   "64 polynomials (704 MiB); one op = one limb transform",
+                       "path": head, "l2": "inputs larger than L2 (704 MiB), no flush",
+                       "parallelism": "replicas" if ws > 1 else "1 GPU"},
+            "paths": results,
+            "hmult": hm,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "peak_kind": peak_kind,
+                         "kernel": "ntt_fwd_kernel<9,2> (u32, N=2^16)",
+                         "traffic": traffic_for("paper_2212_14191_gb300/csrc/ntt_u32.cu", "ntt_fwd_u32_n65536")},
+            "e2e": {"value": ops_per_step * e2e_steps * ws / e2e_t / 1e3, "unit": "KOPS",
+                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clocks,
+        }
+        if not args.no_cpu:
+            line["cpu_baseline"] = cpu_oracle_kops()
+        print(json.dumps(line))
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

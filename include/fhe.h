@@ -1,0 +1,170 @@
+/*
+ * fhe.h -- C ABI of libfhe: batched negacyclic NTT/INTT and CKKS HMULT on one
+ * NVIDIA GB300 (sm_103a), after TensorFHE (arXiv 2212.14191).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Residues are uint32 values in canonical form [0, q) for the limb's prime q.
+ * - Polynomial data use the limb-major (L, B, N) layout of Sec. IV-D: limb l of
+ *   polynomial b starts at element (l * B + b) * N and holds N coefficients
+ *   (coefficient domain) or N NTT values (NTT domain, natural order k = 0..N-1).
+ * - A ciphertext batch is (2, L, B, N): component c (c = 0, 1) first. The pair
+ *   decrypts as c0 + c1 * s; both components are stored in the NTT domain.
+ * - "Modulus index" t numbers the context's moduli: q_0..q_{nq-1} are t = 0..nq-1
+ *   and the special primes p_0..p_{np-1} are t = nq..nq+np-1.
+ * - Device pointers are caller-owned, must be 16-byte aligned and must stay valid
+ *   until the work queued on `stream` has finished. Host pointers are read (or
+ *   written) before the call returns unless stated otherwise.
+ * - Every call is asynchronous on the given CUDA stream (cudaStream_t passed as
+ *   void*; NULL is the legacy default stream) and returns a status code. Nothing
+ *   throws across the ABI. fhe_last_error() gives a message for the calling
+ *   thread's most recent failure.
+ * - Inputs are not checked for being below q (an input >= q gives an unspecified
+ *   but in-bounds result); every other argument is validated before any launch.
+ */
+#ifndef FHE_H
+#define FHE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define FHE_OK 0
+#define FHE_EINVAL 1   /* malformed call: range, null/misaligned pointer, bad moduli */
+#define FHE_ENOMEM 2   /* scratch too small, or a library allocation failed */
+#define FHE_ECUDA 3    /* a CUDA launch or runtime call failed (message has the CUDA error) */
+#define FHE_ETIMEOUT 4 /* a bounded device-side wait expired */
+
+/* NTT implementations (Sec. IV-B/IV-C). FHE_NTT_DEFAULT picks the context's default. */
+#define FHE_NTT_DEFAULT 0
+#define FHE_NTT_U32 1 /* 32-bit integer butterflies on CUDA cores (Shoup/Harvey arithmetic) */
+#define FHE_NTT_TC 2  /* four-step NTT, 8-bit segments on tcgen05 tensor cores */
+
+#define FHE_LOGN_MIN 10
+#define FHE_LOGN_MAX 16
+#define FHE_MAX_MODULI 64
+
+typedef struct fhe_ctx fhe_ctx;
+
+/*
+ * fhe_gen_primes -- the `count` largest primes q < 2^bits with q = 1 mod 2^(logN_max+1),
+ * in descending order, written to host array out[count].
+ * Sec. II-A only asks for a prime with a primitive N-th (here 2N-th) root of unity; this
+ * helper fixes one deterministic choice. bits in [20, 31], logN_max in [10, 16].
+ * Returns FHE_EINVAL when fewer than `count` such primes exist above 2^(bits-1).
+ */
+int fhe_gen_primes(uint32_t logN_max, int bits, int count, uint32_t* out);
+
+/*
+ * fhe_ctx_create -- validate the moduli and build every per-modulus table on the device.
+ *   logN_max : tables are built for every N = 2^logN, FHE_LOGN_MIN <= logN <= logN_max.
+ *   q[nq]    : ciphertext primes q_0..q_{nq-1} (host array), the RNS limbs of Sec. II-B.
+ *   p[np]    : special primes p_0..p_{np-1} of generalized key switching (Sec. II-B); np may
+ *              be 0 (then HMULT and key switching are unavailable).
+ *   alpha    : primes per key-switching slice Q_j (Sec. II-B: alpha = (L+1)/dnum); the last
+ *              slice may be short. Requires prod(p) > every slice product (checked).
+ *   default_path : FHE_NTT_U32 or FHE_NTT_TC, used by FHE_NTT_DEFAULT and by the HMULT pipeline.
+ * Every prime must be distinct, prime, < 2^30 and = 1 mod 2^(logN_max+1); nq + np <= 64;
+ * 1 <= alpha <= 15; np <= 15. The context owns its device tables and is immutable after
+ * creation, so concurrent calls on different streams may share it.
+ * Allocates device memory (cudaMalloc) on the current device; *out = NULL on failure.
+ */
+int fhe_ctx_create(uint32_t logN_max, const uint32_t* q, int nq, const uint32_t* p, int np,
+                   int alpha, int default_path, fhe_ctx** out);
+
+/* Frees the context's device tables. Work using the context must have completed. */
+int fhe_ctx_destroy(fhe_ctx* ctx);
+
+/*
+ * fhe_ntt_fwd -- in-place negacyclic NTT of Eq. (4), Sec. II-A:
+ *     A_k = sum_{n<N} a_n * psi^(2nk+n) mod q,   k in [0, N), natural order in and out,
+ * psi = x^((q-1)/2N) for the smallest quadratic non-residue x of q.
+ *   d          : device (n_limbs, batch, N) uint32, transformed in place.
+ *   first_limb : modulus index of limb 0; limb l uses modulus first_limb + l.
+ *   path       : FHE_NTT_DEFAULT, FHE_NTT_U32 or FHE_NTT_TC.
+ * n_limbs >= 1, first_limb + n_limbs <= nq + np, batch >= 0 (0 is a no-op).
+ */
+int fhe_ntt_fwd(const fhe_ctx* ctx, int path, uint32_t logN, uint32_t* d, int first_limb,
+                int n_limbs, int batch, void* stream);
+
+/*
+ * fhe_ntt_inv -- in-place inverse of fhe_ntt_fwd (Sec. II-A, Eq. (2) with the psi^-n
+ * post-twist of Eq. (3); Sec. IV-C Stage 5 names the N^-1 factor):
+ *     a_n = N^-1 * psi^-n * sum_{k<N} A_k * psi^(-2nk) mod q.
+ * Arguments as fhe_ntt_fwd.
+ */
+int fhe_ntt_inv(const fhe_ctx* ctx, int path, uint32_t logN, uint32_t* d, int first_limb,
+                int n_limbs, int batch, void* stream);
+
+/* Operations for fhe_scratch_bytes. */
+#define FHE_OP_HMULT 1
+#define FHE_OP_KEYSWITCH 2
+#define FHE_OP_RESCALE 3
+#define FHE_OP_HMULT_RELIN 4
+
+/*
+ * fhe_scratch_bytes -- device scratch (bytes) that fhe_hmult / fhe_keyswitch /
+ * fhe_rescale / fhe_hmult_relin need for these sizes; 0 for invalid arguments.
+ */
+size_t fhe_scratch_bytes(const fhe_ctx* ctx, int op, uint32_t logN, int n_limbs, int batch);
+
+/*
+ * fhe_keyswitch -- generalized (hybrid) key switching of Sec. II-B / Sec. IV-A (Alg. 1):
+ * Dcomp + ModUp per slice, inner product with the evaluation key, ModDown.
+ *   d2     : device (n_limbs, batch, N), NTT domain, limbs q_0..q_{n_limbs-1}.
+ *   evk    : device (dnum, 2, nq + np, N), NTT domain, dnum = ceil(nq / alpha); slice j,
+ *            component c, modulus index t at ((j*2 + c)*(nq+np) + t) * N. Only limbs
+ *            t < n_limbs and t >= nq are read.
+ *   ks_out : device (2, n_limbs, batch, N): (ks0, ks1) with ks0 + ks1*s ~ d2 * s^2.
+ *   scratch: device buffer of at least fhe_scratch_bytes(ctx, FHE_OP_KEYSWITCH, ...) bytes.
+ * 1 <= n_limbs <= nq. ks_out must not overlap d2 or scratch.
+ */
+int fhe_keyswitch(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const uint32_t* d2,
+                  const uint32_t* evk, uint32_t* ks_out, void* scratch, size_t scratch_bytes,
+                  void* stream);
+
+/*
+ * fhe_hmult_relin -- HMULT of Sec. II-B without rescale:
+ *   (d0, d1, d2) = (a0*b0, a0*b1 + a1*b0, a1*b1);  out = (d0 + ks0, d1 + ks1), (ks0, ks1) =
+ *   KeySwitch(d2).
+ *   ct_a, ct_b : device (2, n_limbs, batch, N) NTT domain.   out : device (2, n_limbs, batch, N).
+ * out must not overlap the inputs or scratch. 1 <= n_limbs <= nq.
+ */
+int fhe_hmult_relin(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch,
+                    const uint32_t* ct_a, const uint32_t* ct_b, const uint32_t* evk,
+                    uint32_t* out, void* scratch, size_t scratch_bytes, void* stream);
+
+/*
+ * fhe_rescale -- RESCALE of Sec. II-B (Alg. 6): divide by the last prime q_l, rounding to
+ * nearest (the last limb is centred to (-q_l/2, q_l/2] before subtraction).
+ *   ct_in  : device (2, n_limbs, batch, N), NTT domain.
+ *   ct_out : device (2, n_limbs - 1, batch, N); may not overlap ct_in.
+ * 2 <= n_limbs <= nq.
+ */
+int fhe_rescale(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const uint32_t* ct_in,
+                uint32_t* ct_out, void* scratch, size_t scratch_bytes, void* stream);
+
+/*
+ * fhe_hmult -- HMULT with relinearisation followed by RESCALE (Sec. II-B; Alg. 2 then Alg. 6):
+ *   ct_a, ct_b : device (2, n_limbs, batch, N); ct_out : device (2, n_limbs - 1, batch, N).
+ * 2 <= n_limbs <= nq. ct_out must not overlap inputs or scratch.
+ */
+int fhe_hmult(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const uint32_t* ct_a,
+              const uint32_t* ct_b, const uint32_t* evk, uint32_t* ct_out, void* scratch,
+              size_t scratch_bytes, void* stream);
+
+/*
+ * fhe_last_error -- copy the calling thread's last error message (NUL-terminated, truncated
+ * to n bytes) into buf; returns the status code of that failure (FHE_OK if none).
+ */
+int fhe_last_error(char* buf, size_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FHE_H */

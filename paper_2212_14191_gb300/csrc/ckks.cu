@@ -1,0 +1,530 @@
+// CKKS HMULT pipeline on the GPU: tensor product, generalized key switching (Dcomp/ModUp,
+// inner product, ModDown) and RESCALE, composed from the kernels named in Sec. IV-A
+// (Hada-Mult, Ele-Add, Ele-Sub, Conv, NTT).
+//
+// Every elementwise / basis-conversion stage is a coalesced, 16-byte vectorised stream over
+// the (L, B, N) layout of Sec. IV-D: grid.y is the limb (so the modulus is uniform per block)
+// and grid.x strides over the B*N residues of that limb.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace fhe {
+namespace {
+
+struct ModVec {
+    uint32_t q[kMaxLimbs];
+    uint64_t mu[kMaxLimbs];  // floor(2^64 / q) for 64-bit Barrett
+};
+
+ModVec modvec(const fhe_ctx* ctx, const int* mod_idx, int n) {
+    ModVec m;
+    for (int l = 0; l < n; ++l) {
+        m.q[l] = ctx->mods[mod_idx[l]];
+        m.mu[l] = ~0ull / m.q[l];
+    }
+    return m;
+}
+
+__device__ __forceinline__ uint4 ld4(const uint32_t* p, size_t i) {
+    return __ldg(reinterpret_cast<const uint4*>(p) + i);
+}
+__device__ __forceinline__ void st4(uint32_t* p, size_t i, uint4 v) {
+    reinterpret_cast<uint4*>(p)[i] = v;
+}
+__device__ __forceinline__ uint32_t get(const uint4& v, int k) {
+    return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ void set(uint4& v, int k, uint32_t x) {
+    if (k == 0) v.x = x;
+    else if (k == 1) v.y = x;
+    else if (k == 2) v.z = x;
+    else v.w = x;
+}
+
+// ---- HM-1: tensor product (Hada-Mult + Ele-Add), d2 written twice (NTT form + copy for INTT)
+__global__ void k_tensor(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b,
+                         uint32_t* __restrict__ d0, uint32_t* __restrict__ d1,
+                         uint32_t* __restrict__ d2, uint32_t* __restrict__ d2c, size_t L4,
+                         size_t comp4, ModVec m) {
+    const int l = blockIdx.y;
+    const uint32_t q = m.q[l];
+    const uint64_t mu = m.mu[l];
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < L4; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t idx = (size_t)l * L4 + i;
+        uint4 a0 = ld4(a, idx), a1 = ld4(a, comp4 + idx), b0 = ld4(b, idx), b1 = ld4(b, comp4 + idx);
+        uint4 r0, r1, r2;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t x0 = get(a0, k), x1 = get(a1, k), y0 = get(b0, k), y1 = get(b1, k);
+            set(r0, k, reduce_u64((uint64_t)x0 * y0, mu, q));
+            set(r1, k, reduce_u64((uint64_t)x0 * y1 + (uint64_t)x1 * y0, mu, q));
+            set(r2, k, reduce_u64((uint64_t)x1 * y1, mu, q));
+        }
+        st4(d0, idx, r0);
+        st4(d1, idx, r1);
+        st4(d2, idx, r2);
+        st4(d2c, idx, r2);
+    }
+}
+
+// ---- KS-2 / KS-5: Conv (fast basis conversion, Sec. IV-A)
+//   y_i = [x_i * (B/b_i)^-1]_{b_i};  out_t = sum_i y_i * [B/b_i]_t  mod t
+struct ConvArgs {
+    const uint32_t* src;
+    size_t src_stride;  // elements between source limbs
+    int nsrc;
+    uint32_t src_q[16];
+    uint2 hat_inv[16];
+    const uint32_t* hat_mod;  // [nsrc][nmod]
+    int nmod;
+    uint32_t* dst;
+    size_t dst_stride;
+    int ndst;
+    uint8_t dst_mod[kMaxLimbs];
+    ModVec dm;
+    size_t L4;  // residues per limb / 4
+};
+
+__global__ void __launch_bounds__(256) k_conv(const ConvArgs a) {
+    extern __shared__ uint32_t s_hat[];  // [nsrc][ndst]
+    for (int k = threadIdx.x; k < a.nsrc * a.ndst; k += blockDim.x) {
+        int i = k / a.ndst, t = k % a.ndst;
+        s_hat[k] = a.hat_mod[(size_t)i * a.nmod + a.dst_mod[t]];
+    }
+    __syncthreads();
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < a.L4; n += (size_t)gridDim.x * blockDim.x) {
+        uint4 y[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            if (i < a.nsrc) {
+                uint4 x = ld4(a.src, i * (a.src_stride / 4) + n);
+                const uint32_t b = a.src_q[i];
+                const uint2 h = a.hat_inv[i];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) set(y[i], k, mul_shoup(get(x, k), h.x, h.y, b));
+            }
+        }
+        for (int t = 0; t < a.ndst; ++t) {
+            uint64_t acc[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                if (i < a.nsrc) {
+                    const uint64_t h = s_hat[i * a.ndst + t];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) acc[k] += (uint64_t)get(y[i], k) * h;
+                }
+            }
+            uint4 r;
+            const uint32_t qt = a.dm.q[t];
+            const uint64_t mu = a.dm.mu[t];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) set(r, k, reduce_u64(acc[k], mu, qt));
+            st4(a.dst, t * (a.dst_stride / 4) + n, r);
+        }
+    }
+}
+
+// ---- KS-4: inner product with the evaluation key (Hada-Mult + Ele-Add)
+struct IpArgs {
+    const uint32_t* d2;   // (nl, B, N) NTT domain
+    const uint32_t* tmp;  // (nl - (hi - lo) + K, B, N) NTT domain: q limbs outside [lo,hi), then P
+    const uint32_t* evk;  // (dnum, 2, nmod, N)
+    uint32_t* ks;         // (2, nl + K, B, N)
+    int nl, lo, hi, j, nq, nmod, first;
+    size_t L4, N4;        // residues per limb / 4, N / 4
+    ModVec m;             // per extended limb t < nl + K
+};
+
+__global__ void k_inner_product(const IpArgs a) {
+    const int t = blockIdx.y;
+    const int ext = gridDim.y;
+    const uint32_t q = a.m.q[t];
+    const uint64_t mu = a.m.mu[t];
+    const uint32_t* src = (t >= a.lo && t < a.hi) ? a.d2 + (size_t)t * a.L4 * 4
+                                                   : a.tmp + (size_t)(t < a.lo ? t : t - (a.hi - a.lo)) * a.L4 * 4;
+    const int mod = t < a.nl ? t : a.nq + (t - a.nl);
+    const uint32_t* e0 = a.evk + ((size_t)(a.j * 2 + 0) * a.nmod + mod) * a.N4 * 4;
+    const uint32_t* e1 = a.evk + ((size_t)(a.j * 2 + 1) * a.nmod + mod) * a.N4 * 4;
+    uint32_t* k0 = a.ks + (size_t)t * a.L4 * 4;
+    uint32_t* k1 = a.ks + (size_t)(ext + t) * a.L4 * 4;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < a.L4; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t n4 = i % a.N4;
+        uint4 x = ld4(src, i), w0 = ld4(e0, n4), w1 = ld4(e1, n4);
+        uint4 r0, r1;
+        if (a.first) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                set(r0, k, reduce_u64((uint64_t)get(x, k) * get(w0, k), mu, q));
+                set(r1, k, reduce_u64((uint64_t)get(x, k) * get(w1, k), mu, q));
+            }
+        } else {
+            uint4 s0 = ld4(k0, i), s1 = ld4(k1, i);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                set(r0, k, reduce_u64((uint64_t)get(x, k) * get(w0, k) + get(s0, k), mu, q));
+                set(r1, k, reduce_u64((uint64_t)get(x, k) * get(w1, k) + get(s1, k), mu, q));
+            }
+        }
+        st4(k0, i, r0);
+        st4(k1, i, r1);
+    }
+}
+
+// ---- KS-5 tail + HM-2: out_c[i] (+)= (ks_c[i] - y_c[i]) * [P^-1]_{q_i}
+__global__ void k_moddown_combine(const uint32_t* __restrict__ ks, const uint32_t* __restrict__ y,
+                                  uint32_t* __restrict__ out, const uint2* __restrict__ pinv, int nl,
+                                  int ext, int accumulate, size_t L4, ModVec m) {
+    const int c = blockIdx.y / nl, i = blockIdx.y % nl;
+    const uint32_t q = m.q[i];
+    const uint2 pi = __ldg(&pinv[i]);
+    const uint32_t* kp = ks + ((size_t)c * ext + i) * L4 * 4;
+    const uint32_t* yp = y + ((size_t)c * nl + i) * L4 * 4;
+    uint32_t* op = out + ((size_t)c * nl + i) * L4 * 4;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < L4; n += (size_t)gridDim.x * blockDim.x) {
+        uint4 kv = ld4(kp, n), yv = ld4(yp, n);
+        uint4 ov = accumulate ? ld4(op, n) : make_uint4(0, 0, 0, 0);
+        uint4 r;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t d = get(kv, k) + q - get(yv, k);                 // [1, 2q)
+            uint32_t v = mul_shoup(d, pi.x, pi.y, q) + get(ov, k);    // [0, 2q)
+            set(r, k, csub(v, q));
+        }
+        st4(op, n, r);
+    }
+}
+
+// ---- RS-1: gather the last limb of both components
+__global__ void k_copy_limb(const uint32_t* __restrict__ ct, uint32_t* __restrict__ out, int nl, size_t L4) {
+    const int c = blockIdx.y;
+    const uint32_t* src = ct + ((size_t)c * nl + (nl - 1)) * L4 * 4;
+    uint32_t* dst = out + (size_t)c * L4 * 4;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < L4; n += (size_t)gridDim.x * blockDim.x)
+        st4(dst, n, ld4(src, n));
+}
+
+// x in [0, q_l) -> centred value (x - q_l if x > (q_l - 1)/2) reduced mod q_i, for i < nl - 1
+__global__ void k_rescale_broadcast(const uint32_t* __restrict__ last, uint32_t* __restrict__ xb,
+                                    uint32_t ql, int nout, size_t L4, ModVec m) {
+    const int c = blockIdx.y / nout, i = blockIdx.y % nout;
+    const uint32_t q = m.q[i];
+    const uint32_t* src = last + (size_t)c * L4 * 4;
+    uint32_t* dst = xb + ((size_t)c * nout + i) * L4 * 4;
+    const uint32_t half = (ql - 1) / 2;
+    const uint32_t ql_mod = ql % q;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < L4; n += (size_t)gridDim.x * blockDim.x) {
+        uint4 x = ld4(src, n), r;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t v = get(x, k);
+            // v <= half: v mod q;  v > half: (v - ql) mod q = (v mod q) - (ql mod q) mod q
+            uint32_t vm = v % q;
+            uint32_t o = v > half ? (vm + q - ql_mod) : vm;
+            set(r, k, csub(o, q));
+        }
+        st4(dst, n, r);
+    }
+}
+
+// out_c[i] = (ct_c[i] - xb_c[i]) * [q_l^-1]_{q_i}
+__global__ void k_rescale_final(const uint32_t* __restrict__ ct, const uint32_t* __restrict__ xb,
+                                uint32_t* __restrict__ out, const uint2* __restrict__ qlinv, int nl,
+                                size_t L4, ModVec m) {
+    const int nout = nl - 1;
+    const int c = blockIdx.y / nout, i = blockIdx.y % nout;
+    const uint32_t q = m.q[i];
+    const uint2 w = __ldg(&qlinv[i]);
+    const uint32_t* cp = ct + ((size_t)c * nl + i) * L4 * 4;
+    const uint32_t* xp = xb + ((size_t)c * nout + i) * L4 * 4;
+    uint32_t* op = out + ((size_t)c * nout + i) * L4 * 4;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < L4; n += (size_t)gridDim.x * blockDim.x) {
+        uint4 cv = ld4(cp, n), xv = ld4(xp, n), r;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) set(r, k, mul_shoup(get(cv, k) + q - get(xv, k), w.x, w.y, q));
+        st4(op, n, r);
+    }
+}
+
+// ------------------------------------------------------------------ host orchestration
+
+dim3 stream_grid(const fhe_ctx* ctx, size_t L4, int limbs) {
+    // enough blocks per limb to cover ~4 waves of the GPU across all limbs
+    size_t want = (size_t)ctx->num_sms * 8 * 4 / (size_t)std::max(1, limbs) + 1;
+    size_t need = (L4 + 255) / 256;
+    size_t gx = std::min(want, need);
+    if (gx < 1) gx = 1;
+    return dim3((unsigned)gx, (unsigned)limbs, 1);
+}
+
+struct Sizes {
+    size_t N, limb;  // residues per limb (B * N)
+    int nl, K, ext;
+};
+
+size_t ks_scratch_limbs(int nl, int K) {
+    // d2c (nl) + tmp (nl + K) + ks (2 (nl + K)) + y (2 nl)
+    return (size_t)nl + (nl + K) + 2 * (size_t)(nl + K) + 2 * (size_t)nl;
+}
+
+// Key switching of d2 (NTT form) into `out` (2, nl, B, N); accumulate != 0 adds to out.
+// d2c (nl limbs of scratch) may already hold a copy of d2 when d2c_ready != 0.
+int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint32_t* d2,
+                   const uint32_t* evk, uint32_t* out, int accumulate, uint32_t* scratch,
+                   bool d2c_ready, cudaStream_t st) {
+    const size_t N = 1ull << logN, limb = N * batch, L4 = limb / 4;
+    const int K = ctx->np, ext = nl + K, alpha = ctx->alpha, nq = ctx->nq;
+    const int nmod = (int)ctx->mods.size();
+    uint32_t* d2c = scratch;
+    uint32_t* tmp = d2c + (size_t)nl * limb;
+    uint32_t* ks = tmp + (size_t)ext * limb;
+    uint32_t* y = ks + 2 * (size_t)ext * limb;
+    int rc;
+    if (!d2c_ready) FHE_CUDA_TRY(cudaMemcpyAsync(d2c, d2, (size_t)nl * limb * 4, cudaMemcpyDeviceToDevice, st));
+    // KS-1: INTT(d2)
+    if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, true, d2c, nl, batch, contiguous_map(ctx, 0, nl), st))) return rc;
+    int ext_mod[kMaxLimbs];
+    for (int t = 0; t < ext; ++t) ext_mod[t] = t < nl ? t : nq + (t - nl);
+    ModVec ext_m = modvec(ctx, ext_mod, ext);
+    const int dnum = (nl + alpha - 1) / alpha;
+    for (int j = 0; j < dnum; ++j) {
+        const int lo = j * alpha, hi = std::min(nl, (j + 1) * alpha);
+        const ConvTable& ct = ctx->modup[j][hi - lo - 1];
+        // KS-2: Conv Q_j -> (Q_l \ Q_j) u P
+        ConvArgs ca;
+        ca.src = d2c + (size_t)lo * limb;
+        ca.src_stride = limb;
+        ca.nsrc = hi - lo;
+        for (int i = 0; i < ca.nsrc; ++i) {
+            ca.src_q[i] = ctx->mods[lo + i];
+            ca.hat_inv[i] = ct.hat_inv_h[i];
+        }
+        ca.hat_mod = ct.hat_mod;
+        ca.nmod = nmod;
+        ca.dst = tmp;
+        ca.dst_stride = limb;
+        int dmod[kMaxLimbs];
+        int nd = 0;
+        for (int t = 0; t < nl; ++t)
+            if (t < lo || t >= hi) dmod[nd++] = t;
+        for (int k = 0; k < K; ++k) dmod[nd++] = nq + k;
+        ca.ndst = nd;
+        for (int t = 0; t < nd; ++t) ca.dst_mod[t] = (uint8_t)dmod[t];
+        ca.dm = modvec(ctx, dmod, nd);
+        ca.L4 = L4;
+        size_t smem = (size_t)ca.nsrc * nd * 4;
+        dim3 g = stream_grid(ctx, L4, 1);
+        g.x = std::min<unsigned>(g.x * 4, (unsigned)((L4 + 255) / 256));
+        k_conv<<<g, 256, smem, st>>>(ca);
+        FHE_CUDA_TRY(cudaGetLastError());
+        // KS-3: NTT of the converted limbs
+        LimbMap lm;
+        for (int t = 0; t < nd; ++t) {
+            lm.mod[t] = (uint8_t)dmod[t];
+            lm.q[t] = ctx->mods[dmod[t]];
+        }
+        if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, false, tmp, nd, batch, lm, st))) return rc;
+        // KS-4: inner product
+        IpArgs ia;
+        ia.d2 = d2;
+        ia.tmp = tmp;
+        ia.evk = evk;
+        ia.ks = ks;
+        ia.nl = nl;
+        ia.lo = lo;
+        ia.hi = hi;
+        ia.j = j;
+        ia.nq = nq;
+        ia.nmod = nmod;
+        ia.first = (j == 0);
+        ia.L4 = L4;
+        ia.N4 = N / 4;
+        ia.m = ext_m;
+        k_inner_product<<<stream_grid(ctx, L4, ext), 256, 0, st>>>(ia);
+        FHE_CUDA_TRY(cudaGetLastError());
+    }
+    // KS-5: ModDown of ks0, ks1
+    LimbMap pm = contiguous_map(ctx, nq, K);
+    for (int c = 0; c < 2; ++c)
+        if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, true, ks + ((size_t)c * ext + nl) * limb, K, batch, pm, st)))
+            return rc;
+    for (int c = 0; c < 2; ++c) {
+        ConvArgs ca;
+        ca.src = ks + ((size_t)c * ext + nl) * limb;
+        ca.src_stride = limb;
+        ca.nsrc = K;
+        for (int k = 0; k < K; ++k) {
+            ca.src_q[k] = ctx->mods[nq + k];
+            ca.hat_inv[k] = ctx->moddown.hat_inv_h[k];
+        }
+        ca.hat_mod = ctx->moddown.hat_mod;
+        ca.nmod = nmod;
+        ca.dst = y + (size_t)c * nl * limb;
+        ca.dst_stride = limb;
+        ca.ndst = nl;
+        int dmod[kMaxLimbs];
+        for (int t = 0; t < nl; ++t) {
+            dmod[t] = t;
+            ca.dst_mod[t] = (uint8_t)t;
+        }
+        ca.dm = modvec(ctx, dmod, nl);
+        ca.L4 = L4;
+        dim3 g = stream_grid(ctx, L4, 1);
+        g.x = std::min<unsigned>(g.x * 4, (unsigned)((L4 + 255) / 256));
+        k_conv<<<g, 256, (size_t)K * nl * 4, st>>>(ca);
+        FHE_CUDA_TRY(cudaGetLastError());
+    }
+    LimbMap qm2;
+    for (int c = 0; c < 2; ++c)
+        for (int i = 0; i < nl; ++i) {
+            qm2.mod[c * nl + i] = (uint8_t)i;
+            qm2.q[c * nl + i] = ctx->mods[i];
+        }
+    if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, false, y, 2 * nl, batch, qm2, st))) return rc;
+    int qidx[kMaxLimbs];
+    for (int i = 0; i < nl; ++i) qidx[i] = i;
+    k_moddown_combine<<<stream_grid(ctx, L4, 2 * nl), 256, 0, st>>>(ks, y, out, ctx->p_inv, nl, ext, accumulate,
+                                                                  L4, modvec(ctx, qidx, nl));
+    FHE_CUDA_TRY(cudaGetLastError());
+    return FHE_OK;
+}
+
+size_t rescale_scratch_limbs(int nl) { return 2 + 2 * (size_t)(nl - 1); }
+
+int rescale_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint32_t* ct, uint32_t* out,
+                 uint32_t* scratch, cudaStream_t st) {
+    const size_t N = 1ull << logN, limb = N * batch, L4 = limb / 4;
+    const int nout = nl - 1;
+    uint32_t* last = scratch;
+    uint32_t* xb = last + 2 * limb;
+    int rc;
+    k_copy_limb<<<stream_grid(ctx, L4, 2), 256, 0, st>>>(ct, last, nl, L4);
+    FHE_CUDA_TRY(cudaGetLastError());
+    LimbMap lm;
+    lm.mod[0] = lm.mod[1] = (uint8_t)(nl - 1);
+    lm.q[0] = lm.q[1] = ctx->mods[nl - 1];
+    if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, true, last, 2, batch, lm, st))) return rc;
+    int qidx[kMaxLimbs];
+    for (int i = 0; i < nout; ++i) qidx[i] = i;
+    ModVec qm = modvec(ctx, qidx, nout);
+    k_rescale_broadcast<<<stream_grid(ctx, L4, 2 * nout), 256, 0, st>>>(last, xb, ctx->mods[nl - 1], nout, L4, qm);
+    FHE_CUDA_TRY(cudaGetLastError());
+    LimbMap qm2;
+    for (int c = 0; c < 2; ++c)
+        for (int i = 0; i < nout; ++i) {
+            qm2.mod[c * nout + i] = (uint8_t)i;
+            qm2.q[c * nout + i] = ctx->mods[i];
+        }
+    if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, false, xb, 2 * nout, batch, qm2, st))) return rc;
+    k_rescale_final<<<stream_grid(ctx, L4, 2 * nout), 256, 0, st>>>(ct, xb, out, ctx->ql_inv + (size_t)(nl - 1) * ctx->nq,
+                                                                   nl, L4, qm);
+    FHE_CUDA_TRY(cudaGetLastError());
+    return FHE_OK;
+}
+
+int hmult_relin_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint32_t* a, const uint32_t* b,
+                     const uint32_t* evk, uint32_t* out, uint32_t* scratch, cudaStream_t st) {
+    const size_t N = 1ull << logN, limb = N * batch, L4 = limb / 4;
+    uint32_t* d2 = scratch;
+    uint32_t* ks_scratch = d2 + (size_t)nl * limb;  // begins with d2c
+    int qidx[kMaxLimbs];
+    for (int i = 0; i < nl; ++i) qidx[i] = i;
+    k_tensor<<<stream_grid(ctx, L4, nl), 256, 0, st>>>(a, b, out, out + (size_t)nl * limb, d2, ks_scratch, L4,
+                                                     (size_t)nl * L4, modvec(ctx, qidx, nl));
+    FHE_CUDA_TRY(cudaGetLastError());
+    return keyswitch_impl(ctx, logN, nl, batch, d2, evk, out, 1, ks_scratch, true, st);
+}
+
+bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+int check_ckks(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, int min_nl) {
+    FHE_CHECK(ctx != nullptr, "ctx is NULL");
+    FHE_CHECK(ctx->np > 0, "context has no special primes");
+    FHE_CHECK(logN >= FHE_LOGN_MIN && logN <= ctx->logN_max, "logN out of [10, logN_max]");
+    FHE_CHECK(nl >= min_nl && nl <= ctx->nq, "n_limbs out of range");
+    FHE_CHECK(batch >= 0, "batch < 0");
+    return FHE_OK;
+}
+
+int check_ptrs(std::initializer_list<const void*> ps) {
+    for (const void* p : ps) FHE_CHECK(p != nullptr && al16(p), "pointer NULL or not 16-byte aligned");
+    return FHE_OK;
+}
+
+size_t scratch_limbs(const fhe_ctx* ctx, int op, int nl) {
+    const int K = ctx->np;
+    switch (op) {
+        case FHE_OP_KEYSWITCH: return ks_scratch_limbs(nl, K);
+        case FHE_OP_HMULT_RELIN: return (size_t)nl + ks_scratch_limbs(nl, K);
+        case FHE_OP_RESCALE: return rescale_scratch_limbs(nl);
+        case FHE_OP_HMULT:
+            return 2 * (size_t)nl + std::max((size_t)nl + ks_scratch_limbs(nl, K), rescale_scratch_limbs(nl));
+        default: return 0;
+    }
+}
+
+}  // namespace
+}  // namespace fhe
+
+using namespace fhe;
+
+extern "C" {
+
+size_t fhe_scratch_bytes(const fhe_ctx* ctx, int op, uint32_t logN, int n_limbs, int batch) {
+    if (!ctx || ctx->np == 0 || logN < FHE_LOGN_MIN || logN > ctx->logN_max || n_limbs < 1 ||
+        n_limbs > ctx->nq || batch < 0)
+        return 0;
+    if ((op == FHE_OP_RESCALE || op == FHE_OP_HMULT) && n_limbs < 2) return 0;
+    return scratch_limbs(ctx, op, n_limbs) * ((size_t)batch << logN) * 4;
+}
+
+int fhe_keyswitch(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const uint32_t* d2,
+                  const uint32_t* evk, uint32_t* ks_out, void* scratch, size_t scratch_bytes, void* stream) {
+    int rc = check_ckks(ctx, logN, n_limbs, batch, 1);
+    if (rc || batch == 0) return rc;
+    if ((rc = check_ptrs({d2, evk, ks_out, scratch}))) return rc;
+    if (scratch_bytes < fhe_scratch_bytes(ctx, FHE_OP_KEYSWITCH, logN, n_limbs, batch))
+        return set_error(FHE_ENOMEM, "scratch too small");
+    return keyswitch_impl(ctx, logN, n_limbs, batch, d2, evk, ks_out, 0, (uint32_t*)scratch, false,
+                          (cudaStream_t)stream);
+}
+
+int fhe_hmult_relin(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const uint32_t* ct_a,
+                    const uint32_t* ct_b, const uint32_t* evk, uint32_t* out, void* scratch,
+                    size_t scratch_bytes, void* stream) {
+    int rc = check_ckks(ctx, logN, n_limbs, batch, 1);
+    if (rc || batch == 0) return rc;
+    if ((rc = check_ptrs({ct_a, ct_b, evk, out, scratch}))) return rc;
+    if (scratch_bytes < fhe_scratch_bytes(ctx, FHE_OP_HMULT_RELIN, logN, n_limbs, batch))
+        return set_error(FHE_ENOMEM, "scratch too small");
+    return hmult_relin_impl(ctx, logN, n_limbs, batch, ct_a, ct_b, evk, out, (uint32_t*)scratch,
+                            (cudaStream_t)stream);
+}
+
+int fhe_rescale(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const uint32_t* ct_in,
+                uint32_t* ct_out, void* scratch, size_t scratch_bytes, void* stream) {
+    int rc = check_ckks(ctx, logN, n_limbs, batch, 2);
+    if (rc || batch == 0) return rc;
+    if ((rc = check_ptrs({ct_in, ct_out, scratch}))) return rc;
+    if (scratch_bytes < fhe_scratch_bytes(ctx, FHE_OP_RESCALE, logN, n_limbs, batch))
+        return set_error(FHE_ENOMEM, "scratch too small");
+    return rescale_impl(ctx, logN, n_limbs, batch, ct_in, ct_out, (uint32_t*)scratch, (cudaStream_t)stream);
+}
+
+int fhe_hmult(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const uint32_t* ct_a,
+              const uint32_t* ct_b, const uint32_t* evk, uint32_t* ct_out, void* scratch,
+              size_t scratch_bytes, void* stream) {
+    int rc = check_ckks(ctx, logN, n_limbs, batch, 2);
+    if (rc || batch == 0) return rc;
+    if ((rc = check_ptrs({ct_a, ct_b, evk, ct_out, scratch}))) return rc;
+    if (scratch_bytes < fhe_scratch_bytes(ctx, FHE_OP_HMULT, logN, n_limbs, batch))
+        return set_error(FHE_ENOMEM, "scratch too small");
+    const size_t limb = (size_t)batch << logN;
+    uint32_t* relin = (uint32_t*)scratch;
+    uint32_t* rest = relin + 2 * (size_t)n_limbs * limb;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = hmult_relin_impl(ctx, logN, n_limbs, batch, ct_a, ct_b, evk, relin, rest, st))) return rc;
+    return rescale_impl(ctx, logN, n_limbs, batch, relin, ct_out, rest, st);
+}
+
+}  // extern "C"

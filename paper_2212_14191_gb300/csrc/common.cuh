@@ -1,0 +1,167 @@
+// Internal declarations shared by the libfhe translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fhe.h"
+
+namespace fhe {
+
+// ---------------------------------------------------------------- errors
+
+int set_error(int code, const std::string& msg);
+int cuda_error(cudaError_t e, const char* where);
+
+#define FHE_CUDA_TRY(expr)                                  \
+    do {                                                    \
+        cudaError_t _e = (expr);                            \
+        if (_e != cudaSuccess) return cuda_error(_e, #expr); \
+    } while (0)
+
+#define FHE_CHECK(cond, msg)                                \
+    do {                                                    \
+        if (!(cond)) return set_error(FHE_EINVAL, (msg));   \
+    } while (0)
+
+// ---------------------------------------------------------------- host modular arithmetic
+
+static inline uint32_t mulmod_h(uint32_t a, uint32_t b, uint32_t q) {
+    return (uint32_t)((uint64_t)a * b % q);
+}
+uint32_t powmod_h(uint32_t b, uint64_t e, uint32_t q);
+static inline uint32_t invmod_h(uint32_t a, uint32_t q) { return powmod_h(a, (uint64_t)q - 2, q); }
+// Shoup's precomputed quotient floor(w * 2^32 / q) for multiplications by the constant w < q.
+static inline uint32_t shoup_h(uint32_t w, uint32_t q) {
+    return (uint32_t)(((uint64_t)w << 32) / q);
+}
+bool is_prime_u32(uint32_t n);
+uint32_t root_2n(uint32_t q, uint32_t logN);  // primitive 2N-th root from the smallest non-residue
+
+// ---------------------------------------------------------------- context
+
+// Plain-path NTT tables for one ring degree N = 2^logN (device memory).
+struct NttTables {
+    uint2* fwd = nullptr;   // [nmod][N]  (psi^bitrev(i), shoup)
+    uint2* inv = nullptr;   // [nmod][N]  (psi^-bitrev(i), shoup)
+    uint2* fwdC = nullptr;  // [nmod][C][31][T] last-round twiddles, per-thread order
+    uint2* invC = nullptr;
+    uint2* ninv = nullptr;  // [nmod] (N^-1 mod q, shoup)
+};
+
+// Tensor-core path tables for one ring degree (device memory); see ntt_tc.cu.
+struct TcTables {
+    void* w1 = nullptr;     // per modulus: 8-bit digit planes of the first-pass matrices
+    void* w3 = nullptr;     // per modulus: 8-bit digit planes of the second-pass matrices
+    uint2* tw2 = nullptr;   // [nmod][N] twiddle (psi^((2k1+1) n2), shoup), k1-major
+    uint2* tw2i = nullptr;  // inverse twiddles with N^-1 folded in
+    size_t w_stride = 0;    // bytes per modulus in w1/w3
+    int n1 = 0, n2 = 0;
+    bool built = false;
+};
+
+// Basis-conversion constants (Conv of Sec. IV-A) for one source basis.
+struct ConvTable {
+    // src: hat_inv[i] = [(B/b_i)^-1]_{b_i} with Shoup quotient; dst: hat_mod[i][t] = [B/b_i]_t
+    uint2* hat_inv = nullptr;   // [nsrc]
+    uint32_t* hat_mod = nullptr; // [nsrc][nmod]  indexed by destination modulus index
+    std::vector<uint2> hat_inv_h; // host copy of hat_inv (passed to kernels by value)
+    int nsrc = 0;
+};
+
+}  // namespace fhe
+
+struct fhe_ctx {
+    uint32_t logN_max = 0;
+    int nq = 0, np = 0, alpha = 0, default_path = FHE_NTT_U32;
+    int dnum = 0;
+    std::vector<uint32_t> mods;  // q_0.., p_0..
+    fhe::NttTables ntt[FHE_LOGN_MAX + 1];
+    fhe::TcTables tc[FHE_LOGN_MAX + 1];
+    // conv tables: modup[j][e] for slice j ending (exclusive) at limb e; moddown from P
+    std::vector<std::vector<fhe::ConvTable>> modup;
+    fhe::ConvTable moddown;
+    uint2* p_inv = nullptr;        // [nq]  ([P^-1]_{q_i}, shoup)
+    uint2* ql_inv = nullptr;       // [nq][nq]  row l: ([q_l^-1]_{q_i}, shoup)
+    std::vector<void*> allocations;
+    int device = 0;
+    int num_sms = 0;
+};
+
+namespace fhe {
+
+// Per-limb modulus mapping passed by value to kernels.
+// Up to 128 limbs per launch (two ciphertext components of 64 limbs each).
+constexpr int kMaxLimbs = 2 * FHE_MAX_MODULI;
+struct LimbMap {
+    uint32_t q[kMaxLimbs];
+    uint8_t mod[kMaxLimbs];
+};
+
+// Plain-path batched NTT over `n_limbs` limbs whose moduli are map.mod[l].
+int ntt_u32(const fhe_ctx* ctx, uint32_t logN, bool inverse, uint32_t* d, int n_limbs,
+            int batch, const LimbMap& map, cudaStream_t stream);
+// Tensor-core path.
+int ntt_tc(const fhe_ctx* ctx, uint32_t logN, bool inverse, uint32_t* d, int n_limbs,
+           int batch, const LimbMap& map, cudaStream_t stream);
+int build_tc_tables(fhe_ctx* ctx, uint32_t logN);
+int build_ntt_tables(fhe_ctx* ctx, uint32_t logN);
+
+// Dispatch on path.
+int ntt_any(const fhe_ctx* ctx, int path, uint32_t logN, bool inverse, uint32_t* d, int n_limbs,
+            int batch, const LimbMap& map, cudaStream_t stream);
+
+LimbMap contiguous_map(const fhe_ctx* ctx, int first, int n);
+
+template <typename T>
+int dev_alloc(fhe_ctx* ctx, T** p, size_t count) {
+    void* v = nullptr;
+    cudaError_t e = cudaMalloc(&v, count * sizeof(T) + 16);
+    if (e != cudaSuccess) {
+        set_error(FHE_ENOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+        return FHE_ENOMEM;
+    }
+    ctx->allocations.push_back(v);
+    *p = (T*)v;
+    return FHE_OK;
+}
+
+template <typename T>
+int dev_upload(fhe_ctx* ctx, T** p, const std::vector<T>& h) {
+    int rc = dev_alloc(ctx, p, h.size());
+    if (rc) return rc;
+    FHE_CUDA_TRY(cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return FHE_OK;
+}
+
+// ---------------------------------------------------------------- device helpers
+
+// Shoup multiplication by a constant, lazy: for any x < 2^32 returns x*w mod q in [0, 2q).
+__device__ __forceinline__ uint32_t mul_shoup_lazy(uint32_t x, uint32_t w, uint32_t wq, uint32_t q) {
+    uint32_t qt = __umulhi(x, wq);
+    return x * w - qt * q;
+}
+// [0, 2m) -> [0, m) for m = q or 2q; relies on unsigned wrap-around.
+__device__ __forceinline__ uint32_t csub(uint32_t x, uint32_t m) { return min(x, x - m); }
+
+__device__ __forceinline__ uint32_t mul_shoup(uint32_t x, uint32_t w, uint32_t wq, uint32_t q) {
+    return csub(mul_shoup_lazy(x, w, wq, q), q);
+}
+
+// 64-bit Barrett: x mod q for any x < 2^64, with mu = floor(2^64 / q) (q < 2^31).
+__device__ __forceinline__ uint32_t reduce_u64(uint64_t x, uint64_t mu, uint32_t q) {
+    uint64_t qt = __umul64hi(x, mu);
+    uint64_t r = x - qt * (uint64_t)q;  // in [0, 3q)
+    uint32_t r32 = (uint32_t)r;
+    r32 = csub(r32, 2 * q);
+    return csub(r32, q);
+}
+
+__device__ __forceinline__ uint32_t mulmod(uint32_t a, uint32_t b, uint32_t q, uint64_t mu) {
+    return reduce_u64((uint64_t)a * b, mu, q);
+}
+
+}  // namespace fhe

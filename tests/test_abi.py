@@ -1,0 +1,60 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every function that
+include/fhe.h declares, validates arguments before touching the GPU, and its own
+prime generator agrees with the oracle's (two independent implementations)."""
+import ctypes
+
+import pytest
+
+from oracle import params as P
+
+
+@pytest.fixture(scope="module")
+def fhe():
+    from paper_2212_14191_gb300 import build
+    build.build()
+    from paper_2212_14191_gb300 import fhe as f
+    return f
+
+
+def test_exports_every_declared_symbol(fhe):
+    names = fhe.declared_functions()
+    assert len(names) >= 11
+    lib = ctypes.CDLL(fhe.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(fhe._SIGS) == set(names)
+
+
+def test_gen_primes_matches_oracle(fhe):
+    qs, ps = P.default_moduli(44, 8)
+    assert fhe.fhe_gen_primes(16, 30, 52) == ps + qs
+    for logn in (12, 14):
+        assert fhe.fhe_gen_primes(logn, 30, 5) == P.ntt_primes(5, logn_max=logn)
+
+
+def test_argument_validation_without_gpu(fhe):
+    with pytest.raises(fhe.FheError) as e:
+        fhe.fhe_gen_primes(9, 30, 1)
+    assert e.value.code == fhe.FHE_EINVAL
+    with pytest.raises(fhe.FheError):
+        fhe.fhe_gen_primes(16, 19, 1)
+    with pytest.raises(fhe.FheError) as e:
+        fhe.fhe_ntt_fwd(None, 0, 12, 16, 0, 1, 1, 0)
+    assert e.value.code == fhe.FHE_EINVAL and "ctx" in str(e.value)
+    with pytest.raises(fhe.FheError):
+        fhe.fhe_hmult(None, 12, 2, 1, 16, 16, 16, 16, 16, 0, 0)
+    assert fhe.fhe_scratch_bytes(None, fhe.FHE_OP_HMULT, 12, 2, 1) == 0
+    # bad moduli are rejected before any device allocation
+    composite = ((1 << 30) - 1) // (1 << 17) * (1 << 17) + 1   # above the largest such prime
+    assert composite > P.ntt_primes(1)[0]
+    q0 = P.ntt_primes(1)[0]
+    for q, p in (([17], []), ([(1 << 30) + 1], []), ([composite], []), ([q0, q0], [])):
+        with pytest.raises(fhe.FheError) as e:
+            fhe.fhe_ctx_create(16, q, p, 8)
+        assert e.value.code == fhe.FHE_EINVAL
+    qs, ps = P.default_moduli(16, 1)
+    with pytest.raises(fhe.FheError) as e:   # P = p_0 alone is smaller than a slice of 8 primes
+        fhe.fhe_ctx_create(16, qs, ps, 8)
+    assert "P" in str(e.value)
+    code, msg = fhe.last_error()
+    assert code == fhe.FHE_EINVAL and msg

@@ -1,0 +1,146 @@
+"""GPU parity of the HMULT pipeline (tensor product, key switching, rescale) against
+the CPU oracle: bit-exact on seeded inputs, plus CKKS decryption of the GPU result."""
+import numpy as np
+import pytest
+
+from oracle import ckks as C
+from oracle import params as P
+from paper_2212_14191_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+U64 = np.uint64
+
+
+@pytest.fixture(scope="module")
+def fhe():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2212_14191_gb300 import fhe as f
+    return f
+
+
+def make_key(prm, seed, h=64):
+    s = I.ternary_secret(seed, prm.N, hamming_weight=h)
+    L = len(prm.qs)
+    arand = I.uniform_residues(seed + 1, prm.qs + prm.ps, prm.dnum(L), prm.N, dtype=np.uint64).transpose(1, 0, 2)
+    evk = C.keygen_evk(prm, s, arand, I.gaussian_error(seed + 2, (prm.dnum(L), prm.N)))
+    return s, evk
+
+
+def encrypt_pair(prm, nl, s, seed, delta=2.0 ** 30):
+    N = prm.N
+    z = I.uniform_reals(seed, N // 2)
+    m = C.encode(z, N, delta)
+    a = I.uniform_residues(seed + 1, prm.qs[:nl], 1, N, dtype=np.uint64)[:, 0]
+    return z, C.encrypt(prm, nl, m, s, a, I.gaussian_error(seed + 2, N))
+
+
+@pytest.fixture(scope="module")
+def small(fhe):
+    logn = 11
+    qs, ps = P.default_moduli(12, 4)
+    prm = C.Params(1 << logn, qs, ps, alpha=4)
+    s, evk = make_key(prm, 5)
+    ctx = fhe.Context(logn, qs, ps, alpha=4)
+    yield logn, prm, s, evk, ctx
+    ctx.close()
+
+
+def batch_cts(prm, nl, batch, seed):
+    """(2, nl, batch, N) uniform ciphertext residues (uint32)."""
+    x = I.uniform_residues(seed, prm.qs[:nl], 2 * batch, prm.N)
+    return x.reshape(nl, 2, batch, prm.N).transpose(1, 0, 2, 3).copy()
+
+
+@pytest.mark.parametrize("nl", [1, 2, 4, 5, 12])
+def test_keyswitch_bitexact(fhe, small, nl):
+    import torch
+    logn, prm, s, evk, ctx = small
+    d2 = I.uniform_residues(20 + nl, prm.qs[:nl], 3, prm.N)
+    out = ctx.keyswitch(fhe.to_device(d2), fhe.to_device(evk.astype(np.uint32)), logn)
+    torch.cuda.synchronize()
+    got = fhe.to_host(out)
+    for b in range(3):
+        k0, k1 = C.keyswitch(prm, nl, d2[:, b].astype(U64), evk)
+        assert (got[0, :, b] == k0).all() and (got[1, :, b] == k1).all(), b
+
+
+@pytest.mark.parametrize("nl", [2, 3, 7, 12])
+def test_rescale_bitexact(fhe, small, nl):
+    import torch
+    logn, prm, s, evk, ctx = small
+    ct = batch_cts(prm, nl, 3, 40 + nl)
+    out = ctx.rescale(fhe.to_device(ct), logn)
+    torch.cuda.synchronize()
+    got = fhe.to_host(out)
+    for b in range(3):
+        assert (got[:, :, b] == C.rescale(prm, ct[:, :, b].astype(U64))).all(), b
+
+
+@pytest.mark.parametrize("nl", [2, 5, 9, 12])
+def test_hmult_bitexact(fhe, small, nl):
+    import torch
+    logn, prm, s, evk, ctx = small
+    a, b = batch_cts(prm, nl, 3, 60 + nl), batch_cts(prm, nl, 3, 70 + nl)
+    dev_evk = fhe.to_device(evk.astype(np.uint32))
+    da, db = fhe.to_device(a), fhe.to_device(b)
+    relin = ctx.hmult_relin(da, db, dev_evk, logn)
+    out = ctx.hmult(da, db, dev_evk, logn)
+    torch.cuda.synchronize()
+    got_r, got = fhe.to_host(relin), fhe.to_host(out)
+    for k in range(3):
+        r = C.hmult_relin(prm, nl, a[:, :, k].astype(U64), b[:, :, k].astype(U64), evk)
+        assert (got_r[:, :, k] == r).all(), k
+        assert (got[:, :, k] == C.rescale(prm, r)).all(), k
+
+
+def test_hmult_decrypts(fhe, small):
+    import torch
+    logn, prm, s, evk, ctx = small
+    nl = 9
+    za, ca = encrypt_pair(prm, nl, s, 200)
+    zb, cb = encrypt_pair(prm, nl, s, 300)
+    out = ctx.hmult(fhe.to_device(ca[:, :, None, :].astype(np.uint32)),
+                    fhe.to_device(cb[:, :, None, :].astype(np.uint32)),
+                    fhe.to_device(evk.astype(np.uint32)), logn)
+    torch.cuda.synchronize()
+    res = fhe.to_host(out)[:, :, 0, :].astype(U64)
+    scale = 2.0 ** 60 / prm.qs[nl - 1]
+    dec = C.decode(np.array(C.decrypt_coeffs(prm, res, s), dtype=float), scale)
+    ref = za * zb
+    assert np.abs(dec - ref).max() / np.abs(ref).max() < 1e-5
+
+
+def test_hmult_full_size_config(fhe):
+    """N = 2^16, 24 ciphertext limbs + 8 special primes, dnum = 3 (alpha = 8), 128 pairs.
+
+    Two pairs (b = 0 and b = 127) are genuine encryptions under a sparse ternary secret
+    (h = 64); the rest are uniform. The whole batch goes through one fhe_hmult call; the two
+    genuine pairs are compared with the oracle bit-exactly and decrypted (error <= 1e-5).
+    """
+    import torch
+    logn, N, nl, batch = 16, 1 << 16, 24, 128
+    qs, ps = P.default_moduli(24, 8)
+    prm = C.Params(N, qs, ps, alpha=8)
+    s, evk = make_key(prm, 1000)
+    A = batch_cts(prm, nl, batch, 11)
+    B = batch_cts(prm, nl, batch, 12)
+    zs = []
+    for k, b in enumerate((0, batch - 1)):
+        za, ca = encrypt_pair(prm, nl, s, 400 + 10 * k)
+        zb, cb = encrypt_pair(prm, nl, s, 500 + 10 * k)
+        A[:, :, b] = ca
+        B[:, :, b] = cb
+        zs.append(za * zb)
+    ctx = fhe.Context(16, qs, ps, alpha=8)
+    out = ctx.hmult(fhe.to_device(A), fhe.to_device(B), fhe.to_device(evk.astype(np.uint32)), logn)
+    torch.cuda.synchronize()
+    got = fhe.to_host(out)
+    ctx.close()
+    scale = 2.0 ** 60 / qs[nl - 1]
+    for k, b in enumerate((0, batch - 1)):
+        want = C.hmult(prm, nl, A[:, :, b].astype(U64), B[:, :, b].astype(U64), evk)
+        assert (got[:, :, b] == want).all(), b
+        dec = C.decode(np.array(C.decrypt_coeffs(prm, got[:, :, b].astype(U64), s), dtype=float), scale)
+        assert np.abs(dec - zs[k]).max() / np.abs(zs[k]).max() < 1e-5

@@ -1,0 +1,146 @@
+"""GPU parity of the batched negacyclic NTT/INTT against the CPU oracle (bit-exact)."""
+import numpy as np
+import pytest
+
+from oracle import ntt as ON
+from oracle import params as P
+from paper_2212_14191_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+QS, PS = P.default_moduli(44, 8)
+MODS = QS + PS
+PATHS = ["u32"]
+
+
+@pytest.fixture(scope="module")
+def fhe():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2212_14191_gb300 import fhe as f
+    return f
+
+
+@pytest.fixture(scope="module")
+def ctx(fhe):
+    c = fhe.Context(16, QS, PS, alpha=8)
+    yield c
+    c.close()
+
+
+def _path(fhe, name):
+    return {"u32": fhe.FHE_NTT_U32, "tc": fhe.FHE_NTT_TC}[name]
+
+
+def psis(mods, n):
+    return [P.psi(m, n) for m in mods]
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("logn", [10, 11, 12, 13, 14, 15, 16])
+def test_fwd_inv_match_oracle(fhe, ctx, logn, path):
+    import torch
+    n = 1 << logn
+    first, nl, batch = 42, 4, 3          # limbs q_42, q_43, p_0, p_1: crosses the q/p boundary
+    mods = MODS[first:first + nl]
+    x = I.uniform_residues(logn, mods, batch, n)
+    d = fhe.to_device(x)
+    ctx.ntt_fwd(d, logn, first_limb=first, path=_path(fhe, path))
+    torch.cuda.synchronize()
+    want, _ = ON.ntt_batch(x, mods, psis(mods, n))
+    assert (fhe.to_host(d) == want).all()
+    ctx.ntt_inv(d, logn, first_limb=first, path=_path(fhe, path))
+    assert (fhe.to_host(d) == x).all()
+    # inverse on fresh random input against the oracle's inverse
+    y = I.uniform_residues(100 + logn, mods, batch, n)
+    e = fhe.to_device(y)
+    ctx.ntt_inv(e, logn, first_limb=first, path=_path(fhe, path))
+    want, _ = ON.ntt_batch(y, mods, psis(mods, n), inverse=True)
+    assert (fhe.to_host(e) == want).all()
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_plain_ntt_config_n4096(fhe, path):
+    """N = 2^12, one prime q_0, 16 polynomials uniform in [0, q), seed 0."""
+    import torch
+    logn, n = 12, 1 << 12
+    q = QS[0]
+    c = fhe.Context(12, [q])
+    x = I.uniform_residues(0, [q], 16, n)
+    d = fhe.to_device(x)
+    c.ntt_fwd(d, logn, path=_path(fhe, path))
+    torch.cuda.synchronize()
+    A = fhe.to_host(d)
+    psi = P.psi(q, n)
+    want, _ = ON.ntt_batch(x, [q], [psi])
+    assert (A == want).all()
+    assert (A[0, 0] == ON.ntt_brute(x[0, 0], q, psi)).all()
+    # convolution theorem: INTT(NTT(a) . NTT(b)) equals the schoolbook product mod X^N + 1
+    prod = (A[0, 0::2].astype(np.uint64) * A[0, 1::2].astype(np.uint64)) % q
+    p = fhe.to_device(prod.astype(np.uint32)[None])
+    c.ntt_inv(p, logn, path=_path(fhe, path))
+    got = fhe.to_host(p)[0]
+    for i in range(8):
+        assert (got[i] == ON.negacyclic_mul(x[0, 2 * i], x[0, 2 * i + 1], q)).all()
+    c.close()
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_full_size_ckks_batch(fhe, ctx, path):
+    """N = 2^16, 44 limbs q_0..q_43, 64 polynomials (704 MiB), one call per direction.
+
+    Sampled rows are checked against the oracle; the round trip is checked in full.
+    """
+    import torch
+    logn, n, nl, batch = 16, 1 << 16, 44, 64
+    x = I.uniform_residues(7, QS, batch, n)
+    d = fhe.to_device(x)
+    ctx.ntt_fwd(d, logn, path=_path(fhe, path))
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(1)
+    rows = [(l, b) for l in range(nl) for b in (0, batch - 1)] + \
+           [(int(l), int(b)) for l, b in zip(rng.integers(0, nl, 8), rng.integers(0, batch, 8))]
+    got = fhe.to_host(d)
+    for l, b in rows:
+        assert (got[l, b] == ON.ntt(x[l, b], QS[l], P.psi(QS[l], n))).all(), (l, b)
+    ctx.ntt_inv(d, logn, path=_path(fhe, path))
+    xd = fhe.to_device(x)
+    assert torch.equal(d, xd)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_edge_values(fhe, ctx, path):
+    import torch
+    for logn in (10, 16):
+        n = 1 << logn
+        mods = QS[:2]
+        for fill in ("zero", "max"):
+            x = np.zeros((2, 2, n), dtype=np.uint32)
+            if fill == "max":
+                for l, m in enumerate(mods):
+                    x[l] = m - 1
+            d = fhe.to_device(x)
+            ctx.ntt_fwd(d, logn, path=_path(fhe, path))
+            torch.cuda.synchronize()
+            want, _ = ON.ntt_batch(x, mods, psis(mods, n))
+            assert (fhe.to_host(d) == want).all()
+            ctx.ntt_inv(d, logn, path=_path(fhe, path))
+            assert (fhe.to_host(d) == x).all()
+
+
+def test_batch_zero_and_bad_args(fhe, ctx):
+    import torch
+    d = torch.zeros((1, 1, 1024), dtype=torch.int32, device="cuda")
+    fhe.fhe_ntt_fwd(ctx.handle, 0, 10, d.data_ptr(), 0, 1, 0, 0)      # batch 0: no-op
+    assert int(d.abs().sum()) == 0
+    for args in ((0, 9, d.data_ptr(), 0, 1, 1), (0, 17, d.data_ptr(), 0, 1, 1),
+                 (0, 10, d.data_ptr() + 4, 0, 1, 1), (0, 10, d.data_ptr(), 50, 3, 1),
+                 (7, 10, d.data_ptr(), 0, 1, 1), (0, 10, 0, 0, 1, 1)):
+        with pytest.raises(fhe.FheError) as e:
+            fhe.fhe_ntt_fwd(ctx.handle, *args, 0)
+        assert e.value.code == fhe.FHE_EINVAL
+    small = fhe.Context(12, QS[:1])
+    with pytest.raises(fhe.FheError):
+        small.ntt_fwd(torch.zeros((1, 1, 1 << 13), dtype=torch.int32, device="cuda"), 13)
+    small.close()
