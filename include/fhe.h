@@ -158,6 +158,26 @@ int fhe_hmult(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const u
               size_t scratch_bytes, void* stream);
 
 /*
+ * fhe_rescale_noalloc -- the same RESCALE as fhe_rescale, for callers that cannot allocate
+ * device memory: a serving loop that must not stall the device (cudaMalloc/cudaFree may
+ * synchronise it), code whose device memory is all owned by another allocator under a fixed
+ * budget, or a plugin host that forbids device allocations. The paper has no counterpart; it
+ * is an interface convenience of this library.
+ *   Scratch comes from a fixed array of FHE_RESCALE_NOALLOC_MAX_BYTES bytes compiled into the
+ *   library's device image; every GPU that loads the library holds it until process exit.
+ *   The call allocates nothing. A size whose scratch (fhe_scratch_bytes(ctx, FHE_OP_RESCALE,
+ *   ...)) exceeds the array is rejected with FHE_ENOMEM.
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ *   with that device current) and caches it; make that first call before any stream capture.
+ *   All calls share the one array and it keeps the last call's contents: calls whose GPU work
+ *   overlaps (other streams, other threads) race on it, so serialise them on one stream.
+ * Arguments and layouts as fhe_rescale.
+ */
+#define FHE_RESCALE_NOALLOC_MAX_BYTES (32u << 20)
+int fhe_rescale_noalloc(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch,
+                        const uint32_t* ct_in, uint32_t* ct_out, void* stream);
+
+/*
  * fhe_last_error -- copy the calling thread's last error message (NUL-terminated, truncated
  * to n bytes) into buf; returns the status code of that failure (FHE_OK if none).
  */

@@ -19,6 +19,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "fhe.h")
 FHE_OK, FHE_EINVAL, FHE_ENOMEM, FHE_ECUDA, FHE_ETIMEOUT = 0, 1, 2, 3, 4
 FHE_NTT_DEFAULT, FHE_NTT_U32, FHE_NTT_TC = 0, 1, 2
 FHE_OP_HMULT, FHE_OP_KEYSWITCH, FHE_OP_RESCALE, FHE_OP_HMULT_RELIN = 1, 2, 3, 4
+FHE_RESCALE_NOALLOC_MAX_BYTES = 32 << 20
 
 if not os.path.exists(LIB_PATH):
     raise ImportError("libfhe.so is not built (run `python -c 'import __graft_entry__ as g; g.build()'`)")
@@ -42,6 +43,7 @@ _SIGS = {
     "fhe_hmult_relin": (_i, [_vp, _u32, _i, _i, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "fhe_rescale": (_i, [_vp, _u32, _i, _i, _vp, _vp, _vp, _sz, _vp]),
     "fhe_hmult": (_i, [_vp, _u32, _i, _i, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "fhe_rescale_noalloc": (_i, [_vp, _u32, _i, _i, _vp, _vp, _vp]),
     "fhe_last_error": (_i, [ctypes.c_char_p, _sz]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -119,6 +121,10 @@ def fhe_hmult_relin(ctx, logN, n_limbs, batch, a, b, evk, out, scratch, scratch_
 
 def fhe_rescale(ctx, logN, n_limbs, batch, ct_in, ct_out, scratch, scratch_bytes, stream=0):
     return _check(_lib.fhe_rescale(ctx, logN, n_limbs, batch, ct_in, ct_out, scratch, scratch_bytes, stream))
+
+
+def fhe_rescale_noalloc(ctx, logN, n_limbs, batch, ct_in, ct_out, stream=0):
+    return _check(_lib.fhe_rescale_noalloc(ctx, logN, n_limbs, batch, ct_in, ct_out, stream))
 
 
 def fhe_hmult(ctx, logN, n_limbs, batch, a, b, evk, out, scratch, scratch_bytes, stream=0):
