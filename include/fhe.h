@@ -100,6 +100,25 @@ int fhe_ntt_fwd(const fhe_ctx* ctx, int path, uint32_t logN, uint32_t* d, int fi
 int fhe_ntt_inv(const fhe_ctx* ctx, int path, uint32_t logN, uint32_t* d, int first_limb,
                 int n_limbs, int batch, void* stream);
 
+/*
+ * Plain-path kernel shapes (an interface of this library; the paper picks batch sizes per
+ * kernel from the hardware in its API layer, Sec. IV-E, but gives no tuning procedure).
+ * fhe_ntt_variant_count -- number of shapes available for logN (>= 1), or -1 on bad input.
+ * fhe_ntt_get_variant / fhe_ntt_set_variant -- the shape used for logN by every plain-path
+ *   transform of this context (HMULT included). Setting it must not race with calls that use
+ *   the context; it changes only speed, never results.
+ * fhe_autotune_ntt -- times every shape on a forward+inverse round trip over `d`
+ *   (device (n_limbs, batch, N), limbs use moduli 0..n_limbs-1; restored bit-exactly on
+ *   return), keeps the fastest, and writes the per-shape milliseconds to host array
+ *   ms_out[fhe_ntt_variant_count] (nullable; -1 for shapes that do not apply). Synchronises
+ *   `stream`.
+ */
+int fhe_ntt_variant_count(const fhe_ctx* ctx, uint32_t logN);
+int fhe_ntt_get_variant(const fhe_ctx* ctx, uint32_t logN);
+int fhe_ntt_set_variant(fhe_ctx* ctx, uint32_t logN, int variant);
+int fhe_autotune_ntt(fhe_ctx* ctx, uint32_t logN, uint32_t* d, int n_limbs, int batch, int reps,
+                     float* ms_out, void* stream);
+
 /* Operations for fhe_scratch_bytes. */
 #define FHE_OP_HMULT 1
 #define FHE_OP_KEYSWITCH 2
@@ -176,6 +195,13 @@ int fhe_hmult(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const u
 #define FHE_RESCALE_NOALLOC_MAX_BYTES (32u << 20)
 int fhe_rescale_noalloc(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch,
                         const uint32_t* ct_in, uint32_t* ct_out, void* stream);
+
+/*
+ * fhe_device_status -- reads (and with clear != 0 resets) the context's device error word,
+ * which kernels set when a bounded device-side wait expires (their work is then incomplete).
+ * Returns FHE_OK, or FHE_ETIMEOUT. Synchronous: waits for the device copy of the word.
+ */
+int fhe_device_status(const fhe_ctx* ctx, int clear);
 
 /*
  * fhe_last_error -- copy the calling thread's last error message (NUL-terminated, truncated

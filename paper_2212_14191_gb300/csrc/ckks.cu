@@ -125,49 +125,46 @@ __global__ void __launch_bounds__(256) k_conv(const ConvArgs a) {
     }
 }
 
-// ---- KS-4: inner product with the evaluation key (Hada-Mult + Ele-Add)
+// ---- KS-4: inner product with the evaluation key (Hada-Mult + Ele-Add), all slices at once:
+//   ks_c[t] = sum_j d~_j[t] * evk_{j,c}[t],  d~_j[t] = d2[t] on slice j's own limbs, else the
+//   NTT of slice j's ModUp output. One pass reads every slice and writes ks0, ks1 once.
 struct IpArgs {
     const uint32_t* d2;   // (nl, B, N) NTT domain
-    const uint32_t* tmp;  // (nl - (hi - lo) + K, B, N) NTT domain: q limbs outside [lo,hi), then P
-    const uint32_t* evk;  // (dnum, 2, nmod, N)
-    uint32_t* ks;         // (2, nl + K, B, N)
-    int nl, lo, hi, j, nq, nmod, first;
+    const uint32_t* tmp;  // (dnum, ext, B, N): slice j's converted limbs at j*ext (q limbs outside the slice, then P)
+    const uint32_t* evk;  // (dnum_ctx, 2, nmod, N)
+    uint32_t* ks;         // (2, ext, B, N)
+    int nl, alpha, dnum, ext, nq, nmod;
     size_t L4, N4;        // residues per limb / 4, N / 4
-    ModVec m;             // per extended limb t < nl + K
+    ModVec m;             // per extended limb t < ext
 };
 
 __global__ void k_inner_product(const IpArgs a) {
     const int t = blockIdx.y;
-    const int ext = gridDim.y;
     const uint32_t q = a.m.q[t];
     const uint64_t mu = a.m.mu[t];
-    const uint32_t* src = (t >= a.lo && t < a.hi) ? a.d2 + (size_t)t * a.L4 * 4
-                                                   : a.tmp + (size_t)(t < a.lo ? t : t - (a.hi - a.lo)) * a.L4 * 4;
     const int mod = t < a.nl ? t : a.nq + (t - a.nl);
-    const uint32_t* e0 = a.evk + ((size_t)(a.j * 2 + 0) * a.nmod + mod) * a.N4 * 4;
-    const uint32_t* e1 = a.evk + ((size_t)(a.j * 2 + 1) * a.nmod + mod) * a.N4 * 4;
-    uint32_t* k0 = a.ks + (size_t)t * a.L4 * 4;
-    uint32_t* k1 = a.ks + (size_t)(ext + t) * a.L4 * 4;
+    const size_t limb = a.L4 * 4;
+    uint32_t* k0 = a.ks + (size_t)t * limb;
+    uint32_t* k1 = a.ks + (size_t)(a.ext + t) * limb;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < a.L4; i += (size_t)gridDim.x * blockDim.x) {
         const size_t n4 = i % a.N4;
-        uint4 x = ld4(src, i), w0 = ld4(e0, n4), w1 = ld4(e1, n4);
-        uint4 r0, r1;
-        if (a.first) {
+        uint32_t r0[4] = {0, 0, 0, 0}, r1[4] = {0, 0, 0, 0};
+        for (int j = 0; j < a.dnum; ++j) {
+            const int lo = j * a.alpha, hi = min(a.nl, lo + a.alpha);
+            const uint32_t* src = (t >= lo && t < hi)
+                                      ? a.d2 + (size_t)t * limb
+                                      : a.tmp + ((size_t)j * a.ext + (t < lo ? t : t - (hi - lo))) * limb;
+            const uint4 x = ld4(src, i);
+            const uint4 w0 = ld4(a.evk + ((size_t)(j * 2 + 0) * a.nmod + mod) * a.N4 * 4, n4);
+            const uint4 w1 = ld4(a.evk + ((size_t)(j * 2 + 1) * a.nmod + mod) * a.N4 * 4, n4);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                set(r0, k, reduce_u64((uint64_t)get(x, k) * get(w0, k), mu, q));
-                set(r1, k, reduce_u64((uint64_t)get(x, k) * get(w1, k), mu, q));
-            }
-        } else {
-            uint4 s0 = ld4(k0, i), s1 = ld4(k1, i);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                set(r0, k, reduce_u64((uint64_t)get(x, k) * get(w0, k) + get(s0, k), mu, q));
-                set(r1, k, reduce_u64((uint64_t)get(x, k) * get(w1, k) + get(s1, k), mu, q));
+                r0[k] = reduce_u64((uint64_t)get(x, k) * get(w0, k) + r0[k], mu, q);
+                r1[k] = reduce_u64((uint64_t)get(x, k) * get(w1, k) + r1[k], mu, q);
             }
         }
-        st4(k0, i, r0);
-        st4(k1, i, r1);
+        st4(k0, i, make_uint4(r0[0], r0[1], r0[2], r0[3]));
+        st4(k1, i, make_uint4(r1[0], r1[1], r1[2], r1[3]));
     }
 }
 
@@ -262,9 +259,10 @@ struct Sizes {
     int nl, K, ext;
 };
 
-size_t ks_scratch_limbs(int nl, int K) {
-    // d2c (nl) + tmp (nl + K) + ks (2 (nl + K)) + y (2 nl)
-    return (size_t)nl + (nl + K) + 2 * (size_t)(nl + K) + 2 * (size_t)nl;
+size_t ks_scratch_limbs(int nl, int K, int alpha) {
+    // d2c (nl) + ModUp outputs (dnum slices of nl + K) + ks (2 (nl + K)) + y (2 nl)
+    const size_t dnum = (size_t)((nl + alpha - 1) / alpha);
+    return (size_t)nl + dnum * (nl + K) + 2 * (size_t)(nl + K) + 2 * (size_t)nl;
 }
 
 // Key switching of d2 (NTT form) into `out` (2, nl, B, N); accumulate != 0 adds to out.
@@ -275,9 +273,10 @@ int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const u
     const size_t N = 1ull << logN, limb = N * batch, L4 = limb / 4;
     const int K = ctx->np, ext = nl + K, alpha = ctx->alpha, nq = ctx->nq;
     const int nmod = (int)ctx->mods.size();
+    const int dnum = (nl + alpha - 1) / alpha;
     uint32_t* d2c = scratch;
-    uint32_t* tmp = d2c + (size_t)nl * limb;
-    uint32_t* ks = tmp + (size_t)ext * limb;
+    uint32_t* tmp_all = d2c + (size_t)nl * limb;
+    uint32_t* ks = tmp_all + (size_t)dnum * ext * limb;
     uint32_t* y = ks + 2 * (size_t)ext * limb;
     int rc;
     if (!d2c_ready) FHE_CUDA_TRY(cudaMemcpyAsync(d2c, d2, (size_t)nl * limb * 4, cudaMemcpyDeviceToDevice, st));
@@ -286,9 +285,9 @@ int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const u
     int ext_mod[kMaxLimbs];
     for (int t = 0; t < ext; ++t) ext_mod[t] = t < nl ? t : nq + (t - nl);
     ModVec ext_m = modvec(ctx, ext_mod, ext);
-    const int dnum = (nl + alpha - 1) / alpha;
     for (int j = 0; j < dnum; ++j) {
         const int lo = j * alpha, hi = std::min(nl, (j + 1) * alpha);
+        uint32_t* tmp = tmp_all + (size_t)j * ext * limb;
         const ConvTable& ct = ctx->modup[j][hi - lo - 1];
         // KS-2: Conv Q_j -> (Q_l \ Q_j) u P
         ConvArgs ca;
@@ -324,19 +323,20 @@ int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const u
             lm.q[t] = ctx->mods[dmod[t]];
         }
         if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, false, tmp, nd, batch, lm, st))) return rc;
-        // KS-4: inner product
+    }
+    // KS-4: inner product over all slices
+    {
         IpArgs ia;
         ia.d2 = d2;
-        ia.tmp = tmp;
+        ia.tmp = tmp_all;
         ia.evk = evk;
         ia.ks = ks;
         ia.nl = nl;
-        ia.lo = lo;
-        ia.hi = hi;
-        ia.j = j;
+        ia.alpha = alpha;
+        ia.dnum = dnum;
+        ia.ext = ext;
         ia.nq = nq;
         ia.nmod = nmod;
-        ia.first = (j == 0);
         ia.L4 = L4;
         ia.N4 = N / 4;
         ia.m = ext_m;
@@ -454,11 +454,11 @@ int check_ptrs(std::initializer_list<const void*> ps) {
 size_t scratch_limbs(const fhe_ctx* ctx, int op, int nl) {
     const int K = ctx->np;
     switch (op) {
-        case FHE_OP_KEYSWITCH: return ks_scratch_limbs(nl, K);
-        case FHE_OP_HMULT_RELIN: return (size_t)nl + ks_scratch_limbs(nl, K);
+        case FHE_OP_KEYSWITCH: return ks_scratch_limbs(nl, K, ctx->alpha);
+        case FHE_OP_HMULT_RELIN: return (size_t)nl + ks_scratch_limbs(nl, K, ctx->alpha);
         case FHE_OP_RESCALE: return rescale_scratch_limbs(nl);
         case FHE_OP_HMULT:
-            return 2 * (size_t)nl + std::max((size_t)nl + ks_scratch_limbs(nl, K), rescale_scratch_limbs(nl));
+            return 2 * (size_t)nl + std::max((size_t)nl + ks_scratch_limbs(nl, K, ctx->alpha), rescale_scratch_limbs(nl));
         default: return 0;
     }
 }

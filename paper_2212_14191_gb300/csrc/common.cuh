@@ -1,6 +1,7 @@
 // Internal declarations shared by the libfhe translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -43,22 +44,29 @@ uint32_t root_2n(uint32_t q, uint32_t logN);  // primitive 2N-th root from the s
 
 // ---------------------------------------------------------------- context
 
+// Plain-path kernel shapes per ring degree: threads per CTA T = 2^log_t and CTAs per
+// cluster C = 2^log_c with 32 * T * C = N (see ntt_u32.cu).
+constexpr int kNttVariants = 4;
+bool ntt_variant_shape(uint32_t logN, int variant, int* log_t, int* log_c);
+bool ntt_variant_push(int variant);
+
 // Plain-path NTT tables for one ring degree N = 2^logN (device memory).
 struct NttTables {
     uint2* fwd = nullptr;   // [nmod][N]  (psi^bitrev(i), shoup)
     uint2* inv = nullptr;   // [nmod][N]  (psi^-bitrev(i), shoup)
-    uint2* fwdC = nullptr;  // [nmod][C][31][T] last-round twiddles, per-thread order
-    uint2* invC = nullptr;
+    uint2* fwdC[2] = {};  // per shape: [nmod][C][31][T] last-round twiddles, per-thread order
+    uint2* invC[2] = {};
     uint2* ninv = nullptr;  // [nmod] (N^-1 mod q, shoup)
 };
 
-// Tensor-core path tables for one ring degree (device memory); see ntt_tc.cu.
+// Tensor-core path tables for one ring degree (device memory); see ntt_tc.cu. Built on the
+// first tensor-core call at that degree.
 struct TcTables {
-    void* w1 = nullptr;     // per modulus: 8-bit digit planes of the first-pass matrices
-    void* w3 = nullptr;     // per modulus: 8-bit digit planes of the second-pass matrices
-    uint2* tw2 = nullptr;   // [nmod][N] twiddle (psi^((2k1+1) n2), shoup), k1-major
-    uint2* tw2i = nullptr;  // inverse twiddles with N^-1 folded in
-    size_t w_stride = 0;    // bytes per modulus in w1/w3
+    uint16_t* mat[4] = {};     // digit planes (bf16) of W1 fwd, W3 fwd, W3 inv, W1 inv: [nmod][4][cols][4K]
+    uint2* tw_fwd = nullptr;   // [nmod][N1][N2] (psi^((2k1+1) n2), shoup)
+    uint2* tw_inv = nullptr;   // [nmod][N2][N1] (N^-1 psi^(-(2k1+1) n2), shoup)
+    CUtensorMap map_b[4];      // TMA maps over mat[kind]
+    CUtensorMap map_a[2][2];   // TMA maps over the two plane buffers, inner extent 4*N1 / 4*N2
     int n1 = 0, n2 = 0;
     bool built = false;
 };
@@ -80,6 +88,7 @@ struct fhe_ctx {
     int dnum = 0;
     std::vector<uint32_t> mods;  // q_0.., p_0..
     fhe::NttTables ntt[FHE_LOGN_MAX + 1];
+    int ntt_variant[FHE_LOGN_MAX + 1] = {};  // plain-path shape in use per logN (autotuned)
     fhe::TcTables tc[FHE_LOGN_MAX + 1];
     // conv tables: modup[j][e] for slice j ending (exclusive) at limb e; moddown from P
     std::vector<std::vector<fhe::ConvTable>> modup;
@@ -89,6 +98,8 @@ struct fhe_ctx {
     std::vector<void*> allocations;
     int device = 0;
     int num_sms = 0;
+    int* d_status = nullptr;  // device error word written by kernels (FHE_ETIMEOUT, ...)
+    void* tc_planes[2] = {};  // tensor-core path scratch: 8-bit digit planes of two operands
 };
 
 namespace fhe {

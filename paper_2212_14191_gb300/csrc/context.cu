@@ -236,9 +236,16 @@ int fhe_ctx_create(uint32_t logN_max, const uint32_t* q, int nq, const uint32_t*
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e != cudaSuccess) rc = cuda_error(e, "cudaGetDevice");
+    if (rc == FHE_OK) {
+        rc = dev_alloc(ctx, &ctx->d_status, 1);
+        if (rc == FHE_OK) {
+            cudaError_t ce = cudaMemset(ctx->d_status, 0, sizeof(int));
+            if (ce != cudaSuccess) rc = cuda_error(ce, "cudaMemset");
+        }
+    }
     for (uint32_t lg = FHE_LOGN_MIN; rc == FHE_OK && lg <= logN_max; ++lg) rc = build_ntt_tables(ctx, lg);
     if (rc == FHE_OK && np > 0) rc = build_ckks_tables(ctx);
-    if (rc == FHE_OK) {
+    if (rc == FHE_OK && default_path == FHE_NTT_TC) {
         for (uint32_t lg = FHE_LOGN_MIN; rc == FHE_OK && lg <= logN_max; ++lg) rc = build_tc_tables(ctx, lg);
     }
     if (rc != FHE_OK) {
@@ -272,6 +279,82 @@ int fhe_ntt_inv(const fhe_ctx* ctx, int path, uint32_t logN, uint32_t* d, int fi
     if (batch == 0) return FHE_OK;
     return ntt_any(ctx, path, logN, true, d, n_limbs, batch, contiguous_map(ctx, first_limb, n_limbs),
                    (cudaStream_t)stream);
+}
+
+int fhe_device_status(const fhe_ctx* ctx, int clear) {
+    FHE_CHECK(ctx != nullptr, "ctx is NULL");
+    int v = 0;
+    FHE_CUDA_TRY(cudaMemcpy(&v, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (clear && v) FHE_CUDA_TRY(cudaMemset(ctx->d_status, 0, sizeof(int)));
+    if (v == FHE_ETIMEOUT) return set_error(FHE_ETIMEOUT, "a bounded device-side wait expired");
+    if (v) return set_error(v, "device reported an error");
+    return FHE_OK;
+}
+
+int fhe_ntt_variant_count(const fhe_ctx* ctx, uint32_t logN) {
+    if (!ctx || logN < FHE_LOGN_MIN || logN > ctx->logN_max) return -1;
+    int n = 0, lt, lc;
+    for (int v = 0; v < kNttVariants; ++v)
+        if (ntt_variant_shape(logN, v, &lt, &lc)) n = v + 1;
+    return n;
+}
+
+int fhe_ntt_get_variant(const fhe_ctx* ctx, uint32_t logN) {
+    if (!ctx || logN < FHE_LOGN_MIN || logN > ctx->logN_max) return -1;
+    return ctx->ntt_variant[logN];
+}
+
+int fhe_ntt_set_variant(fhe_ctx* ctx, uint32_t logN, int variant) {
+    FHE_CHECK(ctx != nullptr, "ctx is NULL");
+    FHE_CHECK(logN >= FHE_LOGN_MIN && logN <= ctx->logN_max, "logN out of [10, logN_max]");
+    int lt, lc;
+    FHE_CHECK(ntt_variant_shape(logN, variant, &lt, &lc), "no such NTT shape for this logN");
+    ctx->ntt_variant[logN] = variant;
+    return FHE_OK;
+}
+
+int fhe_autotune_ntt(fhe_ctx* ctx, uint32_t logN, uint32_t* d, int n_limbs, int batch, int reps,
+                     float* ms_out, void* stream) {
+    int rc = check_ntt_args(ctx, FHE_NTT_U32, logN, d, 0, n_limbs, batch);
+    if (rc) return rc;
+    FHE_CHECK(batch >= 1 && reps >= 1, "batch and reps must be >= 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    const LimbMap map = contiguous_map(ctx, 0, n_limbs);
+    const int keep = ctx->ntt_variant[logN];
+    int best = keep;
+    float best_ms = 0;
+    cudaEvent_t e0, e1;
+    FHE_CUDA_TRY(cudaEventCreate(&e0));
+    FHE_CUDA_TRY(cudaEventCreate(&e1));
+    for (int v = 0; v < kNttVariants; ++v) {
+        int lt, lc;
+        if (!ntt_variant_shape(logN, v, &lt, &lc)) {
+            if (ms_out) ms_out[v] = -1.0f;
+            continue;
+        }
+        ctx->ntt_variant[logN] = v;
+        for (int r = 0; r <= reps && rc == FHE_OK; ++r) {
+            if (r == 1) cudaEventRecord(e0, st);
+            rc = ntt_u32(ctx, logN, false, d, n_limbs, batch, map, st);
+            if (rc == FHE_OK) rc = ntt_u32(ctx, logN, true, d, n_limbs, batch, map, st);
+        }
+        cudaEventRecord(e1, st);
+        cudaError_t ce = cudaEventSynchronize(e1);
+        if (rc == FHE_OK && ce != cudaSuccess) rc = cuda_error(ce, "cudaEventSynchronize");
+        if (rc != FHE_OK) break;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+        if (ms_out) ms_out[v] = ms;
+        if (v == 0 || ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->ntt_variant[logN] = (rc == FHE_OK) ? best : keep;
+    return rc;
 }
 
 }  // extern "C"

@@ -21,11 +21,10 @@
 // bit-reversed store are free of bank conflicts.
 // Arithmetic: Harvey's lazy butterflies with Shoup's precomputed-quotient multiplication;
 // forward values live in [0, 4q), inverse values in [0, 2q), q < 2^30.
-#include <cooperative_groups.h>
 
 #include "common.cuh"
+#include "ptx.cuh"
 
-namespace cg = cooperative_groups;
 
 namespace fhe {
 namespace {
@@ -37,6 +36,8 @@ struct NttArgs {
     const uint2* tw;    // [nmod][N]
     const uint2* twC;   // [nmod][C][31][T]
     const uint2* ninv;  // [nmod]
+    int* status;        // device error word (FHE_ETIMEOUT on an expired wait)
+    int contiguous;     // row order: 0 = interleaved across clusters, 1 = contiguous ranges
     LimbMap map;
 };
 
@@ -70,33 +71,77 @@ __device__ __forceinline__ void gs_bfly(uint32_t& x, uint32_t& y, uint2 w, uint3
 template <int LOG_T>
 constexpr int kMinBlocks = (1 << (14 - LOG_T)) / 32 > 0 ? (1 << (14 - LOG_T)) / 32 : 1;
 
-__device__ __forceinline__ void cluster_sync_all() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n"
-                 "barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+// Shared memory (32-bit words) of a CTA: a working buffer holding its 32 * T residues and,
+// with push exchange in a cluster, a receive buffer that peers store their outputs into.
+// It is kept this small on purpose: the rest of the SM's 256 KB L1/shared array caches
+// twiddle tables.
+template <int LOG_T, int LOG_C, bool PUSH>
+constexpr int kSmemWords = (32 << LOG_T) * ((LOG_C > 0 && PUSH) ? 2 : 1);
+
+// Swizzle of the receive buffer: forward pushes arrive at stride C words per lane.
+template <int LOG_C>
+__device__ __forceinline__ int swo(int off) {
+    return off ^ ((off >> 5) & ((1 << LOG_C) - 1));
 }
 
-template <int LOG_T, int LOG_C>
+// Rows handled by this cluster: interleaved (row = blockIdx.y + i * gridDim.y, so the
+// clusters running at one time share a limb and its twiddle tables in L2) or one contiguous
+// range (consecutive rows of a cluster share a limb, favouring L1).
+struct RowIter {
+    int row, end, step;
+};
+__device__ __forceinline__ RowIter row_iter(int rows, int contiguous) {
+    if (contiguous) {
+        const int per = (rows + gridDim.y - 1) / gridDim.y;
+        const int b = min(rows, (int)blockIdx.y * per);
+        return {b, min(rows, b + per), 1};
+    }
+    return {(int)blockIdx.y, rows, (int)gridDim.y};
+}
+
+// Ask the TMA unit to pull this CTA's share of a row into L2 ahead of its loads:
+// forward with C > 1, the slice [c*PER, (c+1)*PER) of each of the C quarters; otherwise the
+// CTA's contiguous range [c*NC, (c+1)*NC).
+template <int LOG_T, int LOG_C, bool FWD>
+__device__ __forceinline__ void prefetch_row(const uint32_t* data_row, int c) {
+    constexpr int T = 1 << LOG_T, C = 1 << LOG_C;
+    constexpr int NC = 32 * T;
+    if (FWD && C > 1) {
+        constexpr int PER = NC / C;
+#pragma unroll
+        for (int qq = 0; qq < C; ++qq) ptx::prefetch_l2(data_row + qq * NC + c * PER, PER * 4);
+    } else {
+        ptx::prefetch_l2(data_row + c * NC, NC * 4);
+    }
+}
+
+template <int LOG_T, int LOG_C, bool PUSH>
 __global__ void __launch_bounds__(1 << LOG_T, kMinBlocks<LOG_T>)
-ntt_fwd_kernel(NttArgs a) {
+ntt_fwd_kernel(const NttArgs a) {
     constexpr int T = 1 << LOG_T, C = 1 << LOG_C;
     constexpr int LOG_NC = LOG_T + 5, NC = 1 << LOG_NC;
     constexpr int N = NC * C;
     constexpr int RB = LOG_T - 5;
-    extern __shared__ uint32_t sm[];
+    extern __shared__ __align__(128) uint32_t work[];
+    const uint32_t work_s = ptx::smem_u32(work);
     const int tid = threadIdx.x;
     const int c = (C > 1) ? (int)blockIdx.x : 0;
-    cg::cluster_group cluster = cg::this_cluster();
+    const RowIter ri = row_iter(a.rows, a.contiguous);
+    if constexpr (C > 1) ptx::cluster_sync();  // every peer is resident before the first push
 
-    for (int row = blockIdx.y; row < a.rows; row += gridDim.y) {
+    for (int row = ri.row; row < ri.end; row += ri.step) {
         const int limb = row / a.batch;
         const uint32_t q = a.map.q[limb];
         const int mod = a.map.mod[limb];
         const uint2* tw = a.tw + (size_t)mod * N;
         uint32_t* data = a.data + (size_t)row * N;
+        if (tid == 0 && row + ri.step < ri.end) prefetch_row<LOG_T, LOG_C, true>(data + (size_t)ri.step * N, c);
         uint32_t v[32];
 
         if constexpr (C > 1) {
-            cluster_sync_all();  // peers resident; previous row's remote reads finished
+            // push: peers finished reading their `work` before the previous row's second
+            // barrier; pull: peers may still be reading this CTA's `work` (gather)
+            if constexpr (!PUSH) ptx::cluster_sync();
             constexpr int PER = NC / C;  // elements of each quarter handled by this CTA
 #pragma unroll
             for (int u = 0; u < PER / T; ++u) {
@@ -116,14 +161,12 @@ ntt_fwd_kernel(NttArgs a) {
                     }
                 }
 #pragma unroll
-                for (int qq = 0; qq < C; ++qq) {
-                    uint32_t* dst = cluster.map_shared_rank(sm, qq);
-                    dst[swz<LOG_T>(jj)] = x[qq];
-                }
+                for (int qq = 0; qq < C; ++qq)
+                    ptx::st_cluster(ptx::mapa(work_s + 4u * swz<LOG_T>(jj), qq), x[qq]);
             }
-            cluster_sync_all();
+            ptx::cluster_sync();
 #pragma unroll
-            for (int e = 0; e < 32; ++e) v[e] = sm[swz<LOG_T>(tid + T * e)];
+            for (int e = 0; e < 32; ++e) v[e] = work[swz<LOG_T>(tid + T * e)];
         } else {
 #pragma unroll
             for (int e = 0; e < 32; ++e) v[e] = __ldg(&data[tid + T * e]);
@@ -142,7 +185,7 @@ ntt_fwd_kernel(NttArgs a) {
             }
         }
 #pragma unroll
-        for (int e = 0; e < 32; ++e) sm[swz<LOG_T>(tid + T * e)] = v[e];
+        for (int e = 0; e < 32; ++e) work[swz<LOG_T>(tid + T * e)] = v[e];
         __syncthreads();
 
         // ---- round B: RB stages on groups (g, lane): p = T*g + lane + 32*e, e < 2^RB
@@ -155,7 +198,7 @@ ntt_fwd_kernel(NttArgs a) {
                 const int g = w_ * GPT + gi;
                 uint32_t* vv = v + gi * EG;
 #pragma unroll
-                for (int e = 0; e < EG; ++e) vv[e] = sm[swz<LOG_T>(T * g + lane + 32 * e)];
+                for (int e = 0; e < EG; ++e) vv[e] = work[swz<LOG_T>(T * g + lane + 32 * e)];
 #pragma unroll
                 for (int k = 0; k < RB; ++k) {
                     const int half = EG >> (k + 1);
@@ -167,14 +210,8 @@ ntt_fwd_kernel(NttArgs a) {
                         }
                     }
                 }
-            }
-            __syncthreads();
 #pragma unroll
-            for (int gi = 0; gi < GPT; ++gi) {
-                const int g = w_ * GPT + gi;
-                uint32_t* vv = v + gi * EG;
-#pragma unroll
-                for (int e = 0; e < EG; ++e) sm[swz<LOG_T>(T * g + lane + 32 * e)] = vv[e];
+                for (int e = 0; e < EG; ++e) work[swz<LOG_T>(T * g + lane + 32 * e)] = vv[e];
             }
             __syncthreads();
         }
@@ -183,7 +220,7 @@ ntt_fwd_kernel(NttArgs a) {
         {
             const int gidx = rev_bits<LOG_T>(tid);
 #pragma unroll
-            for (int e = 0; e < 32; ++e) v[e] = sm[swz<LOG_T>(32 * gidx + e)];
+            for (int e = 0; e < 32; ++e) v[e] = work[swz<LOG_T>(32 * gidx + e)];
             const uint2* twc = a.twC + (((size_t)mod * C + c) * 31) * T + tid;
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
@@ -203,59 +240,78 @@ ntt_fwd_kernel(NttArgs a) {
         if constexpr (C == 1) {
 #pragma unroll
             for (int e = 0; e < 32; ++e) data[rev_bits<5>(e) * T + tid] = v[e];
-            __syncthreads();  // sm is rewritten by the next row's round A
-        } else {
+            __syncthreads();  // `work` is rewritten by the next row's round A
+        } else if constexpr (!PUSH) {
             __syncthreads();  // every thread has read its round-C inputs
 #pragma unroll
-            for (int e = 0; e < 32; ++e) sm[swz<LOG_T>(rev_bits<5>(e) * T + tid)] = v[e];
-            cluster_sync_all();
+            for (int e = 0; e < 32; ++e) work[swz<LOG_T>(rev_bits<5>(e) * T + tid)] = v[e];
+            ptx::cluster_sync();
             // CTA c writes k in [c*NC, (c+1)*NC); k lives in CTA rev(k mod C) at k / C.
 #pragma unroll 8
             for (int u = 0; u < 32; ++u) {
                 const int k = c * NC + u * T + tid;
                 const int own = rev_bits<LOG_C>(k & (C - 1));
-                const uint32_t* src = cluster.map_shared_rank(sm, own);
-                data[k] = src[swz<LOG_T>(k >> LOG_C)];
+                data[k] = ptx::ld_cluster(ptx::mapa(work_s + 4u * swz<LOG_T>(k >> LOG_C), own));
+            }
+        } else {
+            // output k = k_local * C + rev(c) goes to the CTA that stores [d*NC, (d+1)*NC)
+            uint32_t* const recv = work + NC;
+            const uint32_t recv_s = work_s + 4u * NC;
+            const int rc = rev_bits<LOG_C>(c);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                const int k = (rev_bits<5>(e) * T + tid) * C + rc;
+                ptx::st_cluster(ptx::mapa(recv_s + 4u * swo<LOG_C>(k & (NC - 1)), k >> LOG_NC), v[e]);
+            }
+            ptx::cluster_sync();
+#pragma unroll
+            for (int u = 0; u < 32; ++u) {
+                const int off = u * T + tid;
+                data[c * NC + off] = recv[swo<LOG_C>(off)];
             }
         }
     }
-    if constexpr (C > 1) cluster_sync_all();  // peers may still read this CTA's sm
+    if constexpr (C > 1) ptx::cluster_sync();
 }
 
-template <int LOG_T, int LOG_C>
+template <int LOG_T, int LOG_C, bool PUSH>
 __global__ void __launch_bounds__(1 << LOG_T, kMinBlocks<LOG_T>)
-ntt_inv_kernel(NttArgs a) {
+ntt_inv_kernel(const NttArgs a) {
     constexpr int T = 1 << LOG_T, C = 1 << LOG_C;
     constexpr int LOG_NC = LOG_T + 5, NC = 1 << LOG_NC;
     constexpr int N = NC * C;
     constexpr int RB = LOG_T - 5;
-    extern __shared__ uint32_t sm[];
+    extern __shared__ __align__(128) uint32_t work[];
+    const uint32_t work_s = ptx::smem_u32(work);
     const int tid = threadIdx.x;
     const int c = (C > 1) ? (int)blockIdx.x : 0;
-    cg::cluster_group cluster = cg::this_cluster();
+    const RowIter ri = row_iter(a.rows, a.contiguous);
+    if constexpr (C > 1) ptx::cluster_sync();  // every peer is resident before the first push
 
-    for (int row = blockIdx.y; row < a.rows; row += gridDim.y) {
+    for (int row = ri.row; row < ri.end; row += ri.step) {
         const int limb = row / a.batch;
         const uint32_t q = a.map.q[limb];
         const int mod = a.map.mod[limb];
         const uint2* tw = a.tw + (size_t)mod * N;
         uint32_t* data = a.data + (size_t)row * N;
+        if (tid == 0 && row + ri.step < ri.end) prefetch_row<LOG_T, LOG_C, false>(data + (size_t)ri.step * N, c);
         uint32_t v[32];
 
-        // ---- load in bit-reversed order: thread tid gets k_local = rev5(e)*T + tid
+        // ---- input in bit-reversed order: thread tid gets k_local = rev5(e)*T + tid
         if constexpr (C > 1) {
-            cluster_sync_all();
+            // push: peers finished reading their `work` before the previous row's second
+            // barrier; pull: peers may still be reading this CTA's `work` (cross stages)
+            if constexpr (!PUSH) ptx::cluster_sync();
 #pragma unroll 8
             for (int u = 0; u < 32; ++u) {
                 const int k = c * NC + u * T + tid;
                 const int own = rev_bits<LOG_C>(k & (C - 1));
-                uint32_t* dst = cluster.map_shared_rank(sm, own);
-                dst[swz<LOG_T>(k >> LOG_C)] = __ldg(&data[k]);
+                ptx::st_cluster(ptx::mapa(work_s + 4u * swz<LOG_T>(k >> LOG_C), own), __ldg(&data[k]));
             }
-            cluster_sync_all();
+            ptx::cluster_sync();
 #pragma unroll
-            for (int e = 0; e < 32; ++e) v[e] = sm[swz<LOG_T>(rev_bits<5>(e) * T + tid)];
-            __syncthreads();  // sm is rewritten below at round-C positions
+            for (int e = 0; e < 32; ++e) v[e] = work[swz<LOG_T>(rev_bits<5>(e) * T + tid)];
+            __syncthreads();  // `work` is rewritten below
         } else {
 #pragma unroll
             for (int e = 0; e < 32; ++e) v[e] = __ldg(&data[rev_bits<5>(e) * T + tid]);
@@ -278,7 +334,7 @@ ntt_inv_kernel(NttArgs a) {
                 }
             }
 #pragma unroll
-            for (int e = 0; e < 32; ++e) sm[swz<LOG_T>(32 * gidx + e)] = v[e];
+            for (int e = 0; e < 32; ++e) work[swz<LOG_T>(32 * gidx + e)] = v[e];
             __syncthreads();
         }
 
@@ -292,7 +348,7 @@ ntt_inv_kernel(NttArgs a) {
                 const int g = w_ * GPT + gi;
                 uint32_t* vv = v + gi * EG;
 #pragma unroll
-                for (int e = 0; e < EG; ++e) vv[e] = sm[swz<LOG_T>(T * g + lane + 32 * e)];
+                for (int e = 0; e < EG; ++e) vv[e] = work[swz<LOG_T>(T * g + lane + 32 * e)];
 #pragma unroll
                 for (int k = RB - 1; k >= 0; --k) {
                     const int half = EG >> (k + 1);
@@ -304,21 +360,15 @@ ntt_inv_kernel(NttArgs a) {
                         }
                     }
                 }
-            }
-            __syncthreads();
 #pragma unroll
-            for (int gi = 0; gi < GPT; ++gi) {
-                const int g = w_ * GPT + gi;
-                uint32_t* vv = v + gi * EG;
-#pragma unroll
-                for (int e = 0; e < EG; ++e) sm[swz<LOG_T>(T * g + lane + 32 * e)] = vv[e];
+                for (int e = 0; e < EG; ++e) work[swz<LOG_T>(T * g + lane + 32 * e)] = vv[e];
             }
             __syncthreads();
         }
 
         // ---- round A'
 #pragma unroll
-        for (int e = 0; e < 32; ++e) v[e] = sm[swz<LOG_T>(tid + T * e)];
+        for (int e = 0; e < 32; ++e) v[e] = work[swz<LOG_T>(tid + T * e)];
 #pragma unroll
         for (int k = 4; k >= 0; --k) {
             const int half = 16 >> k;
@@ -336,19 +386,34 @@ ntt_inv_kernel(NttArgs a) {
             for (int e = 0; e < 32; ++e) data[tid + T * e] = mul_shoup(v[e], ni.x, ni.y, q);
             __syncthreads();
         } else {
-            __syncthreads();
-#pragma unroll
-            for (int e = 0; e < 32; ++e) sm[swz<LOG_T>(tid + T * e)] = v[e];
-            cluster_sync_all();
             constexpr int PER = NC / C;
+            uint32_t* const recv = work + NC;
+            if constexpr (PUSH) {
+                // quarter c's value at p goes to CTA p / PER, which runs the cross stages there
+#pragma unroll
+                const uint32_t recv_s = work_s + 4u * NC;
+                for (int e = 0; e < 32; ++e) {
+                    const int p = tid + T * e;
+                    ptx::st_cluster(ptx::mapa(recv_s + 4u * (c * PER + (p & (PER - 1))), p / PER), v[e]);
+                }
+            } else {
+                // each thread rewrites exactly the positions it read in round A'
+#pragma unroll
+                for (int e = 0; e < 32; ++e) work[swz<LOG_T>(tid + T * e)] = v[e];
+            }
+            ptx::cluster_sync();
 #pragma unroll
             for (int u = 0; u < PER / T; ++u) {
-                const int jj = c * PER + u * T + tid;
+                const int jl = u * T + tid;
+                const int jj = c * PER + jl;
                 uint32_t x[C];
 #pragma unroll
                 for (int qq = 0; qq < C; ++qq) {
-                    const uint32_t* src = cluster.map_shared_rank(sm, qq);
-                    x[qq] = src[swz<LOG_T>(jj)];
+                    if constexpr (PUSH) {
+                        x[qq] = recv[qq * PER + jl];
+                    } else {
+                        x[qq] = ptx::ld_cluster(ptx::mapa(work_s + 4u * swz<LOG_T>(jj), qq));
+                    }
                 }
 #pragma unroll
                 for (int s = LOG_C - 1; s >= 0; --s) {
@@ -366,33 +431,31 @@ ntt_inv_kernel(NttArgs a) {
             }
         }
     }
-    if constexpr (C > 1) cluster_sync_all();
+    if constexpr (C > 1) ptx::cluster_sync();
 }
 
-template <int LOG_T, int LOG_C>
-int launch(const fhe_ctx* ctx, const NttTables& t, bool inverse, uint32_t* d, int rows,
+template <int LOG_T, int LOG_C, bool PUSH>
+int launch(const fhe_ctx* ctx, const NttTables& t, int variant, bool inverse, uint32_t* d, int rows,
            int batch, const LimbMap& map, cudaStream_t stream) {
     constexpr int T = 1 << LOG_T, C = 1 << LOG_C;
-    constexpr int smem = (T * 32) * 4;
+    constexpr int smem = kSmemWords<LOG_T, LOG_C, PUSH> * 4;
     NttArgs args;
     args.data = d;
     args.rows = rows;
     args.batch = batch;
     args.tw = inverse ? t.inv : t.fwd;
-    args.twC = inverse ? t.invC : t.fwdC;
+    args.twC = inverse ? t.invC[variant & 1] : t.fwdC[variant & 1];
     args.ninv = t.ninv;
+    args.status = ctx->d_status;
+    args.contiguous = 0;
     args.map = map;
-    void (*kern)(NttArgs) = inverse ? ntt_inv_kernel<LOG_T, LOG_C> : ntt_fwd_kernel<LOG_T, LOG_C>;
+    void (*kern)(NttArgs) = inverse ? ntt_inv_kernel<LOG_T, LOG_C, PUSH> : ntt_fwd_kernel<LOG_T, LOG_C, PUSH>;
     FHE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    // give the rest of the L1/shared array to L1, which caches the twiddle tables
+    int carve = (int)((kMinBlocks<LOG_T> * (smem + 1024) * 100 + 228 * 1024 - 1) / (228 * 1024));
+    FHE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carve > 100 ? 100 : carve));
     if (C > 1) FHE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    // rows beyond the grid are looped over; size the grid to a few waves of the GPU
-    int per_sm = (LOG_T >= 9) ? 2 : 4;
-    int max_rows = ctx->num_sms * per_sm * 8 / C;
-    if (max_rows < 1) max_rows = 1;
-    int gy = rows < max_rows ? rows : max_rows;
-    if (gy > 65535) gy = 65535;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(C, gy, 1);
     cfg.blockDim = dim3(T, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
@@ -403,6 +466,21 @@ int launch(const fhe_ctx* ctx, const NttTables& t, bool inverse, uint32_t* d, in
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    // persistent: exactly one wave of clusters. Clusters must fit inside a GPC, so the number
+    // that can be resident at once is asked from the occupancy calculator, not derived from
+    // the SM count (a second, partial wave would double the run time).
+    static int max_clusters[2] = {0, 0};
+    int& mc = max_clusters[inverse ? 1 : 0];
+    if (mc == 0) {
+        cfg.gridDim = dim3(C, 1, 1);
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess || n < 1)
+            n = ctx->num_sms * kMinBlocks<LOG_T> / C;
+        mc = n < 1 ? 1 : n;
+    }
+    int gy = rows < mc ? rows : mc;
+    if (gy > 65535) gy = 65535;
+    cfg.gridDim = dim3(C, gy, 1);
     FHE_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, args));
     return FHE_OK;
 }
@@ -413,21 +491,30 @@ uint32_t rev_h(uint32_t x, int bits) {
     return r;
 }
 
-void ntt_shape(uint32_t logN, int* log_t, int* log_c) {
-    *log_c = logN > 14 ? (int)logN - 14 : 0;
-    *log_t = (int)logN - 5 - *log_c;
-}
-
 }  // namespace
+
+// Variant bit 0 selects the shape: CTAs of up to 512 threads (one limb of N <= 2^14 per CTA),
+// or CTAs of half the size in clusters twice as large (two CTAs share an SM). Variant bit 1
+// selects how a cluster exchanges data: peers read each other's buffers (pull, one buffer,
+// three barriers per row) or store into a receive buffer (push, two buffers, two barriers).
+bool ntt_variant_push(int variant) { return (variant & 2) != 0; }
+
+bool ntt_variant_shape(uint32_t logN, int variant, int* log_t, int* log_c) {
+    if (logN < FHE_LOGN_MIN || logN > FHE_LOGN_MAX || variant < 0 || variant >= kNttVariants) return false;
+    int lt = logN >= 14 ? 9 : (int)logN - 5;
+    if ((variant & 1) == 1) {
+        if (logN <= 11) return false;
+        lt -= 1;
+    }
+    *log_t = lt;
+    *log_c = (int)logN - 5 - lt;
+    return true;
+}
 
 int build_ntt_tables(fhe_ctx* ctx, uint32_t logN) {
     const int nmod = (int)ctx->mods.size();
     const uint32_t N = 1u << logN;
-    int log_t, log_c;
-    ntt_shape(logN, &log_t, &log_c);
-    const int T = 1 << log_t, C = 1 << log_c;
     std::vector<uint2> fwd((size_t)nmod * N), inv((size_t)nmod * N);
-    std::vector<uint2> fwdC((size_t)nmod * C * 31 * T), invC((size_t)nmod * C * 31 * T);
     std::vector<uint2> ninv(nmod);
     for (int m = 0; m < nmod; ++m) {
         const uint32_t q = ctx->mods[m];
@@ -446,28 +533,35 @@ int build_ntt_tables(fhe_ctx* ctx, uint32_t logN) {
             fwd[(size_t)m * N + i] = make_uint2(pw[r], shoup_h(pw[r], q));
             inv[(size_t)m * N + i] = make_uint2(pwi[r], shoup_h(pwi[r], q));
         }
-        // last-round tables: thread tid of CTA c, entry (2^k - 1 + b) holds
-        // tw[2^k * ((C + c) * T + rev(tid)) + b]
-        for (int c = 0; c < C; ++c)
-            for (int tid = 0; tid < T; ++tid) {
-                uint32_t gidx = rev_h((uint32_t)tid, log_t);
-                for (int k = 0; k < 5; ++k)
-                    for (int bb = 0; bb < (1 << k); ++bb) {
-                        size_t idx = (size_t)(1u << k) * ((uint32_t)(C + c) * T + gidx) + bb;
-                        size_t dst = (((size_t)m * C + c) * 31 + ((1 << k) - 1 + bb)) * T + tid;
-                        fwdC[dst] = fwd[(size_t)m * N + idx];
-                        invC[dst] = inv[(size_t)m * N + idx];
-                    }
-            }
         uint32_t ni = invmod_h(N % q, q);
         ninv[m] = make_uint2(ni, shoup_h(ni, q));
     }
     NttTables& t = ctx->ntt[logN];
     int rc;
+    // last-round tables per shape: thread tid of CTA c, entry (2^k - 1 + b) holds
+    // tw[2^k * ((C + c) * T + rev(tid)) + b]
+    for (int v = 0; v < 2; ++v) {
+        int log_t, log_c;
+        if (!ntt_variant_shape(logN, v, &log_t, &log_c)) continue;
+        const int T = 1 << log_t, C = 1 << log_c;
+        std::vector<uint2> fwdC((size_t)nmod * C * 31 * T), invC((size_t)nmod * C * 31 * T);
+        for (int m = 0; m < nmod; ++m)
+            for (int c = 0; c < C; ++c)
+                for (int tid = 0; tid < T; ++tid) {
+                    uint32_t gidx = rev_h((uint32_t)tid, log_t);
+                    for (int k = 0; k < 5; ++k)
+                        for (int bb = 0; bb < (1 << k); ++bb) {
+                            size_t idx = (size_t)(1u << k) * ((uint32_t)(C + c) * T + gidx) + bb;
+                            size_t dst = (((size_t)m * C + c) * 31 + ((1 << k) - 1 + bb)) * T + tid;
+                            fwdC[dst] = fwd[(size_t)m * N + idx];
+                            invC[dst] = inv[(size_t)m * N + idx];
+                        }
+                }
+        if ((rc = dev_upload(ctx, &t.fwdC[v], fwdC))) return rc;
+        if ((rc = dev_upload(ctx, &t.invC[v], invC))) return rc;
+    }
     if ((rc = dev_upload(ctx, &t.fwd, fwd))) return rc;
     if ((rc = dev_upload(ctx, &t.inv, inv))) return rc;
-    if ((rc = dev_upload(ctx, &t.fwdC, fwdC))) return rc;
-    if ((rc = dev_upload(ctx, &t.invC, invC))) return rc;
     if ((rc = dev_upload(ctx, &t.ninv, ninv))) return rc;
     return FHE_OK;
 }
@@ -479,16 +573,29 @@ int ntt_u32(const fhe_ctx* ctx, uint32_t logN, bool inverse, uint32_t* d, int n_
     const long long rows = (long long)n_limbs * batch;
     if (rows == 0) return FHE_OK;
     if (rows > (1LL << 30)) return set_error(FHE_EINVAL, "too many rows");
-    switch (logN) {
-        case 10: return launch<5, 0>(ctx, t, inverse, d, (int)rows, batch, map, stream);
-        case 11: return launch<6, 0>(ctx, t, inverse, d, (int)rows, batch, map, stream);
-        case 12: return launch<7, 0>(ctx, t, inverse, d, (int)rows, batch, map, stream);
-        case 13: return launch<8, 0>(ctx, t, inverse, d, (int)rows, batch, map, stream);
-        case 14: return launch<9, 0>(ctx, t, inverse, d, (int)rows, batch, map, stream);
-        case 15: return launch<9, 1>(ctx, t, inverse, d, (int)rows, batch, map, stream);
-        case 16: return launch<9, 2>(ctx, t, inverse, d, (int)rows, batch, map, stream);
-        default: return set_error(FHE_EINVAL, "logN out of range");
+    const int v = ctx->ntt_variant[logN];
+    int log_t, log_c;
+    if (!ntt_variant_shape(logN, v, &log_t, &log_c)) return set_error(FHE_EINVAL, "logN out of range");
+#define FHE_NTT_CASE(LT, LC)                                                                       \
+    if (log_t == LT && log_c == LC) {                                                              \
+        if (LC > 0 && ntt_variant_push(v))                                                         \
+            return launch<LT, LC, true>(ctx, t, v, inverse, d, (int)rows, batch, map, stream);     \
+        return launch<LT, LC, false>(ctx, t, v, inverse, d, (int)rows, batch, map, stream);        \
     }
+    FHE_NTT_CASE(5, 0)
+    FHE_NTT_CASE(6, 0)
+    FHE_NTT_CASE(7, 0)
+    FHE_NTT_CASE(8, 0)
+    FHE_NTT_CASE(9, 0)
+    FHE_NTT_CASE(9, 1)
+    FHE_NTT_CASE(9, 2)
+    FHE_NTT_CASE(6, 1)
+    FHE_NTT_CASE(7, 1)
+    FHE_NTT_CASE(8, 1)
+    FHE_NTT_CASE(8, 2)
+    FHE_NTT_CASE(8, 3)
+#undef FHE_NTT_CASE
+    return set_error(FHE_EINVAL, "no kernel for this NTT shape");
 }
 
 }  // namespace fhe

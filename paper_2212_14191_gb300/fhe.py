@@ -44,6 +44,11 @@ _SIGS = {
     "fhe_rescale": (_i, [_vp, _u32, _i, _i, _vp, _vp, _vp, _sz, _vp]),
     "fhe_hmult": (_i, [_vp, _u32, _i, _i, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "fhe_rescale_noalloc": (_i, [_vp, _u32, _i, _i, _vp, _vp, _vp]),
+    "fhe_device_status": (_i, [_vp, _i]),
+    "fhe_ntt_variant_count": (_i, [_vp, _u32]),
+    "fhe_ntt_get_variant": (_i, [_vp, _u32]),
+    "fhe_ntt_set_variant": (_i, [_vp, _u32, _i]),
+    "fhe_autotune_ntt": (_i, [_vp, _u32, _vp, _i, _i, _i, ctypes.POINTER(ctypes.c_float), _vp]),
     "fhe_last_error": (_i, [ctypes.c_char_p, _sz]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -129,6 +134,30 @@ def fhe_rescale_noalloc(ctx, logN, n_limbs, batch, ct_in, ct_out, stream=0):
 
 def fhe_hmult(ctx, logN, n_limbs, batch, a, b, evk, out, scratch, scratch_bytes, stream=0):
     return _check(_lib.fhe_hmult(ctx, logN, n_limbs, batch, a, b, evk, out, scratch, scratch_bytes, stream))
+
+
+def fhe_device_status(ctx, clear=1):
+    return _check(_lib.fhe_device_status(ctx, clear))
+
+
+def fhe_ntt_variant_count(ctx, logN):
+    return int(_lib.fhe_ntt_variant_count(ctx, logN))
+
+
+def fhe_ntt_get_variant(ctx, logN):
+    return int(_lib.fhe_ntt_get_variant(ctx, logN))
+
+
+def fhe_ntt_set_variant(ctx, logN, variant):
+    return _check(_lib.fhe_ntt_set_variant(ctx, logN, variant))
+
+
+def fhe_autotune_ntt(ctx, logN, d_ptr, n_limbs, batch, reps=3, stream=0):
+    """Returns the per-shape milliseconds (forward + inverse) measured by the library."""
+    n = max(1, fhe_ntt_variant_count(ctx, logN))
+    ms = (ctypes.c_float * n)()
+    _check(_lib.fhe_autotune_ntt(ctx, logN, d_ptr, n_limbs, batch, reps, ms, stream))
+    return [float(x) for x in ms]
 
 
 # ---------------------------------------------------------------- torch convenience layer

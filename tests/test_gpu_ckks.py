@@ -144,3 +144,22 @@ def test_hmult_full_size_config(fhe):
         assert (got[:, :, b] == want).all(), b
         dec = C.decode(np.array(C.decrypt_coeffs(prm, got[:, :, b].astype(U64), s), dtype=float), scale)
         assert np.abs(dec - zs[k]).max() / np.abs(zs[k]).max() < 1e-5
+
+
+def test_hmult_tensor_core_path(fhe):
+    """The whole HMULT with the tensor-core NTT as the context's default path."""
+    import torch
+    logn, nl = 12, 6
+    qs, ps = P.default_moduli(8, 4)
+    prm = C.Params(1 << logn, qs, ps, alpha=4)
+    s, evk = make_key(prm, 77)
+    ctx = fhe.Context(logn, qs, ps, alpha=4, default_path=fhe.FHE_NTT_TC)
+    a, b = batch_cts(prm, nl, 2, 81), batch_cts(prm, nl, 2, 82)
+    out = ctx.hmult(fhe.to_device(a), fhe.to_device(b), fhe.to_device(evk.astype(np.uint32)), logn)
+    torch.cuda.synchronize()
+    fhe.fhe_device_status(ctx.handle, 1)
+    got = fhe.to_host(out)
+    for k in range(2):
+        want = C.hmult(prm, nl, a[:, :, k].astype(U64), b[:, :, k].astype(U64), evk)
+        assert (got[:, :, k] == want).all(), k
+    ctx.close()

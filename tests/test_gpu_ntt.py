@@ -10,7 +10,7 @@ pytestmark = pytest.mark.gpu
 
 QS, PS = P.default_moduli(44, 8)
 MODS = QS + PS
-PATHS = ["u32"]
+PATHS = ["u32", "tc"]
 
 
 @pytest.fixture(scope="module")
@@ -37,10 +37,17 @@ def psis(mods, n):
     return [P.psi(m, n) for m in mods]
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("logn", [10, 11, 12, 13, 14, 15, 16])
-def test_fwd_inv_match_oracle(fhe, ctx, logn, path):
+def test_fwd_inv_match_oracle(fhe, ctx, logn, path, variant):
     import torch
+    if path == "tc" and variant > 0:
+        pytest.skip("kernel shapes apply to the 32-bit path")
+    try:
+        fhe.fhe_ntt_set_variant(ctx.handle, logn, variant)
+    except fhe.FheError:
+        pytest.skip("no such shape at this N")
     n = 1 << logn
     first, nl, batch = 42, 4, 3          # limbs q_42, q_43, p_0, p_1: crosses the q/p boundary
     mods = MODS[first:first + nl]
@@ -58,6 +65,7 @@ def test_fwd_inv_match_oracle(fhe, ctx, logn, path):
     ctx.ntt_inv(e, logn, first_limb=first, path=_path(fhe, path))
     want, _ = ON.ntt_batch(y, mods, psis(mods, n), inverse=True)
     assert (fhe.to_host(e) == want).all()
+    fhe.fhe_ntt_set_variant(ctx.handle, logn, 0)
 
 
 @pytest.mark.parametrize("path", PATHS)
@@ -127,6 +135,29 @@ def test_edge_values(fhe, ctx, path):
             assert (fhe.to_host(d) == want).all()
             ctx.ntt_inv(d, logn, path=_path(fhe, path))
             assert (fhe.to_host(d) == x).all()
+
+
+@pytest.mark.parametrize("logn", [12, 16])
+def test_autotune_keeps_results(fhe, ctx, logn):
+    import torch
+    n = 1 << logn
+    x = I.uniform_residues(55, QS[:4], 8, n)
+    d = fhe.to_device(x)
+    ms = fhe.fhe_autotune_ntt(ctx.handle, logn, d.data_ptr(), 4, 8, reps=2,
+                              stream=torch.cuda.current_stream().cuda_stream)
+    assert len(ms) == fhe.fhe_ntt_variant_count(ctx.handle, logn)
+    valid = [i for i, m in enumerate(ms) if m > 0]
+    assert valid and all(ms[i] == -1 for i in range(len(ms)) if i not in valid)
+    assert fhe.fhe_ntt_get_variant(ctx.handle, logn) == min(valid, key=lambda i: ms[i])
+    assert (fhe.to_host(d) == x).all()          # the round trips restore the input
+    ctx.ntt_fwd(d, logn)
+    want, _ = ON.ntt_batch(x, QS[:4], psis(QS[:4], n))
+    assert (fhe.to_host(d) == want).all()
+    fhe.fhe_ntt_set_variant(ctx.handle, logn, 0)
+
+
+def test_device_status_clean(fhe, ctx):
+    fhe.fhe_device_status(ctx.handle, 1)
 
 
 def test_batch_zero_and_bad_args(fhe, ctx):
