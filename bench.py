@@ -38,12 +38,16 @@ HM_LIMBS, HM_K, HM_ALPHA, HM_BATCH = 24, 8, 8, 128
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--hmult-steps", type=int, default=3)
     ap.add_argument("--no-hmult", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=2000)
+    ap.add_argument("--batch-ops", type=int, default=1000)
     return ap.parse_args()
 
 
@@ -63,7 +67,7 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """Samples nvidia-smi every 200 ms while the timed region runs."""
+    """Samples nvidia-smi every 50 ms while the timed region runs."""
 
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -78,7 +82,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except OSError:
@@ -337,6 +341,10 @@ def ours(args):
             torch.cuda.empty_cache()
         del a, b, evk, out
 
+    batch_res = None if args.no_batch else mixed_batch(args, fhe, ctx, qs, ps, st, barrier, max_over_ranks, ws)
+
+    serve_res = None if args.no_serving else serving_bench(args, fhe, qs, ps)
+
     if rank == 0:
         peaks, peak_kind = measured_peaks()
         n1, n2 = 1 << ((LOGN + 1) // 2), 1 << (LOGN // 2)
@@ -374,6 +382,8 @@ def ours(args):
                        "parallelism": "replicas" if ws > 1 else "1 GPU"},
             "paths": results,
             "hmult": hm,
+            "mixed_batch": batch_res,
+            "serving": serve_res,
             "roofline": roof,
             "roofline_u32": roof_u32,
             "roofline_tc": roof_tc,
@@ -389,6 +399,128 @@ def ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def mixed_batch(args, fhe, ctx, qs, ps, st, barrier, max_over_ranks, ws):
+    """Uneven batch: `--batch-ops` operations, kind uniform over {NTT, INTT, HMULT}, N uniform
+    over {2^14, 2^15, 2^16}, level count (ciphertext limbs) uniform in 3..44, batch 1 each.
+    One CUDA-graph replay of the batched plan vs. one library call per operation."""
+    import torch
+    g = np.random.default_rng(4)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(4)
+    sh = st.cuda_stream
+    n_ops = args.batch_ops
+    mods = qs + ps
+    dnum = -(-len(qs) // HM_ALPHA)
+    evk = {}
+    ops, tensors, desc = [], [], []
+    limb_transforms = 0
+    for i in range(n_ops):
+        kind = int(g.integers(0, 3))
+        logn = int(g.choice([14, 15, 16]))
+        nl = int(g.integers(3, 45))
+        n = 1 << logn
+        if kind < 2:
+            d = torch.randint(0, 1 << 29, (nl, 1, n), dtype=torch.int32, device="cuda", generator=gen)
+            k = fhe.FHE_OPK_NTT_FWD if kind == 0 else fhe.FHE_OPK_NTT_INV
+            ops.append(fhe.FheOp(kind=k, logN=logn, first_limb=0, n_limbs=nl, batch=1, data=d.data_ptr()))
+            tensors.append(d)
+            desc.append((k, logn, nl, d))
+            limb_transforms += nl
+        else:
+            if logn not in evk:
+                evk[logn] = torch.randint(0, 1 << 29, (dnum, 2, len(mods), n), dtype=torch.int32, device="cuda",
+                                          generator=gen)
+            a = torch.randint(0, 1 << 29, (2, nl, 1, n), dtype=torch.int32, device="cuda", generator=gen)
+            b = torch.randint(0, 1 << 29, (2, nl, 1, n), dtype=torch.int32, device="cuda", generator=gen)
+            out = torch.empty((2, nl - 1, 1, n), dtype=torch.int32, device="cuda")
+            ops.append(fhe.FheOp(kind=fhe.FHE_OPK_HMULT, logN=logn, n_limbs=nl, batch=1, a=a.data_ptr(),
+                                 b=b.data_ptr(), evk=evk[logn].data_ptr(), out=out.data_ptr()))
+            tensors += [a, b, out]
+            desc.append((fhe.FHE_OPK_HMULT, logn, nl, (a, b, out)))
+    plan = fhe.fhe_batch_create(ctx.handle, ops)
+    nbytes = fhe.fhe_batch_scratch_bytes(plan)
+    scratch = torch.empty(nbytes // 4 + 4, dtype=torch.int32, device="cuda")
+    fhe.fhe_batch_capture(plan, scratch.data_ptr(), nbytes)
+    per_op_bytes = max(fhe.fhe_scratch_bytes(ctx.handle, fhe.FHE_OP_HMULT, lg, 44, 1) for lg in (14, 15, 16))
+    op_scratch = torch.empty(per_op_bytes // 4 + 4, dtype=torch.int32, device="cuda")
+
+    def per_op():
+        for k, logn, nl, t in desc:
+            if k == fhe.FHE_OPK_NTT_FWD:
+                fhe.fhe_ntt_fwd(ctx.handle, fhe.FHE_NTT_U32, logn, t.data_ptr(), 0, nl, 1, sh)
+            elif k == fhe.FHE_OPK_NTT_INV:
+                fhe.fhe_ntt_inv(ctx.handle, fhe.FHE_NTT_U32, logn, t.data_ptr(), 0, nl, 1, sh)
+            else:
+                a, b, out = t
+                fhe.fhe_hmult(ctx.handle, logn, nl, 1, a.data_ptr(), b.data_ptr(), evk[logn].data_ptr(),
+                              out.data_ptr(), op_scratch.data_ptr(), per_op_bytes, sh)
+
+    def timed(fn, reps):
+        fn()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        barrier()
+        return max_over_ranks(e0.elapsed_time(e1) / 1e3 / reps)
+
+    t_graph = timed(lambda: fhe.fhe_batch_launch(plan, sh), 3)
+    t_ops = timed(per_op, 2)
+    n_hm = sum(1 for d in desc if d[0] == fhe.FHE_OPK_HMULT)
+    res = {"ops": n_ops, "hmult_ops": n_hm, "ntt_ops": n_ops - n_hm, "ntt_limb_transforms": limb_transforms,
+           "graph_ms": t_graph * 1e3, "per_op_ms": t_ops * 1e3,
+           "graph_kops": n_ops * ws / t_graph / 1e3, "per_op_kops": n_ops * ws / t_ops / 1e3,
+           "config": "N in {2^14,2^15,2^16}, 3..44 limbs, batch 1 per op, one graph launch vs one call per op",
+           "ntt_variant_16": fhe.fhe_ntt_get_variant(ctx.handle, 16)}
+    fhe.fhe_device_status(ctx.handle, 1)
+    fhe.fhe_batch_destroy(plan)
+    del tensors, scratch, op_scratch, evk
+    torch.cuda.empty_cache()
+    return res
+
+
+def serving_bench(args, fhe, qs, ps):
+    """Poisson stream (mean 50k requests/s) of HMULT / RESCALE / KEYSWITCH requests, N in
+    {2^15, 2^16}, 3..24 limbs, operands and evaluation keys resident in HBM, admitted by HBM
+    footprint (24 GiB budget), continuous batching over 4 CUDA streams."""
+    import torch
+    from paper_2212_14191_gb300 import serving as S
+    logns = (15, 16)
+    ctxs = {lg: fhe.Context(lg, qs[:HM_LIMBS], ps, alpha=HM_ALPHA) for lg in logns}
+    dnum = -(-HM_LIMBS // HM_ALPHA)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    evks = {lg: torch.randint(0, 1 << 29, (dnum, 2, HM_LIMBS + HM_K, 1 << lg), dtype=torch.int32, device="cuda",
+                              generator=gen) for lg in logns}
+
+    def make_inputs(kind, logN, nl, rid):
+        n = 1 << logN
+        if kind == S.KEYSWITCH:
+            return (torch.randint(0, 1 << 29, (nl, 1, n), dtype=torch.int32, device="cuda", generator=gen),)
+        k = 2 if kind == S.HMULT else 1
+        return tuple(torch.randint(0, 1 << 29, (2, nl, 1, n), dtype=torch.int32, device="cuda", generator=gen)
+                     for _ in range(k))
+
+    kinds = [S.HMULT, S.RESCALE, S.KEYSWITCH]
+    warm = S.poisson_requests(6, 60, 50000.0, kinds, logns, (3, 24), make_inputs)
+    server = S.Server(ctxs, evks, budget_bytes=24 << 30, n_streams=4, max_batch=32)
+    server.run(warm)
+    reqs = S.poisson_requests(7, args.serving_requests, 50000.0, kinds, logns, (3, 24), make_inputs)
+    torch.cuda.synchronize()
+    stats = server.run(reqs)
+    torch.cuda.synchronize()
+    stats["config"] = ("Poisson 50k req/s, HMULT/RESCALE/KEYSWITCH, N in {2^15,2^16}, 3..24 limbs, "
+                       "24 GiB admission budget, 4 streams, batches of <= 32")
+    for c in ctxs.values():
+        fhe.fhe_device_status(c.handle, 1)
+        c.close()
+    del reqs, warm, evks
+    torch.cuda.empty_cache()
+    return stats
 
 
 def main():

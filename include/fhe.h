@@ -177,6 +177,47 @@ int fhe_hmult(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const u
               size_t scratch_bytes, void* stream);
 
 /*
+ * Operation-level batching (Sec. IV-D) of many independent operations with uneven ring
+ * degree and level, replayed as one CUDA graph launch.
+ *   fhe_op: one operation. kind FHE_OPK_NTT_FWD / FHE_OPK_NTT_INV transform `data`
+ *     (n_limbs, batch, N) in place with moduli first_limb.. (plain 32-bit path); kind
+ *     FHE_OPK_HMULT computes out = fhe_hmult(a, b, evk) at n_limbs ciphertext limbs
+ *     (first_limb ignored). All device pointers 16-byte aligned; operations must not
+ *     overlap in memory; their results equal those of the single-operation calls.
+ *   fhe_batch_create -- validates and plans the list: every limb transform of one (N,
+ *     direction) becomes a row of one NTT launch; HMULTs sharing (N, n_limbs, evk) are
+ *     gathered into one batch. Allocates the plan's device tables (cudaMalloc). The op list
+ *     may be freed afterwards; the buffers it names must outlive the plan's runs.
+ *   fhe_batch_scratch_bytes -- device scratch needed by fhe_batch_run / _capture.
+ *   fhe_batch_run -- enqueues the plan on `stream` (capturable in a CUDA graph).
+ *   fhe_batch_capture -- runs the plan once, then captures it into a graph owned by the plan
+ *     (bound to this scratch buffer); fhe_batch_launch replays that graph on `stream`.
+ *   fhe_batch_destroy -- frees the plan and its graph (no work may be pending).
+ */
+#define FHE_OPK_NTT_FWD 1
+#define FHE_OPK_NTT_INV 2
+#define FHE_OPK_HMULT 3
+typedef struct fhe_op {
+    int kind;
+    uint32_t logN;
+    int first_limb;
+    int n_limbs;
+    int batch;
+    uint32_t* data;
+    const uint32_t* a;
+    const uint32_t* b;
+    const uint32_t* evk;
+    uint32_t* out;
+} fhe_op;
+typedef struct fhe_batch fhe_batch;
+int fhe_batch_create(const fhe_ctx* ctx, const fhe_op* ops, int n, fhe_batch** out);
+size_t fhe_batch_scratch_bytes(const fhe_batch* b);
+int fhe_batch_run(const fhe_batch* b, void* scratch, size_t scratch_bytes, void* stream);
+int fhe_batch_capture(fhe_batch* b, void* scratch, size_t scratch_bytes);
+int fhe_batch_launch(const fhe_batch* b, void* stream);
+int fhe_batch_destroy(fhe_batch* b);
+
+/*
  * fhe_rescale_noalloc -- the same RESCALE as fhe_rescale, for callers that cannot allocate
  * device memory: a serving loop that must not stall the device (cudaMalloc/cudaFree may
  * synchronise it), code whose device memory is all owned by another allocator under a fixed

@@ -374,9 +374,10 @@ int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const u
         k_conv<<<g, 256, (size_t)K * nl * 4, st>>>(ca);
         FHE_CUDA_TRY(cudaGetLastError());
     }
+    if (2 * nl > kMaxLimbs) return set_error(FHE_EINVAL, "too many limbs");
     LimbMap qm2;
     for (int c = 0; c < 2; ++c)
-        for (int i = 0; i < nl; ++i) {
+        for (int i = 0; i < nl && i < FHE_MAX_MODULI; ++i) {
             qm2.mod[c * nl + i] = (uint8_t)i;
             qm2.q[c * nl + i] = ctx->mods[i];
         }
@@ -409,9 +410,10 @@ int rescale_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uin
     ModVec qm = modvec(ctx, qidx, nout);
     k_rescale_broadcast<<<stream_grid(ctx, L4, 2 * nout), 256, 0, st>>>(last, xb, ctx->mods[nl - 1], nout, L4, qm);
     FHE_CUDA_TRY(cudaGetLastError());
+    if (2 * nout > kMaxLimbs) return set_error(FHE_EINVAL, "too many limbs");
     LimbMap qm2;
     for (int c = 0; c < 2; ++c)
-        for (int i = 0; i < nout; ++i) {
+        for (int i = 0; i < nout && i < FHE_MAX_MODULI; ++i) {
             qm2.mod[c * nout + i] = (uint8_t)i;
             qm2.q[c * nout + i] = ctx->mods[i];
         }

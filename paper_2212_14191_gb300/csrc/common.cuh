@@ -100,6 +100,7 @@ struct fhe_ctx {
     int num_sms = 0;
     int* d_status = nullptr;  // device error word written by kernels (FHE_ETIMEOUT, ...)
     void* tc_planes[2] = {};  // tensor-core path scratch: 8-bit digit planes of two operands
+    uint32_t* d_mods = nullptr;  // device copy of `mods`
 };
 
 namespace fhe {
@@ -111,6 +112,18 @@ struct LimbMap {
     uint32_t q[kMaxLimbs];
     uint8_t mod[kMaxLimbs];
 };
+
+// One row of a row-table NTT launch: a polynomial limb anywhere in device memory.
+struct RowRef {
+    uint32_t* ptr;
+    uint32_t mod;  // modulus index into the context's moduli
+    uint32_t pad;
+};
+
+// Plain-path NTT over rows listed in a device table (operation-level batching of rows
+// that live in different buffers).
+int ntt_u32_rows(const fhe_ctx* ctx, uint32_t logN, bool inverse, const RowRef* d_rows, int nrows,
+                 cudaStream_t stream);
 
 // Plain-path batched NTT over `n_limbs` limbs whose moduli are map.mod[l].
 int ntt_u32(const fhe_ctx* ctx, uint32_t logN, bool inverse, uint32_t* d, int n_limbs,

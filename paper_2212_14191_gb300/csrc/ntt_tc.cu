@@ -165,7 +165,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer
-        constexpr uint32_t idesc = ptx::idesc_bf16(kTileM, NT);
+        // the four digit planes of the constant matrix are consecutive rows of one B tile, so
+        // a single M=128, N=4*NT MMA per K step fills all four accumulators (TMEM columns
+        // [i*NT, (i+1)*NT) hold acc_i) and reads the A tile once
+        constexpr uint32_t idesc = ptx::idesc_bf16(kTileM, 4 * NT);
         bool ok = true;
         for (int c = 0; c < nchunks; ++c) {
             const int s = c % S;
@@ -177,11 +180,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 #pragma unroll
             for (int kk = 0; kk < kChunk / 16; ++kk) {
                 const uint64_t adesc = ptx::sdesc_sw128(As + kk * 32);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const uint64_t bdesc = ptx::sdesc_sw128(Bs + i * NT * 128 + kk * 32);
-                    ptx::mma_bf16(tmem + i * NT, adesc, bdesc, idesc, (c > 0 || kk > 0) ? 1u : 0u);
-                }
+                const uint64_t bdesc = ptx::sdesc_sw128(Bs + kk * 32);
+                ptx::mma_bf16(tmem, adesc, bdesc, idesc, (c > 0 || kk > 0) ? 1u : 0u);
             }
             ptx::mma_commit(&empty[s]);
         }

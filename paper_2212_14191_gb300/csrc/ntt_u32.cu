@@ -25,6 +25,8 @@
 #include "common.cuh"
 #include "ptx.cuh"
 
+#include <string.h>
+
 
 namespace fhe {
 namespace {
@@ -38,8 +40,30 @@ struct NttArgs {
     const uint2* ninv;  // [nmod]
     int* status;        // device error word (FHE_ETIMEOUT on an expired wait)
     int contiguous;     // row order: 0 = interleaved across clusters, 1 = contiguous ranges
+    const RowRef* rowtab;    // if set: row r is rowtab[r] (any buffer, any modulus) ...
+    const uint32_t* mod_q;   // ... with modulus mod_q[rowtab[r].mod]; `data`/`map` unused
     LimbMap map;
 };
+
+// Data pointer, modulus and modulus index of a row.
+template <int N>
+__device__ __forceinline__ uint32_t* row_ref(const NttArgs& a, int row, uint32_t* q, int* mod) {
+    if (a.rowtab) {
+        const RowRef r = a.rowtab[row];
+        *mod = (int)r.mod;
+        *q = __ldg(&a.mod_q[r.mod]);
+        return r.ptr;
+    }
+    const int limb = row / a.batch;
+    *q = a.map.q[limb];
+    *mod = a.map.mod[limb];
+    return a.data + (size_t)row * N;
+}
+
+template <int N>
+__device__ __forceinline__ uint32_t* row_ptr(const NttArgs& a, int row) {
+    return a.rowtab ? a.rowtab[row].ptr : a.data + (size_t)row * N;
+}
 
 template <int BITS>
 __device__ __forceinline__ uint32_t rev_bits(uint32_t x) {
@@ -130,12 +154,11 @@ ntt_fwd_kernel(const NttArgs a) {
     if constexpr (C > 1) ptx::cluster_sync();  // every peer is resident before the first push
 
     for (int row = ri.row; row < ri.end; row += ri.step) {
-        const int limb = row / a.batch;
-        const uint32_t q = a.map.q[limb];
-        const int mod = a.map.mod[limb];
+        uint32_t q;
+        int mod;
+        uint32_t* data = row_ref<N>(a, row, &q, &mod);
         const uint2* tw = a.tw + (size_t)mod * N;
-        uint32_t* data = a.data + (size_t)row * N;
-        if (tid == 0 && row + ri.step < ri.end) prefetch_row<LOG_T, LOG_C, true>(data + (size_t)ri.step * N, c);
+        if (tid == 0 && row + ri.step < ri.end) prefetch_row<LOG_T, LOG_C, true>(row_ptr<N>(a, row + ri.step), c);
         uint32_t v[32];
 
         if constexpr (C > 1) {
@@ -289,12 +312,11 @@ ntt_inv_kernel(const NttArgs a) {
     if constexpr (C > 1) ptx::cluster_sync();  // every peer is resident before the first push
 
     for (int row = ri.row; row < ri.end; row += ri.step) {
-        const int limb = row / a.batch;
-        const uint32_t q = a.map.q[limb];
-        const int mod = a.map.mod[limb];
+        uint32_t q;
+        int mod;
+        uint32_t* data = row_ref<N>(a, row, &q, &mod);
         const uint2* tw = a.tw + (size_t)mod * N;
-        uint32_t* data = a.data + (size_t)row * N;
-        if (tid == 0 && row + ri.step < ri.end) prefetch_row<LOG_T, LOG_C, false>(data + (size_t)ri.step * N, c);
+        if (tid == 0 && row + ri.step < ri.end) prefetch_row<LOG_T, LOG_C, false>(row_ptr<N>(a, row + ri.step), c);
         uint32_t v[32];
 
         // ---- input in bit-reversed order: thread tid gets k_local = rev5(e)*T + tid
@@ -390,8 +412,8 @@ ntt_inv_kernel(const NttArgs a) {
             uint32_t* const recv = work + NC;
             if constexpr (PUSH) {
                 // quarter c's value at p goes to CTA p / PER, which runs the cross stages there
-#pragma unroll
                 const uint32_t recv_s = work_s + 4u * NC;
+#pragma unroll
                 for (int e = 0; e < 32; ++e) {
                     const int p = tid + T * e;
                     ptx::st_cluster(ptx::mapa(recv_s + 4u * (c * PER + (p & (PER - 1))), p / PER), v[e]);
@@ -436,7 +458,7 @@ ntt_inv_kernel(const NttArgs a) {
 
 template <int LOG_T, int LOG_C, bool PUSH>
 int launch(const fhe_ctx* ctx, const NttTables& t, int variant, bool inverse, uint32_t* d, int rows,
-           int batch, const LimbMap& map, cudaStream_t stream) {
+           int batch, const LimbMap& map, const RowRef* rowtab, cudaStream_t stream) {
     constexpr int T = 1 << LOG_T, C = 1 << LOG_C;
     constexpr int smem = kSmemWords<LOG_T, LOG_C, PUSH> * 4;
     NttArgs args;
@@ -448,6 +470,8 @@ int launch(const fhe_ctx* ctx, const NttTables& t, int variant, bool inverse, ui
     args.ninv = t.ninv;
     args.status = ctx->d_status;
     args.contiguous = 0;
+    args.rowtab = rowtab;
+    args.mod_q = ctx->d_mods;
     args.map = map;
     void (*kern)(NttArgs) = inverse ? ntt_inv_kernel<LOG_T, LOG_C, PUSH> : ntt_fwd_kernel<LOG_T, LOG_C, PUSH>;
     FHE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -566,11 +590,28 @@ int build_ntt_tables(fhe_ctx* ctx, uint32_t logN) {
     return FHE_OK;
 }
 
+namespace {
+int ntt_u32_dispatch(const fhe_ctx* ctx, uint32_t logN, bool inverse, uint32_t* d, long long rows, int batch,
+                     const LimbMap& map, const RowRef* rowtab, cudaStream_t stream);
+}
+
 int ntt_u32(const fhe_ctx* ctx, uint32_t logN, bool inverse, uint32_t* d, int n_limbs, int batch,
             const LimbMap& map, cudaStream_t stream) {
+    return ntt_u32_dispatch(ctx, logN, inverse, d, (long long)n_limbs * batch, batch, map, nullptr, stream);
+}
+
+int ntt_u32_rows(const fhe_ctx* ctx, uint32_t logN, bool inverse, const RowRef* d_rows, int nrows,
+                 cudaStream_t stream) {
+    LimbMap unused;
+    memset(&unused, 0, sizeof(unused));
+    return ntt_u32_dispatch(ctx, logN, inverse, nullptr, nrows, 1, unused, d_rows, stream);
+}
+
+namespace {
+int ntt_u32_dispatch(const fhe_ctx* ctx, uint32_t logN, bool inverse, uint32_t* d, long long rows, int batch,
+                     const LimbMap& map, const RowRef* rowtab, cudaStream_t stream) {
     const NttTables& t = ctx->ntt[logN];
     if (!t.fwd) return set_error(FHE_EINVAL, "no NTT tables for this logN");
-    const long long rows = (long long)n_limbs * batch;
     if (rows == 0) return FHE_OK;
     if (rows > (1LL << 30)) return set_error(FHE_EINVAL, "too many rows");
     const int v = ctx->ntt_variant[logN];
@@ -579,8 +620,8 @@ int ntt_u32(const fhe_ctx* ctx, uint32_t logN, bool inverse, uint32_t* d, int n_
 #define FHE_NTT_CASE(LT, LC)                                                                       \
     if (log_t == LT && log_c == LC) {                                                              \
         if (LC > 0 && ntt_variant_push(v))                                                         \
-            return launch<LT, LC, true>(ctx, t, v, inverse, d, (int)rows, batch, map, stream);     \
-        return launch<LT, LC, false>(ctx, t, v, inverse, d, (int)rows, batch, map, stream);        \
+            return launch<LT, LC, true>(ctx, t, v, inverse, d, (int)rows, batch, map, rowtab, stream); \
+        return launch<LT, LC, false>(ctx, t, v, inverse, d, (int)rows, batch, map, rowtab, stream);\
     }
     FHE_NTT_CASE(5, 0)
     FHE_NTT_CASE(6, 0)
@@ -597,5 +638,6 @@ int ntt_u32(const fhe_ctx* ctx, uint32_t logN, bool inverse, uint32_t* d, int n_
 #undef FHE_NTT_CASE
     return set_error(FHE_EINVAL, "no kernel for this NTT shape");
 }
+}  // namespace
 
 }  // namespace fhe

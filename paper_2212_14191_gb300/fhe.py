@@ -32,6 +32,17 @@ _u32 = ctypes.c_uint32
 _i = ctypes.c_int
 _sz = ctypes.c_size_t
 
+FHE_OPK_NTT_FWD, FHE_OPK_NTT_INV, FHE_OPK_HMULT = 1, 2, 3
+
+
+class FheOp(ctypes.Structure):
+    """struct fhe_op of include/fhe.h."""
+    _fields_ = [("kind", ctypes.c_int), ("logN", ctypes.c_uint32), ("first_limb", ctypes.c_int),
+                ("n_limbs", ctypes.c_int), ("batch", ctypes.c_int), ("data", ctypes.c_void_p),
+                ("a", ctypes.c_void_p), ("b", ctypes.c_void_p), ("evk", ctypes.c_void_p),
+                ("out", ctypes.c_void_p)]
+
+
 _SIGS = {
     "fhe_gen_primes": (_i, [_u32, _i, _i, _u32p]),
     "fhe_ctx_create": (_i, [_u32, _u32p, _i, _u32p, _i, _i, _i, ctypes.POINTER(_vp)]),
@@ -50,6 +61,12 @@ _SIGS = {
     "fhe_ntt_set_variant": (_i, [_vp, _u32, _i]),
     "fhe_autotune_ntt": (_i, [_vp, _u32, _vp, _i, _i, _i, ctypes.POINTER(ctypes.c_float), _vp]),
     "fhe_last_error": (_i, [ctypes.c_char_p, _sz]),
+    "fhe_batch_create": (_i, [_vp, ctypes.POINTER(FheOp), _i, ctypes.POINTER(_vp)]),
+    "fhe_batch_scratch_bytes": (_sz, [_vp]),
+    "fhe_batch_run": (_i, [_vp, _vp, _sz, _vp]),
+    "fhe_batch_capture": (_i, [_vp, _vp, _sz]),
+    "fhe_batch_launch": (_i, [_vp, _vp]),
+    "fhe_batch_destroy": (_i, [_vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -158,6 +175,33 @@ def fhe_autotune_ntt(ctx, logN, d_ptr, n_limbs, batch, reps=3, stream=0):
     ms = (ctypes.c_float * n)()
     _check(_lib.fhe_autotune_ntt(ctx, logN, d_ptr, n_limbs, batch, reps, ms, stream))
     return [float(x) for x in ms]
+
+
+def fhe_batch_create(ctx, ops):
+    arr = (FheOp * max(1, len(ops)))(*ops)
+    h = _vp()
+    _check(_lib.fhe_batch_create(ctx, arr, len(ops), ctypes.byref(h)))
+    return h.value
+
+
+def fhe_batch_scratch_bytes(batch):
+    return int(_lib.fhe_batch_scratch_bytes(batch))
+
+
+def fhe_batch_run(batch, scratch, scratch_bytes, stream=0):
+    return _check(_lib.fhe_batch_run(batch, scratch, scratch_bytes, stream))
+
+
+def fhe_batch_capture(batch, scratch, scratch_bytes):
+    return _check(_lib.fhe_batch_capture(batch, scratch, scratch_bytes))
+
+
+def fhe_batch_launch(batch, stream=0):
+    return _check(_lib.fhe_batch_launch(batch, stream))
+
+
+def fhe_batch_destroy(batch):
+    return _check(_lib.fhe_batch_destroy(batch))
 
 
 # ---------------------------------------------------------------- torch convenience layer

@@ -1,0 +1,177 @@
+"""Continuous-batching request loop for HMULT / RESCALE / KEYSWITCH (the API layer of
+Sec. IV-E: it collects operation requests, picks batch sizes from the hardware's memory and
+invokes the kernels, with intermediate results kept in device memory).
+
+Each request names an operation, a ring degree N = 2^logN and a limb count, and its
+ciphertext operands already live in HBM; evaluation keys are resident per ring degree.
+The server
+  * admits a request only while the HBM footprint of everything admitted and in flight
+    (operands, result and the batch's scratch share) stays under `budget_bytes`;
+  * keeps one queue per (operation, N, limbs) class and, whenever one of its CUDA streams is
+    free, launches up to `max_batch` queued requests of the class with the oldest request as
+    one batched library call on that stream;
+  * polls completion events, releases the footprint and records latencies.
+Requests that arrive while others run are admitted as memory frees and join the next
+batches (continuous batching); batches on different streams overlap on the GPU.
+All arithmetic runs in libfhe's kernels; batching changes only the batch dimension, so a
+request's result is identical alone and in any mix.
+"""
+import collections
+import time
+
+import torch
+
+from . import fhe
+
+HMULT, RESCALE, KEYSWITCH = "hmult", "rescale", "keyswitch"
+
+
+class Request:
+    __slots__ = ("rid", "kind", "logN", "nl", "arrival", "inputs", "out", "t_admit", "t_launch", "t_done",
+                 "footprint")
+
+    def __init__(self, rid, kind, logN, nl, arrival, inputs):
+        self.rid, self.kind, self.logN, self.nl, self.arrival = rid, kind, logN, nl, arrival
+        self.inputs = inputs  # HMULT: (a, b) each (2, nl, 1, N); RESCALE: (ct,); KEYSWITCH: (d2,) (nl, 1, N)
+        self.out = None
+        self.t_admit = self.t_launch = self.t_done = None
+        self.footprint = 0
+
+
+def _out_shape(kind, nl, batch, n):
+    if kind == HMULT or kind == RESCALE:
+        return (2, nl - 1, batch, n)
+    return (2, nl, batch, n)
+
+
+def _op_code(kind):
+    return {HMULT: fhe.FHE_OP_HMULT, RESCALE: fhe.FHE_OP_RESCALE, KEYSWITCH: fhe.FHE_OP_KEYSWITCH}[kind]
+
+
+class Server:
+    def __init__(self, contexts, evks, budget_bytes, n_streams=4, max_batch=16):
+        """contexts: {logN: fhe.Context}; evks: {logN: int32 CUDA tensor (dnum, 2, nq+np, N)}."""
+        self.ctx = contexts
+        self.evk = evks
+        self.budget = budget_bytes
+        self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
+        self.max_batch = max_batch
+
+    def footprint(self, r):
+        n = 1 << r.logN
+        ins = sum(t.numel() * 4 for t in r.inputs)
+        out = 4 * n
+        for d in _out_shape(r.kind, r.nl, 1, n)[:-1]:
+            out *= d
+        scratch = fhe.fhe_scratch_bytes(self.ctx[r.logN].handle, _op_code(r.kind), r.logN, r.nl, 1)
+        return ins + out + scratch
+
+    def _launch(self, reqs, stream):
+        r0 = reqs[0]
+        kind, logN, nl, n = r0.kind, r0.logN, r0.nl, 1 << r0.logN
+        ctx = self.ctx[logN]
+        bsz = len(reqs)
+        with torch.cuda.stream(stream):
+            if kind == KEYSWITCH:
+                ins = [torch.cat([r.inputs[0] for r in reqs], dim=1)]
+            else:
+                ins = [torch.cat([r.inputs[k] for r in reqs], dim=2) for k in range(len(r0.inputs))]
+            out = torch.empty(_out_shape(kind, nl, bsz, n), dtype=torch.int32, device="cuda")
+            nbytes = fhe.fhe_scratch_bytes(ctx.handle, _op_code(kind), logN, nl, bsz)
+            scratch = torch.empty(max(4, nbytes // 4 + 4), dtype=torch.int32, device="cuda")
+            sh = stream.cuda_stream
+            if kind == HMULT:
+                fhe.fhe_hmult(ctx.handle, logN, nl, bsz, ins[0].data_ptr(), ins[1].data_ptr(),
+                              self.evk[logN].data_ptr(), out.data_ptr(), scratch.data_ptr(), nbytes, sh)
+            elif kind == RESCALE:
+                fhe.fhe_rescale(ctx.handle, logN, nl, bsz, ins[0].data_ptr(), out.data_ptr(), scratch.data_ptr(),
+                                nbytes, sh)
+            else:
+                fhe.fhe_keyswitch(ctx.handle, logN, nl, bsz, ins[0].data_ptr(), self.evk[logN].data_ptr(),
+                                  out.data_ptr(), scratch.data_ptr(), nbytes, sh)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        for j, r in enumerate(reqs):
+            r.out = out[:, :, j:j + 1]
+        return {"reqs": reqs, "event": ev, "keep": (ins, out, scratch), "stream": stream}
+
+    def run(self, requests, clock=time.perf_counter):
+        """Serve `requests` (sorted by arrival, seconds from start) to completion.
+
+        Returns a dict of latency percentiles (ms), throughput and batch statistics.
+        """
+        pending = collections.OrderedDict()   # class -> deque of admitted requests
+        arrivals = collections.deque(requests)
+        inflight = []
+        used = 0
+        free_streams = list(self.streams)
+        batches = []
+        peak_used = 0
+        t0 = clock()
+        done = 0
+        n = len(requests)
+        while done < n:
+            now = clock() - t0
+            # admission by HBM footprint
+            while arrivals and arrivals[0].arrival <= now:
+                r = arrivals[0]
+                if not r.footprint:
+                    r.footprint = self.footprint(r)
+                if used + r.footprint > self.budget and (inflight or any(pending.values())):
+                    break
+                arrivals.popleft()
+                r.t_admit = now
+                used += r.footprint
+                peak_used = max(peak_used, used)
+                pending.setdefault((r.kind, r.logN, r.nl), collections.deque()).append(r)
+            # launch on free streams, oldest class first
+            while free_streams:
+                live = [(q[0].t_admit, key) for key, q in pending.items() if q]
+                if not live:
+                    break
+                _, key = min(live)
+                q = pending[key]
+                reqs = [q.popleft() for _ in range(min(self.max_batch, len(q)))]
+                for r in reqs:
+                    r.t_launch = now
+                inflight.append(self._launch(reqs, free_streams.pop()))
+                batches.append(len(reqs))
+            # completions
+            still = []
+            for b in inflight:
+                if b["event"].query():
+                    t = clock() - t0
+                    for r in b["reqs"]:
+                        r.t_done = t
+                        used -= r.footprint
+                    done += len(b["reqs"])
+                    free_streams.append(b["stream"])
+                else:
+                    still.append(b)
+            inflight = still
+        t_end = max(r.t_done for r in requests)
+        lat = sorted((r.t_done - r.arrival) * 1e3 for r in requests)
+
+        def pct(p):
+            return lat[min(len(lat) - 1, int(round(p / 100.0 * (len(lat) - 1))))]
+
+        return {"requests": n, "p50_ms": pct(50), "p99_ms": pct(99), "max_ms": lat[-1],
+                "throughput_kops": n / t_end / 1e3, "wall_s": t_end, "batches": len(batches),
+                "mean_batch": sum(batches) / max(1, len(batches)), "peak_footprint_bytes": peak_used,
+                "budget_bytes": self.budget, "streams": len(self.streams)}
+
+
+def poisson_requests(seed, n, rate_per_s, kinds, logNs, nl_range, make_inputs):
+    """n requests with exponential inter-arrival times (mean 1/rate); kind, ring degree and
+    limb count drawn uniformly. make_inputs(kind, logN, nl, rid) returns the operand tensors."""
+    import numpy as np
+    g = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for rid in range(n):
+        t += g.exponential(1.0 / rate_per_s)
+        kind = kinds[int(g.integers(0, len(kinds)))]
+        logN = int(logNs[int(g.integers(0, len(logNs)))])
+        nl = int(g.integers(nl_range[0], nl_range[1] + 1))
+        out.append(Request(rid, kind, logN, nl, t, make_inputs(kind, logN, nl, rid)))
+    return out

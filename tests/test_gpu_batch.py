@@ -1,0 +1,167 @@
+"""Operation-level batching: a plan of mixed NTT / INTT / HMULT operations of uneven ring
+degree and level gives exactly the results of the single-operation calls, eagerly and when
+replayed as one CUDA graph."""
+import numpy as np
+import pytest
+
+from oracle import ckks as C
+from oracle import ntt as ON
+from oracle import params as P
+from paper_2212_14191_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fhe():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2212_14191_gb300 import fhe as f
+    return f
+
+
+def make_ops(fhe, qs, ps, seed):
+    """Mixed list: NTT/INTT at N = 2^12..2^14 over varying limb ranges, HMULT at 2^12/2^13."""
+    import torch
+    g = np.random.default_rng(seed)
+    mods = qs + ps
+    ops, keep = [], []
+    evks = {}
+    for logn in (12, 13):
+        dnum = -(-len(qs) // 4)
+        evks[logn] = fhe.to_device(I.uniform_residues(seed + logn, mods, 2 * dnum, 1 << logn).reshape(
+            len(mods), dnum, 2, 1 << logn).transpose(1, 2, 0, 3).copy())
+    for i in range(14):
+        kind = [fhe.FHE_OPK_NTT_FWD, fhe.FHE_OPK_NTT_INV, fhe.FHE_OPK_HMULT][i % 3]
+        if kind == fhe.FHE_OPK_HMULT:
+            logn = int(g.choice([12, 13]))
+            nl, batch = int(g.integers(2, len(qs) + 1)), int(g.integers(1, 3))
+            n = 1 << logn
+            a = fhe.to_device(I.uniform_residues(seed + 100 + i, qs[:nl], 2 * batch, n).reshape(
+                nl, 2, batch, n).transpose(1, 0, 2, 3).copy())
+            b = fhe.to_device(I.uniform_residues(seed + 200 + i, qs[:nl], 2 * batch, n).reshape(
+                nl, 2, batch, n).transpose(1, 0, 2, 3).copy())
+            out = torch.empty((2, nl - 1, batch, n), dtype=torch.int32, device="cuda")
+            ops.append(fhe.FheOp(kind=kind, logN=logn, first_limb=0, n_limbs=nl, batch=batch,
+                                 a=a.data_ptr(), b=b.data_ptr(), evk=evks[logn].data_ptr(), out=out.data_ptr()))
+            keep.append(("hmult", logn, nl, batch, a, b, evks[logn], out))
+        else:
+            logn = int(g.choice([12, 13, 14]))
+            first = int(g.integers(0, len(mods) - 1))
+            nl = int(g.integers(1, len(mods) - first + 1))
+            batch = int(g.integers(1, 4))
+            x = I.uniform_residues(seed + 300 + i, mods[first:first + nl], batch, 1 << logn)
+            d = fhe.to_device(x)
+            ops.append(fhe.FheOp(kind=kind, logN=logn, first_limb=first, n_limbs=nl, batch=batch,
+                                 data=d.data_ptr()))
+            keep.append(("ntt", logn, first, nl, batch, d, x, kind))
+    return ops, keep
+
+
+def reference_results(fhe, ctx, keep):
+    import torch
+    res = []
+    for k in keep:
+        if k[0] == "hmult":
+            _, logn, nl, batch, a, b, evk, out = k
+            res.append(fhe.to_host(ctx.hmult(a, b, evk, logn)))
+        else:
+            _, logn, first, nl, batch, d, x, kind = k
+            t = fhe.to_device(x)
+            if kind == fhe.FHE_OPK_NTT_FWD:
+                ctx.ntt_fwd(t, logn, first_limb=first)
+            else:
+                ctx.ntt_inv(t, logn, first_limb=first)
+            res.append(fhe.to_host(t))
+    torch.cuda.synchronize()
+    return res
+
+
+def batch_results(fhe, keep):
+    return [fhe.to_host(k[7] if k[0] == "hmult" else k[5]) for k in keep]
+
+
+def reset_inputs(fhe, keep):
+    for k in keep:
+        if k[0] == "ntt":
+            k[5].copy_(fhe.to_device(k[6]))
+
+
+def test_batch_equals_single_calls(fhe):
+    import torch
+    qs, ps = P.default_moduli(8, 4)
+    ctx = fhe.Context(14, qs, ps, alpha=4)
+    ops, keep = make_ops(fhe, qs, ps, 7)
+    want = reference_results(fhe, ctx, keep)
+    plan = fhe.fhe_batch_create(ctx.handle, ops)
+    nbytes = fhe.fhe_batch_scratch_bytes(plan)
+    scratch = torch.empty(max(4, nbytes // 4 + 4), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    fhe.fhe_batch_run(plan, scratch.data_ptr(), nbytes, stream)
+    torch.cuda.synchronize()
+    got = batch_results(fhe, keep)
+    for w, g in zip(want, got):
+        assert (w == g).all()
+    # one NTT op against the oracle directly
+    for k, g in zip(keep, got):
+        if k[0] == "ntt" and k[7] == fhe.FHE_OPK_NTT_FWD:
+            _, logn, first, nl, batch, d, x, kind = k
+            mods = (qs + ps)[first:first + nl]
+            ref, _ = ON.ntt_batch(x, mods, [P.psi(m, 1 << logn) for m in mods])
+            assert (g == ref).all()
+            break
+    # graph capture and two replays
+    reset_inputs(fhe, keep)
+    fhe.fhe_batch_capture(plan, scratch.data_ptr(), nbytes)   # runs once, then captures
+    for _ in range(2):
+        reset_inputs(fhe, keep)
+        fhe.fhe_batch_launch(plan, stream)
+        torch.cuda.synchronize()
+        for w, g in zip(want, batch_results(fhe, keep)):
+            assert (w == g).all()
+    fhe.fhe_device_status(ctx.handle, 1)
+    fhe.fhe_batch_destroy(plan)
+    ctx.close()
+
+
+def test_batch_hmult_matches_oracle(fhe):
+    import torch
+    qs, ps = P.default_moduli(8, 4)
+    logn, n = 12, 1 << 12
+    prm = C.Params(n, qs, ps, alpha=4)
+    evk_h = I.uniform_residues(5, qs + ps, 2 * prm.dnum(8), n).reshape(12, prm.dnum(8), 2, n).transpose(1, 2, 0, 3).copy()
+    evk = fhe.to_device(evk_h)
+    ctx = fhe.Context(logn, qs, ps, alpha=4)
+    ops, cts = [], []
+    for i, nl in enumerate((3, 3, 6)):
+        a = I.uniform_residues(40 + i, qs[:nl], 2, n).reshape(nl, 2, 1, n).transpose(1, 0, 2, 3).copy()
+        b = I.uniform_residues(50 + i, qs[:nl], 2, n).reshape(nl, 2, 1, n).transpose(1, 0, 2, 3).copy()
+        da, db = fhe.to_device(a), fhe.to_device(b)
+        out = torch.empty((2, nl - 1, 1, n), dtype=torch.int32, device="cuda")
+        ops.append(fhe.FheOp(kind=fhe.FHE_OPK_HMULT, logN=logn, n_limbs=nl, batch=1, a=da.data_ptr(),
+                             b=db.data_ptr(), evk=evk.data_ptr(), out=out.data_ptr()))
+        cts.append((nl, a, b, da, db, out))
+    plan = fhe.fhe_batch_create(ctx.handle, ops)
+    nbytes = fhe.fhe_batch_scratch_bytes(plan)
+    scratch = torch.empty(nbytes // 4 + 4, dtype=torch.int32, device="cuda")
+    fhe.fhe_batch_run(plan, scratch.data_ptr(), nbytes, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    for nl, a, b, _, _, out in cts:
+        want = C.hmult(prm, nl, a[:, :, 0].astype(np.uint64), b[:, :, 0].astype(np.uint64), evk_h.astype(np.uint64))
+        assert (fhe.to_host(out)[:, :, 0] == want).all()
+    fhe.fhe_batch_destroy(plan)
+    ctx.close()
+
+
+def test_batch_rejects_bad_ops(fhe):
+    qs, ps = P.default_moduli(4, 2)
+    ctx = fhe.Context(12, qs, ps, alpha=2)
+    for op in (fhe.FheOp(kind=9, logN=12, n_limbs=1, batch=1, data=16),
+               fhe.FheOp(kind=fhe.FHE_OPK_NTT_FWD, logN=13, n_limbs=1, batch=1, data=16),
+               fhe.FheOp(kind=fhe.FHE_OPK_NTT_FWD, logN=12, first_limb=5, n_limbs=2, batch=1, data=16),
+               fhe.FheOp(kind=fhe.FHE_OPK_HMULT, logN=12, n_limbs=1, batch=1, a=16, b=16, evk=16, out=16)):
+        with pytest.raises(fhe.FheError) as e:
+            fhe.fhe_batch_create(ctx.handle, [op])
+        assert e.value.code == fhe.FHE_EINVAL
+    ctx.close()
