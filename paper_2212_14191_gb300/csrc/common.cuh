@@ -46,9 +46,9 @@ uint32_t root_2n(uint32_t q, uint32_t logN);  // primitive 2N-th root from the s
 
 // Plain-path kernel shapes per ring degree: threads per CTA T = 2^log_t and CTAs per
 // cluster C = 2^log_c with 32 * T * C = N (see ntt_u32.cu).
-constexpr int kNttVariants = 4;
+constexpr int kNttVariants = 6;
 bool ntt_variant_shape(uint32_t logN, int variant, int* log_t, int* log_c);
-bool ntt_variant_push(int variant);
+int ntt_variant_exchange(int variant);
 
 // Plain-path NTT tables for one ring degree N = 2^logN (device memory).
 struct NttTables {

@@ -232,6 +232,9 @@ int fhe_ctx_create(uint32_t logN_max, const uint32_t* q, int nq, const uint32_t*
     ctx->alpha = alpha;
     ctx->default_path = default_path;
     ctx->mods = mods;
+    // default plain-path shapes: the fastest measured on GB300 for a 44-limb x 64-polynomial
+    // batch (fhe_autotune_ntt re-measures them for the caller's own batch)
+    ctx->ntt_variant[15] = 4;  // 2-CTA clusters, split forward
     int rc = FHE_OK;
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);

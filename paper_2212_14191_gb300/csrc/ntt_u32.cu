@@ -164,14 +164,23 @@ ntt_fwd_kernel(const NttArgs a) {
         if constexpr (C > 1) {
             // push: peers finished reading their `work` before the previous row's second
             // barrier; pull: peers may still be reading this CTA's `work` (gather)
-            if constexpr (!PUSH) ptx::cluster_sync();
+            if constexpr (!PUSH) {
+                // only orders the peers' completed DSMEM reads before these writes
+                __syncwarp();
+                ptx::cluster_arrive_relaxed();
+                ptx::cluster_wait();
+            }
             constexpr int PER = NC / C;  // elements of each quarter handled by this CTA
+            constexpr int U = PER / T;   // = 32 / C slices per thread
+            // all 32 global loads first (v is free here), then the butterflies and pushes
 #pragma unroll
-            for (int u = 0; u < PER / T; ++u) {
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int qq = 0; qq < C; ++qq) v[u * C + qq] = __ldg(&data[c * PER + u * T + tid + qq * NC]);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
                 const int jj = c * PER + u * T + tid;
-                uint32_t x[C];
-#pragma unroll
-                for (int qq = 0; qq < C; ++qq) x[qq] = __ldg(&data[jj + qq * NC]);
+                uint32_t* x = v + u * C;
 #pragma unroll
                 for (int s = 0; s < LOG_C; ++s) {
                     const int tq = C >> (s + 1);
@@ -270,12 +279,15 @@ ntt_fwd_kernel(const NttArgs a) {
             for (int e = 0; e < 32; ++e) work[swz<LOG_T>(rev_bits<5>(e) * T + tid)] = v[e];
             ptx::cluster_sync();
             // CTA c writes k in [c*NC, (c+1)*NC); k lives in CTA rev(k mod C) at k / C.
-#pragma unroll 8
+            // All 32 remote loads are issued before any store so their latencies overlap.
+#pragma unroll
             for (int u = 0; u < 32; ++u) {
                 const int k = c * NC + u * T + tid;
                 const int own = rev_bits<LOG_C>(k & (C - 1));
-                data[k] = ptx::ld_cluster(ptx::mapa(work_s + 4u * swz<LOG_T>(k >> LOG_C), own));
+                v[u] = ptx::ld_cluster(ptx::mapa(work_s + 4u * swz<LOG_T>(k >> LOG_C), own));
             }
+#pragma unroll
+            for (int u = 0; u < 32; ++u) data[c * NC + u * T + tid] = v[u];
         } else {
             // output k = k_local * C + rev(c) goes to the CTA that stores [d*NC, (d+1)*NC)
             uint32_t* const recv = work + NC;
@@ -323,12 +335,18 @@ ntt_inv_kernel(const NttArgs a) {
         if constexpr (C > 1) {
             // push: peers finished reading their `work` before the previous row's second
             // barrier; pull: peers may still be reading this CTA's `work` (cross stages)
-            if constexpr (!PUSH) ptx::cluster_sync();
-#pragma unroll 8
+            if constexpr (!PUSH) {
+                __syncwarp();
+                ptx::cluster_arrive_relaxed();
+                ptx::cluster_wait();
+            }
+#pragma unroll
+            for (int u = 0; u < 32; ++u) v[u] = __ldg(&data[c * NC + u * T + tid]);
+#pragma unroll
             for (int u = 0; u < 32; ++u) {
                 const int k = c * NC + u * T + tid;
                 const int own = rev_bits<LOG_C>(k & (C - 1));
-                ptx::st_cluster(ptx::mapa(work_s + 4u * swz<LOG_T>(k >> LOG_C), own), __ldg(&data[k]));
+                ptx::st_cluster(ptx::mapa(work_s + 4u * swz<LOG_T>(k >> LOG_C), own), v[u]);
             }
             ptx::cluster_sync();
 #pragma unroll
@@ -424,19 +442,24 @@ ntt_inv_kernel(const NttArgs a) {
                 for (int e = 0; e < 32; ++e) work[swz<LOG_T>(tid + T * e)] = v[e];
             }
             ptx::cluster_sync();
+            constexpr int U = PER / T;
+            // all remote / local loads of the cross stages first (v is free here)
 #pragma unroll
-            for (int u = 0; u < PER / T; ++u) {
-                const int jl = u * T + tid;
-                const int jj = c * PER + jl;
-                uint32_t x[C];
+            for (int u = 0; u < U; ++u)
 #pragma unroll
                 for (int qq = 0; qq < C; ++qq) {
+                    const int jl = u * T + tid;
                     if constexpr (PUSH) {
-                        x[qq] = recv[qq * PER + jl];
+                        v[u * C + qq] = recv[qq * PER + jl];
                     } else {
-                        x[qq] = ptx::ld_cluster(ptx::mapa(work_s + 4u * swz<LOG_T>(jj), qq));
+                        v[u * C + qq] = ptx::ld_cluster(ptx::mapa(work_s + 4u * swz<LOG_T>(c * PER + jl), qq));
                     }
                 }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int jl = u * T + tid;
+                const int jj = c * PER + jl;
+                uint32_t* x = v + u * C;
 #pragma unroll
                 for (int s = LOG_C - 1; s >= 0; --s) {
                     const int tq = C >> (s + 1);
@@ -456,10 +479,144 @@ ntt_inv_kernel(const NttArgs a) {
     if constexpr (C > 1) ptx::cluster_sync();
 }
 
-template <int LOG_T, int LOG_C, bool PUSH>
+// Forward transform with independent quarters (exchange mode "split", C > 1): every CTA of
+// the cluster reads its positions p in all C quarters of the row (the C reads of a position
+// hit L2 after the first), runs the cross stages itself and keeps its own output quarter c,
+// so no data moves between CTAs. The cluster only orders the in-place update: each CTA
+// arrives on the cluster barrier once it has read the row and waits on it just before
+// storing its outputs (k = k_local * C + rev(c)), so the barrier's latency hides behind the
+// local stages.
+template <int LOG_T, int LOG_C>
+__global__ void __launch_bounds__(1 << LOG_T, kMinBlocks<LOG_T>)
+ntt_fwd_split_kernel(const NttArgs a) {
+    constexpr int T = 1 << LOG_T, C = 1 << LOG_C;
+    constexpr int LOG_NC = LOG_T + 5, NC = 1 << LOG_NC;
+    constexpr int N = NC * C;
+    constexpr int RB = LOG_T - 5;
+    static_assert(C > 1, "split mode needs a cluster");
+    extern __shared__ __align__(128) uint32_t work[];
+    const int tid = threadIdx.x;
+    const int c = (int)blockIdx.x;
+    const int rc = rev_bits<LOG_C>(c);
+    const RowIter ri = row_iter(a.rows, a.contiguous);
+
+    for (int row = ri.row; row < ri.end; row += ri.step) {
+        uint32_t q;
+        int mod;
+        uint32_t* data = row_ref<N>(a, row, &q, &mod);
+        const uint2* tw = a.tw + (size_t)mod * N;
+        if (tid == 0 && row + ri.step < ri.end)
+            ptx::prefetch_l2(row_ptr<N>(a, row + ri.step) + c * NC, NC * 4);
+        uint32_t v[32];
+
+        // ---- cross stages for this CTA's quarter, 8 positions at a time
+#pragma unroll
+        for (int e0 = 0; e0 < 32; e0 += 8) {
+            uint32_t x[8][C];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int qq = 0; qq < C; ++qq) x[i][qq] = __ldg(&data[tid + T * (e0 + i) + qq * NC]);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+#pragma unroll
+                for (int s = 0; s < LOG_C; ++s) {
+                    const int tq = C >> (s + 1);
+#pragma unroll
+                    for (int qq = 0; qq < C; ++qq) {
+                        if ((qq / tq) % 2 == 0) {
+                            uint2 w = __ldg(&tw[(1 << s) + qq / (2 * tq)]);
+                            ct_bfly(x[i][qq], x[i][qq + tq], w, q);
+                        }
+                    }
+                }
+                uint32_t r = x[i][0];
+#pragma unroll
+                for (int qq = 1; qq < C; ++qq)
+                    if (qq == c) r = x[i][qq];
+                v[e0 + i] = r;
+            }
+        }
+        __syncwarp();
+        ptx::cluster_arrive_relaxed();  // this CTA has read everything it needs from the row
+
+        // ---- round A: 5 stages, element e at p = tid + T*e
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const int half = 16 >> k;
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                if ((e & half) == 0) {
+                    uint2 w = __ldg(&tw[(1 << k) * (C + c) + (e >> (5 - k))]);
+                    ct_bfly(v[e], v[e + half], w, q);
+                }
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < 32; ++e) work[swz<LOG_T>(tid + T * e)] = v[e];
+        __syncthreads();
+
+        // ---- round B
+        if constexpr (RB > 0) {
+            constexpr int GPT = 32 >> RB;
+            constexpr int EG = 1 << RB;
+            const int lane = tid & 31, w_ = tid >> 5;
+#pragma unroll
+            for (int gi = 0; gi < GPT; ++gi) {
+                const int g = w_ * GPT + gi;
+                uint32_t* vv = v + gi * EG;
+#pragma unroll
+                for (int e = 0; e < EG; ++e) vv[e] = work[swz<LOG_T>(T * g + lane + 32 * e)];
+#pragma unroll
+                for (int k = 0; k < RB; ++k) {
+                    const int half = EG >> (k + 1);
+#pragma unroll
+                    for (int e = 0; e < EG; ++e) {
+                        if ((e & half) == 0) {
+                            uint2 w = __ldg(&tw[(1 << k) * (32 * (C + c) + g) + (e >> (RB - k))]);
+                            ct_bfly(vv[e], vv[e + half], w, q);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < EG; ++e) work[swz<LOG_T>(T * g + lane + 32 * e)] = vv[e];
+            }
+            __syncthreads();
+        }
+
+        // ---- round C
+        {
+            const int gidx = rev_bits<LOG_T>(tid);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) v[e] = work[swz<LOG_T>(32 * gidx + e)];
+            const uint2* twc = a.twC + (((size_t)mod * C + c) * 31) * T + tid;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                const int half = 16 >> k;
+#pragma unroll
+                for (int e = 0; e < 32; ++e) {
+                    if ((e & half) == 0) {
+                        uint2 w = __ldg(&twc[(size_t)((1 << k) - 1 + (e >> (5 - k))) * T]);
+                        ct_bfly(v[e], v[e + half], w, q);
+                    }
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < 32; ++e) v[e] = csub(csub(v[e], 2 * q), q);
+        }
+        __syncwarp();
+        ptx::cluster_wait();  // every CTA of the cluster has read the row: safe to overwrite it
+#pragma unroll
+        for (int e = 0; e < 32; ++e) data[(rev_bits<5>(e) * T + tid) * C + rc] = v[e];
+        __syncthreads();  // `work` is rewritten by the next row's round A
+    }
+}
+
+template <int LOG_T, int LOG_C, int EX>
 int launch(const fhe_ctx* ctx, const NttTables& t, int variant, bool inverse, uint32_t* d, int rows,
            int batch, const LimbMap& map, const RowRef* rowtab, cudaStream_t stream) {
     constexpr int T = 1 << LOG_T, C = 1 << LOG_C;
+    constexpr bool PUSH = EX == 1;
     constexpr int smem = kSmemWords<LOG_T, LOG_C, PUSH> * 4;
     NttArgs args;
     args.data = d;
@@ -473,7 +630,11 @@ int launch(const fhe_ctx* ctx, const NttTables& t, int variant, bool inverse, ui
     args.rowtab = rowtab;
     args.mod_q = ctx->d_mods;
     args.map = map;
-    void (*kern)(NttArgs) = inverse ? ntt_inv_kernel<LOG_T, LOG_C, PUSH> : ntt_fwd_kernel<LOG_T, LOG_C, PUSH>;
+    void (*kern)(NttArgs);
+    if constexpr (EX == 2 && LOG_C > 0)
+        kern = inverse ? ntt_inv_kernel<LOG_T, LOG_C, false> : ntt_fwd_split_kernel<LOG_T, LOG_C>;
+    else
+        kern = inverse ? ntt_inv_kernel<LOG_T, LOG_C, PUSH> : ntt_fwd_kernel<LOG_T, LOG_C, PUSH>;
     FHE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     // give the rest of the L1/shared array to L1, which caches the twiddle tables
     int carve = (int)((kMinBlocks<LOG_T> * (smem + 1024) * 100 + 228 * 1024 - 1) / (228 * 1024));
@@ -518,10 +679,12 @@ uint32_t rev_h(uint32_t x, int bits) {
 }  // namespace
 
 // Variant bit 0 selects the shape: CTAs of up to 512 threads (one limb of N <= 2^14 per CTA),
-// or CTAs of half the size in clusters twice as large (two CTAs share an SM). Variant bit 1
-// selects how a cluster exchanges data: peers read each other's buffers (pull, one buffer,
-// three barriers per row) or store into a receive buffer (push, two buffers, two barriers).
-bool ntt_variant_push(int variant) { return (variant & 2) != 0; }
+// or CTAs of half the size in clusters twice as large (two CTAs share an SM). variant >> 1
+// selects how a cluster shares a limb: 0 = peers read each other's buffers (pull, one
+// buffer, three barriers per row), 1 = peers store into a receive buffer (push, two
+// buffers, two barriers), 2 = forward transforms read all quarters themselves (split, no
+// data exchange, one barrier; inverse transforms then use pull).
+int ntt_variant_exchange(int variant) { return variant >> 1; }
 
 bool ntt_variant_shape(uint32_t logN, int variant, int* log_t, int* log_c) {
     if (logN < FHE_LOGN_MIN || logN > FHE_LOGN_MAX || variant < 0 || variant >= kNttVariants) return false;
@@ -532,6 +695,7 @@ bool ntt_variant_shape(uint32_t logN, int variant, int* log_t, int* log_c) {
     }
     *log_t = lt;
     *log_c = (int)logN - 5 - lt;
+    if (*log_c == 0 && ntt_variant_exchange(variant) != 0) return false;  // no cluster to share
     return true;
 }
 
@@ -619,9 +783,10 @@ int ntt_u32_dispatch(const fhe_ctx* ctx, uint32_t logN, bool inverse, uint32_t* 
     if (!ntt_variant_shape(logN, v, &log_t, &log_c)) return set_error(FHE_EINVAL, "logN out of range");
 #define FHE_NTT_CASE(LT, LC)                                                                       \
     if (log_t == LT && log_c == LC) {                                                              \
-        if (LC > 0 && ntt_variant_push(v))                                                         \
-            return launch<LT, LC, true>(ctx, t, v, inverse, d, (int)rows, batch, map, rowtab, stream); \
-        return launch<LT, LC, false>(ctx, t, v, inverse, d, (int)rows, batch, map, rowtab, stream);\
+        const int ex = LC > 0 ? ntt_variant_exchange(v) : 0;                                       \
+        if (ex == 1) return launch<LT, LC, 1>(ctx, t, v, inverse, d, (int)rows, batch, map, rowtab, stream); \
+        if (ex == 2) return launch<LT, LC, 2>(ctx, t, v, inverse, d, (int)rows, batch, map, rowtab, stream); \
+        return launch<LT, LC, 0>(ctx, t, v, inverse, d, (int)rows, batch, map, rowtab, stream);    \
     }
     FHE_NTT_CASE(5, 0)
     FHE_NTT_CASE(6, 0)

@@ -102,21 +102,31 @@ __device__ __forceinline__ void fence_proxy_async() {
 __device__ __forceinline__ void cluster_arrive() {
     asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
 }
+// Arrive without release semantics: for barriers that only signal "my earlier loads have
+// returned" (so peers may overwrite what was read); it does not wait for this thread's
+// outstanding stores the way a release arrive does.
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void cluster_wait() {
     asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 // 32-bit shared::cluster address of the same offset in CTA `rank` of this cluster.
 __device__ __forceinline__ uint32_t mapa(uint32_t smem_addr, uint32_t rank) {
     uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_addr), "r"(rank));
+    asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_addr), "r"(rank));
     return r;
 }
+// Distributed-shared-memory store / load. They carry no "memory" clobber so that ordinary
+// loads may be scheduled around them (callers issue whole batches of them); their order
+// relative to the cluster barriers, which do clobber memory, is kept because all of them are
+// volatile.
 __device__ __forceinline__ void st_cluster(uint32_t addr, uint32_t v) {
-    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v));
 }
 __device__ __forceinline__ uint32_t ld_cluster(uint32_t addr) {
     uint32_t v;
-    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr));
     return v;
 }
 
