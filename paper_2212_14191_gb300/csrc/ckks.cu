@@ -86,34 +86,33 @@ struct ConvArgs {
     size_t L4;  // residues per limb / 4
 };
 
+// NS = number of source limbs (a compile-time constant so no issue slot is spent on
+// predicated-off source terms).
+template <int NS>
 __global__ void __launch_bounds__(256) k_conv(const ConvArgs a) {
     extern __shared__ uint32_t s_hat[];  // [nsrc][ndst]
-    for (int k = threadIdx.x; k < a.nsrc * a.ndst; k += blockDim.x) {
+    for (int k = threadIdx.x; k < NS * a.ndst; k += blockDim.x) {
         int i = k / a.ndst, t = k % a.ndst;
         s_hat[k] = a.hat_mod[(size_t)i * a.nmod + a.dst_mod[t]];
     }
     __syncthreads();
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < a.L4; n += (size_t)gridDim.x * blockDim.x) {
-        uint4 y[16];
+        uint4 y[NS];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            if (i < a.nsrc) {
-                uint4 x = ld4(a.src, i * (a.src_stride / 4) + n);
-                const uint32_t b = a.src_q[i];
-                const uint2 h = a.hat_inv[i];
+        for (int i = 0; i < NS; ++i) {
+            uint4 x = ld4(a.src, i * (a.src_stride / 4) + n);
+            const uint32_t b = a.src_q[i];
+            const uint2 h = a.hat_inv[i];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) set(y[i], k, mul_shoup(get(x, k), h.x, h.y, b));
-            }
+            for (int k = 0; k < 4; ++k) set(y[i], k, mul_shoup(get(x, k), h.x, h.y, b));
         }
         for (int t = 0; t < a.ndst; ++t) {
             uint64_t acc[4] = {0, 0, 0, 0};
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                if (i < a.nsrc) {
-                    const uint64_t h = s_hat[i * a.ndst + t];
+            for (int i = 0; i < NS; ++i) {
+                const uint64_t h = s_hat[i * a.ndst + t];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) acc[k] += (uint64_t)get(y[i], k) * h;
-                }
+                for (int k = 0; k < 4; ++k) acc[k] += (uint64_t)get(y[i], k) * h;
             }
             uint4 r;
             const uint32_t qt = a.dm.q[t];
@@ -123,6 +122,20 @@ __global__ void __launch_bounds__(256) k_conv(const ConvArgs a) {
             st4(a.dst, t * (a.dst_stride / 4) + n, r);
         }
     }
+}
+
+int launch_conv(const ConvArgs& ca, dim3 grid, size_t smem, cudaStream_t st) {
+    switch (ca.nsrc) {
+#define FHE_CONV_CASE(K) \
+    case K: k_conv<K><<<grid, 256, smem, st>>>(ca); break;
+        FHE_CONV_CASE(1) FHE_CONV_CASE(2) FHE_CONV_CASE(3) FHE_CONV_CASE(4) FHE_CONV_CASE(5)
+        FHE_CONV_CASE(6) FHE_CONV_CASE(7) FHE_CONV_CASE(8) FHE_CONV_CASE(9) FHE_CONV_CASE(10)
+        FHE_CONV_CASE(11) FHE_CONV_CASE(12) FHE_CONV_CASE(13) FHE_CONV_CASE(14) FHE_CONV_CASE(15)
+#undef FHE_CONV_CASE
+        default: return set_error(FHE_EINVAL, "Conv source count out of [1, 15]");
+    }
+    FHE_CUDA_TRY(cudaGetLastError());
+    return FHE_OK;
 }
 
 // ---- KS-4: inner product with the evaluation key (Hada-Mult + Ele-Add), all slices at once:
@@ -243,6 +256,53 @@ __global__ void k_rescale_final(const uint32_t* __restrict__ ct, const uint32_t*
     }
 }
 
+// ---- HMULT tail, fused: the relinearised result (d_c + (ks_c - y_c) P^-1) is formed only
+// for the last limb (it feeds the rescale's INTT) and, for the other limbs, directly inside
+// the rescale's final step, so the relinearised ciphertext is never written out.
+// last_c = d_c[l] + (ks_c[l] - y_c[l]) [P^-1]_{q_l}, both components, limb l = nl - 1
+__global__ void k_relin_last(const uint32_t* __restrict__ d, const uint32_t* __restrict__ ks,
+                             const uint32_t* __restrict__ y, uint32_t* __restrict__ last, uint2 pinv, uint32_t q,
+                             int nl, int ext, size_t L4) {
+    const int c = blockIdx.y, l = nl - 1;
+    const uint32_t* dp = d + ((size_t)c * nl + l) * L4 * 4;
+    const uint32_t* kp = ks + ((size_t)c * ext + l) * L4 * 4;
+    const uint32_t* yp = y + ((size_t)c * nl + l) * L4 * 4;
+    uint32_t* op = last + (size_t)c * L4 * 4;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < L4; n += (size_t)gridDim.x * blockDim.x) {
+        uint4 dv = ld4(dp, n), kv = ld4(kp, n), yv = ld4(yp, n), r;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            set(r, k, csub(mul_shoup(get(kv, k) + q - get(yv, k), pinv.x, pinv.y, q) + get(dv, k), q));
+        st4(op, n, r);
+    }
+}
+
+// out_c[i] = ((d_c[i] + (ks_c[i] - y_c[i]) [P^-1]_{q_i}) - xb_c[i]) [q_l^-1]_{q_i},  i < nl - 1
+__global__ void k_hmult_final(const uint32_t* __restrict__ d, const uint32_t* __restrict__ ks,
+                              const uint32_t* __restrict__ y, const uint32_t* __restrict__ xb,
+                              uint32_t* __restrict__ out, const uint2* __restrict__ pinv,
+                              const uint2* __restrict__ qlinv, int nl, int ext, size_t L4, ModVec m) {
+    const int nout = nl - 1;
+    const int c = blockIdx.y / nout, i = blockIdx.y % nout;
+    const uint32_t q = m.q[i];
+    const uint2 pi = __ldg(&pinv[i]), qi = __ldg(&qlinv[i]);
+    const size_t limb = L4 * 4;
+    const uint32_t* dp = d + ((size_t)c * nl + i) * limb;
+    const uint32_t* kp = ks + ((size_t)c * ext + i) * limb;
+    const uint32_t* yp = y + ((size_t)c * nl + i) * limb;
+    const uint32_t* xp = xb + ((size_t)c * nout + i) * limb;
+    uint32_t* op = out + ((size_t)c * nout + i) * limb;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < L4; n += (size_t)gridDim.x * blockDim.x) {
+        uint4 dv = ld4(dp, n), kv = ld4(kp, n), yv = ld4(yp, n), xv = ld4(xp, n), r;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t rel = csub(mul_shoup(get(kv, k) + q - get(yv, k), pi.x, pi.y, q) + get(dv, k), q);
+            set(r, k, mul_shoup(rel + q - get(xv, k), qi.x, qi.y, q));
+        }
+        st4(op, n, r);
+    }
+}
+
 // ------------------------------------------------------------------ host orchestration
 
 dim3 stream_grid(const fhe_ctx* ctx, size_t L4, int limbs) {
@@ -314,8 +374,7 @@ int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const u
         size_t smem = (size_t)ca.nsrc * nd * 4;
         dim3 g = stream_grid(ctx, L4, 1);
         g.x = std::min<unsigned>(g.x * 4, (unsigned)((L4 + 255) / 256));
-        k_conv<<<g, 256, smem, st>>>(ca);
-        FHE_CUDA_TRY(cudaGetLastError());
+        if ((rc = launch_conv(ca, g, smem, st))) return rc;
         // KS-3: NTT of the converted limbs
         LimbMap lm;
         for (int t = 0; t < nd; ++t) {
@@ -371,8 +430,7 @@ int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const u
         ca.L4 = L4;
         dim3 g = stream_grid(ctx, L4, 1);
         g.x = std::min<unsigned>(g.x * 4, (unsigned)((L4 + 255) / 256));
-        k_conv<<<g, 256, (size_t)K * nl * 4, st>>>(ca);
-        FHE_CUDA_TRY(cudaGetLastError());
+        if ((rc = launch_conv(ca, g, (size_t)K * nl * 4, st))) return rc;
     }
     if (2 * nl > kMaxLimbs) return set_error(FHE_EINVAL, "too many limbs");
     LimbMap qm2;
@@ -384,6 +442,7 @@ int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const u
     if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, false, y, 2 * nl, batch, qm2, st))) return rc;
     int qidx[kMaxLimbs];
     for (int i = 0; i < nl; ++i) qidx[i] = i;
+    if (out == nullptr) return FHE_OK;  // the caller fuses the ModDown combine (see hmult_fused)
     k_moddown_combine<<<stream_grid(ctx, L4, 2 * nl), 256, 0, st>>>(ks, y, out, ctx->p_inv, nl, ext, accumulate,
                                                                   L4, modvec(ctx, qidx, nl));
     FHE_CUDA_TRY(cudaGetLastError());
@@ -437,6 +496,55 @@ int hmult_relin_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const
     return keyswitch_impl(ctx, logN, nl, batch, d2, evk, out, 1, ks_scratch, true, st);
 }
 
+// HMULT + RESCALE with the fused tail. Scratch: relin-d (2 nl limbs: d0, d1), d2 (nl), then
+// the key-switching scratch (d2c, ModUp outputs, ks, y); after the inner product the d2c /
+// ModUp region is reused for the rescale's last limb and broadcast (2 + 2 (nl - 1) limbs,
+// which fit: nl + dnum (nl + K) >= 2 nl).
+int hmult_fused(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint32_t* a, const uint32_t* b,
+                const uint32_t* evk, uint32_t* out, uint32_t* scratch, cudaStream_t st) {
+    const size_t N = 1ull << logN, limb = N * batch, L4 = limb / 4;
+    const int K = ctx->np, ext = nl + K, alpha = ctx->alpha;
+    const int dnum = (nl + alpha - 1) / alpha;
+    uint32_t* dd = scratch;                       // (2, nl): d0, d1
+    uint32_t* d2 = dd + 2 * (size_t)nl * limb;    // (nl)
+    uint32_t* ksx = d2 + (size_t)nl * limb;       // key-switching scratch, begins with d2c
+    uint32_t* ks = ksx + ((size_t)nl + (size_t)dnum * ext) * limb;
+    uint32_t* y = ks + 2 * (size_t)ext * limb;
+    uint32_t* last = ksx;                         // reuses d2c / ModUp space
+    uint32_t* xb = last + 2 * limb;
+    int qidx[kMaxLimbs];
+    for (int i = 0; i < nl; ++i) qidx[i] = i;
+    k_tensor<<<stream_grid(ctx, L4, nl), 256, 0, st>>>(a, b, dd, dd + (size_t)nl * limb, d2, ksx, L4,
+                                                     (size_t)nl * L4, modvec(ctx, qidx, nl));
+    FHE_CUDA_TRY(cudaGetLastError());
+    int rc = keyswitch_impl(ctx, logN, nl, batch, d2, evk, nullptr, 0, ksx, true, st);
+    if (rc) return rc;
+    const uint32_t ql = ctx->mods[nl - 1];
+    const uint2 pinv_l = ctx->p_inv_h[nl - 1];
+    k_relin_last<<<stream_grid(ctx, L4, 2), 256, 0, st>>>(dd, ks, y, last, pinv_l, ql, nl, ext, L4);
+    FHE_CUDA_TRY(cudaGetLastError());
+    LimbMap lm;
+    lm.mod[0] = lm.mod[1] = (uint8_t)(nl - 1);
+    lm.q[0] = lm.q[1] = ql;
+    if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, true, last, 2, batch, lm, st))) return rc;
+    const int nout = nl - 1;
+    ModVec qm = modvec(ctx, qidx, nout);
+    k_rescale_broadcast<<<stream_grid(ctx, L4, 2 * nout), 256, 0, st>>>(last, xb, ql, nout, L4, qm);
+    FHE_CUDA_TRY(cudaGetLastError());
+    LimbMap qm2;
+    for (int c = 0; c < 2; ++c)
+        for (int i = 0; i < nout && i < FHE_MAX_MODULI; ++i) {
+            qm2.mod[c * nout + i] = (uint8_t)i;
+            qm2.q[c * nout + i] = ctx->mods[i];
+        }
+    if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, false, xb, 2 * nout, batch, qm2, st))) return rc;
+    k_hmult_final<<<stream_grid(ctx, L4, 2 * nout), 256, 0, st>>>(dd, ks, y, xb, out, ctx->p_inv,
+                                                                ctx->ql_inv + (size_t)(nl - 1) * ctx->nq, nl, ext,
+                                                                L4, qm);
+    FHE_CUDA_TRY(cudaGetLastError());
+    return FHE_OK;
+}
+
 bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 int check_ckks(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, int min_nl) {
@@ -459,8 +567,7 @@ size_t scratch_limbs(const fhe_ctx* ctx, int op, int nl) {
         case FHE_OP_KEYSWITCH: return ks_scratch_limbs(nl, K, ctx->alpha);
         case FHE_OP_HMULT_RELIN: return (size_t)nl + ks_scratch_limbs(nl, K, ctx->alpha);
         case FHE_OP_RESCALE: return rescale_scratch_limbs(nl);
-        case FHE_OP_HMULT:
-            return 2 * (size_t)nl + std::max((size_t)nl + ks_scratch_limbs(nl, K, ctx->alpha), rescale_scratch_limbs(nl));
+        case FHE_OP_HMULT: return 2 * (size_t)nl + (size_t)nl + ks_scratch_limbs(nl, K, ctx->alpha);
         default: return 0;
     }
 }
@@ -521,12 +628,7 @@ int fhe_hmult(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const u
     if ((rc = check_ptrs({ct_a, ct_b, evk, ct_out, scratch}))) return rc;
     if (scratch_bytes < fhe_scratch_bytes(ctx, FHE_OP_HMULT, logN, n_limbs, batch))
         return set_error(FHE_ENOMEM, "scratch too small");
-    const size_t limb = (size_t)batch << logN;
-    uint32_t* relin = (uint32_t*)scratch;
-    uint32_t* rest = relin + 2 * (size_t)n_limbs * limb;
-    cudaStream_t st = (cudaStream_t)stream;
-    if ((rc = hmult_relin_impl(ctx, logN, n_limbs, batch, ct_a, ct_b, evk, relin, rest, st))) return rc;
-    return rescale_impl(ctx, logN, n_limbs, batch, relin, ct_out, rest, st);
+    return hmult_fused(ctx, logN, n_limbs, batch, ct_a, ct_b, evk, ct_out, (uint32_t*)scratch, (cudaStream_t)stream);
 }
 
 }  // extern "C"

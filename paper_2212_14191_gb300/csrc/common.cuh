@@ -94,6 +94,7 @@ struct fhe_ctx {
     std::vector<std::vector<fhe::ConvTable>> modup;
     fhe::ConvTable moddown;
     uint2* p_inv = nullptr;        // [nq]  ([P^-1]_{q_i}, shoup)
+    std::vector<uint2> p_inv_h;    // host copy of p_inv
     uint2* ql_inv = nullptr;       // [nq][nq]  row l: ([q_l^-1]_{q_i}, shoup)
     std::vector<void*> allocations;
     int device = 0;

@@ -145,6 +145,7 @@ static int build_ckks_tables(fhe_ctx* ctx) {
             uint32_t inv = (i == l) ? 0 : invmod_h(ctx->mods[l] % qi, qi);
             qlinv[(size_t)l * nq + i] = make_uint2(inv, shoup_h(inv, qi));
         }
+    ctx->p_inv_h = pinv;
     if ((rc = dev_upload(ctx, &ctx->p_inv, pinv))) return rc;
     if ((rc = dev_upload(ctx, &ctx->ql_inv, qlinv))) return rc;
     return FHE_OK;
