@@ -46,7 +46,8 @@ uint32_t root_2n(uint32_t q, uint32_t logN);  // primitive 2N-th root from the s
 
 // Plain-path kernel shapes per ring degree: threads per CTA T = 2^log_t and CTAs per
 // cluster C = 2^log_c with 32 * T * C = N (see ntt_u32.cu).
-constexpr int kNttVariants = 6;
+constexpr int kNttVariants = 8;
+constexpr size_t kNttTempBytes = 64ull << 20;
 bool ntt_variant_shape(uint32_t logN, int variant, int* log_t, int* log_c);
 int ntt_variant_exchange(int variant);
 
@@ -101,6 +102,7 @@ struct fhe_ctx {
     int num_sms = 0;
     int* d_status = nullptr;  // device error word written by kernels (FHE_ETIMEOUT, ...)
     void* tc_planes[2] = {};  // tensor-core path scratch: 8-bit digit planes of two operands
+    uint32_t* ntt_temp = nullptr;  // two-pass plain NTT scratch (kNttTempBytes, stays in L2)
     uint32_t* d_mods = nullptr;  // device copy of `mods`
 };
 
@@ -125,6 +127,10 @@ struct RowRef {
 // that live in different buffers).
 int ntt_u32_rows(const fhe_ctx* ctx, uint32_t logN, bool inverse, const RowRef* d_rows, int nrows,
                  cudaStream_t stream);
+
+// Plain-path NTT for N >= 2^15 in two passes through an L2-resident scratch (ntt_u32_l2.cu).
+int ntt_u32_l2(const fhe_ctx* ctx, uint32_t logN, int shape, bool inverse, uint32_t* d, int rows, int batch,
+               const LimbMap& map, const RowRef* rowtab, cudaStream_t st);
 
 // Plain-path batched NTT over `n_limbs` limbs whose moduli are map.mod[l].
 int ntt_u32(const fhe_ctx* ctx, uint32_t logN, bool inverse, uint32_t* d, int n_limbs,

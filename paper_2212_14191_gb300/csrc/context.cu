@@ -248,6 +248,7 @@ int fhe_ctx_create(uint32_t logN_max, const uint32_t* q, int nq, const uint32_t*
         }
     }
     if (rc == FHE_OK) rc = dev_upload(ctx, &ctx->d_mods, ctx->mods);
+    if (rc == FHE_OK && logN_max >= 15) rc = dev_alloc(ctx, &ctx->ntt_temp, kNttTempBytes / 4);
     for (uint32_t lg = FHE_LOGN_MIN; rc == FHE_OK && lg <= logN_max; ++lg) rc = build_ntt_tables(ctx, lg);
     if (rc == FHE_OK && np > 0) rc = build_ckks_tables(ctx);
     if (rc == FHE_OK && default_path == FHE_NTT_TC) {

@@ -683,7 +683,8 @@ uint32_t rev_h(uint32_t x, int bits) {
 // selects how a cluster shares a limb: 0 = peers read each other's buffers (pull, one
 // buffer, three barriers per row), 1 = peers store into a receive buffer (push, two
 // buffers, two barriers), 2 = forward transforms read all quarters themselves (split, no
-// data exchange, one barrier; inverse transforms then use pull).
+// data exchange, one barrier; inverse transforms then use pull), 3 = no cluster: two passes
+// through an L2-resident scratch (ntt_u32_l2.cu).
 int ntt_variant_exchange(int variant) { return variant >> 1; }
 
 bool ntt_variant_shape(uint32_t logN, int variant, int* log_t, int* log_c) {
@@ -696,6 +697,7 @@ bool ntt_variant_shape(uint32_t logN, int variant, int* log_t, int* log_c) {
     *log_t = lt;
     *log_c = (int)logN - 5 - lt;
     if (*log_c == 0 && ntt_variant_exchange(variant) != 0) return false;  // no cluster to share
+    if (ntt_variant_exchange(variant) == 3 && logN < 15) return false;    // two-pass kernels: N >= 2^15
     return true;
 }
 
@@ -784,6 +786,7 @@ int ntt_u32_dispatch(const fhe_ctx* ctx, uint32_t logN, bool inverse, uint32_t* 
 #define FHE_NTT_CASE(LT, LC)                                                                       \
     if (log_t == LT && log_c == LC) {                                                              \
         const int ex = LC > 0 ? ntt_variant_exchange(v) : 0;                                       \
+        if (ex == 3) return ntt_u32_l2(ctx, logN, v & 1, inverse, d, (int)rows, batch, map, rowtab, stream); \
         if (ex == 1) return launch<LT, LC, 1>(ctx, t, v, inverse, d, (int)rows, batch, map, rowtab, stream); \
         if (ex == 2) return launch<LT, LC, 2>(ctx, t, v, inverse, d, (int)rows, batch, map, rowtab, stream); \
         return launch<LT, LC, 0>(ctx, t, v, inverse, d, (int)rows, batch, map, rowtab, stream);    \

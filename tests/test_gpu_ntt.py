@@ -37,7 +37,7 @@ def psis(mods, n):
     return [P.psi(m, n) for m in mods]
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", list(range(8)))
 @pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("logn", [10, 11, 12, 13, 14, 15, 16])
 def test_fwd_inv_match_oracle(fhe, ctx, logn, path, variant):
