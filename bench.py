@@ -52,10 +52,8 @@ def parse():
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2212_14191_gb300 import replicas
+    return replicas.dist_env()
 
 
 def measured_peaks():
@@ -206,32 +204,23 @@ def ours(args):
     import torch
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2212_14191_gb300 import fhe
     from paper_2212_14191_gb300 import inputs as I
+    from paper_2212_14191_gb300 import replicas as R
+    R.init(ws, "nccl", torch.device("cuda", local))
 
     def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
-        torch.cuda.synchronize()
+        R.barrier(ws)
 
     def max_over_ranks(v):
-        if ws == 1:
-            return v
-        import torch.distributed as dist
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return R.max_over_ranks(v, ws)
 
     allp = fhe.fhe_gen_primes(16, 30, NTT_LIMBS + 8)
     ps, qs = allp[:8], allp[8:]
     ctx = fhe.Context(16, qs, ps, alpha=HM_ALPHA, default_path=fhe.FHE_NTT_U32)
     st = torch.cuda.current_stream()
     sh = st.cuda_stream
-    x_host = I.uniform_residues(1234 + rank, qs, NTT_BATCH, N)
+    x_host = I.uniform_residues(R.rank_seed(1234, rank), qs, NTT_BATCH, N)
     x = fhe.to_device(x_host)
     ops_per_step = 2 * NTT_LIMBS * NTT_BATCH
 
@@ -273,7 +262,7 @@ def ours(args):
             total, fwd, inv = time_path(path, args.steps, args.warmup)
         if clocks is None or name == "u32":
             clocks = cs.summary()
-        results[name] = {"kops": ops_per_step * args.steps * ws / total / 1e3,
+        results[name] = {"kops": R.whole_job_rate(ops_per_step * args.steps, ws, total) / 1e3,
                          "fwd_ms": fwd * 1e3, "inv_ms": inv * 1e3}
     results["u32"]["autotune_ms"] = tune_ms
     results["u32"]["variant"] = fhe.fhe_ntt_get_variant(ctx.handle, LOGN)
@@ -396,9 +385,7 @@ def ours(args):
             line["cpu_baseline"] = cpu_oracle_kops()
         print(json.dumps(line))
     ctx.close()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    R.finish(ws)
 
 
 def mixed_batch(args, fhe, ctx, qs, ps, st, barrier, max_over_ranks, ws):
