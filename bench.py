@@ -251,8 +251,9 @@ def ours(args):
         inv = statistics.mean(e[1].elapsed_time(e[2]) for e in evs) / 1e3
         return max_over_ranks(total), fwd, inv
 
-    # the library's autotuner picks the plain-path kernel shape for this workload first
-    tune_ms = fhe.fhe_autotune_ntt(ctx.handle, LOGN, x.data_ptr(), NTT_LIMBS, NTT_BATCH, reps=2, stream=sh)
+    # the library's autotuner picks the plain-path variant of each direction for this workload
+    tune_fwd, tune_inv = fhe.fhe_autotune_ntt(ctx.handle, LOGN, x.data_ptr(), NTT_LIMBS, NTT_BATCH, reps=2,
+                                              stream=sh)
     x.copy_(fhe.to_device(x_host))
     paths = {"u32": fhe.FHE_NTT_U32, "tc": fhe.FHE_NTT_TC}
     results = {}
@@ -264,8 +265,9 @@ def ours(args):
             clocks = cs.summary()
         results[name] = {"kops": R.whole_job_rate(ops_per_step * args.steps, ws, total) / 1e3,
                          "fwd_ms": fwd * 1e3, "inv_ms": inv * 1e3}
-    results["u32"]["autotune_ms"] = tune_ms
-    results["u32"]["variant"] = fhe.fhe_ntt_get_variant(ctx.handle, LOGN)
+    results["u32"]["autotune_ms"] = {"fwd": [round(v, 4) for v in tune_fwd], "inv": [round(v, 4) for v in tune_inv]}
+    results["u32"]["variant"] = {"fwd": fhe.fhe_ntt_get_variant(ctx.handle, LOGN, 0),
+                                 "inv": fhe.fhe_ntt_get_variant(ctx.handle, LOGN, 1)}
     fhe.fhe_device_status(ctx.handle, 1)
     head = max(results, key=lambda k: results[k]["kops"])
     # kernels per step: u32 = one forward + one inverse launch; tensor cores = 3 per chunk of
@@ -311,7 +313,8 @@ def ours(args):
         for name, path in (("u32", fhe.FHE_NTT_U32), ("tc", fhe.FHE_NTT_TC)):
             hctx = fhe.Context(16, qs[:HM_LIMBS], ps, alpha=HM_ALPHA, default_path=path)
             if path == fhe.FHE_NTT_U32:
-                fhe.fhe_ntt_set_variant(hctx.handle, LOGN, fhe.fhe_ntt_get_variant(ctx.handle, LOGN))
+                fhe.fhe_ntt_set_variant(hctx.handle, LOGN, fhe.fhe_ntt_get_variant(ctx.handle, LOGN, 0),
+                                        fhe.fhe_ntt_get_variant(ctx.handle, LOGN, 1))
             hctx.hmult(a, b, evk, LOGN, out=out)
             barrier()
             h0 = torch.cuda.Event(enable_timing=True)
@@ -462,7 +465,7 @@ def mixed_batch(args, fhe, ctx, qs, ps, st, barrier, max_over_ranks, ws):
            "graph_ms": t_graph * 1e3, "per_op_ms": t_ops * 1e3,
            "graph_kops": n_ops * ws / t_graph / 1e3, "per_op_kops": n_ops * ws / t_ops / 1e3,
            "config": "N in {2^14,2^15,2^16}, 3..44 limbs, batch 1 per op, one graph launch vs one call per op",
-           "ntt_variant_16": fhe.fhe_ntt_get_variant(ctx.handle, 16)}
+           "ntt_variant_16": [fhe.fhe_ntt_get_variant(ctx.handle, 16, 0), fhe.fhe_ntt_get_variant(ctx.handle, 16, 1)]}
     fhe.fhe_device_status(ctx.handle, 1)
     fhe.fhe_batch_destroy(plan)
     del tensors, scratch, op_scratch, evk

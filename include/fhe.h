@@ -101,21 +101,26 @@ int fhe_ntt_inv(const fhe_ctx* ctx, int path, uint32_t logN, uint32_t* d, int fi
                 int n_limbs, int batch, void* stream);
 
 /*
- * Plain-path kernel shapes (an interface of this library; the paper picks batch sizes per
- * kernel from the hardware in its API layer, Sec. IV-E, but gives no tuning procedure).
- * fhe_ntt_variant_count -- number of shapes available for logN (>= 1), or -1 on bad input.
- * fhe_ntt_get_variant / fhe_ntt_set_variant -- the shape used for logN by every plain-path
- *   transform of this context (HMULT included). Setting it must not race with calls that use
- *   the context; it changes only speed, never results.
- * fhe_autotune_ntt -- times every shape on a forward+inverse round trip over `d`
- *   (device (n_limbs, batch, N), limbs use moduli 0..n_limbs-1; restored bit-exactly on
- *   return), keeps the fastest, and writes the per-shape milliseconds to host array
- *   ms_out[fhe_ntt_variant_count] (nullable; -1 for shapes that do not apply). Synchronises
- *   `stream`.
+ * Plain-path kernel variants (an interface of this library; the paper picks batch sizes per
+ * kernel from the hardware in its API layer, Sec. IV-E, but gives no tuning procedure). A
+ * variant fixes the CTA shape, how a thread-block cluster shares a limb, where last-round
+ * twiddles live and the register budget; variants change only speed, never results.
+ * fhe_ntt_variant_count -- number of variant ids for logN (ids 0..count-1, not all of which
+ *   apply at every logN), or -1 on bad input.
+ * fhe_ntt_get_variant -- the variant used for logN by forward (inverse = 0) or inverse
+ *   (inverse != 0) plain-path transforms of this context (HMULT included), or -1 on bad
+ *   input.
+ * fhe_ntt_set_variant -- select the forward and the inverse variant for logN; FHE_EINVAL if
+ *   either does not apply. Must not race with calls that use the context.
+ * fhe_autotune_ntt -- times every applicable variant on forward and inverse transforms of
+ *   `d` (device (n_limbs, batch, N), limbs use moduli 0..n_limbs-1; restored bit-exactly on
+ *   return), keeps the fastest for each direction, and writes milliseconds per call to host
+ *   array ms_out[2 * fhe_ntt_variant_count] (nullable): forward times at [v], inverse times
+ *   at [count + v], -1 where variant v does not apply. Synchronises `stream`.
  */
 int fhe_ntt_variant_count(const fhe_ctx* ctx, uint32_t logN);
-int fhe_ntt_get_variant(const fhe_ctx* ctx, uint32_t logN);
-int fhe_ntt_set_variant(fhe_ctx* ctx, uint32_t logN, int variant);
+int fhe_ntt_get_variant(const fhe_ctx* ctx, uint32_t logN, int inverse);
+int fhe_ntt_set_variant(fhe_ctx* ctx, uint32_t logN, int fwd_variant, int inv_variant);
 int fhe_autotune_ntt(fhe_ctx* ctx, uint32_t logN, uint32_t* d, int n_limbs, int batch, int reps,
                      float* ms_out, void* stream);
 

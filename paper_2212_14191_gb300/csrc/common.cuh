@@ -46,10 +46,12 @@ uint32_t root_2n(uint32_t q, uint32_t logN);  // primitive 2N-th root from the s
 
 // Plain-path kernel shapes per ring degree: threads per CTA T = 2^log_t and CTAs per
 // cluster C = 2^log_c with 32 * T * C = N (see ntt_u32.cu).
-constexpr int kNttVariants = 8;
+constexpr int kNttVariants = 32;
 constexpr size_t kNttTempBytes = 64ull << 20;
 bool ntt_variant_shape(uint32_t logN, int variant, int* log_t, int* log_c);
 int ntt_variant_exchange(int variant);
+bool ntt_variant_tws(int variant);
+bool ntt_variant_occ2(int variant);
 
 // Plain-path NTT tables for one ring degree N = 2^logN (device memory).
 struct NttTables {
@@ -89,7 +91,7 @@ struct fhe_ctx {
     int dnum = 0;
     std::vector<uint32_t> mods;  // q_0.., p_0..
     fhe::NttTables ntt[FHE_LOGN_MAX + 1];
-    int ntt_variant[FHE_LOGN_MAX + 1] = {};  // plain-path shape in use per logN (autotuned)
+    int ntt_variant[2][FHE_LOGN_MAX + 1] = {};  // plain-path variant per direction (0 fwd, 1 inv) and logN
     fhe::TcTables tc[FHE_LOGN_MAX + 1];
     // conv tables: modup[j][e] for slice j ending (exclusive) at limb e; moddown from P
     std::vector<std::vector<fhe::ConvTable>> modup;
@@ -169,6 +171,30 @@ int dev_upload(fhe_ctx* ctx, T** p, const std::vector<T>& h) {
 }
 
 // ---------------------------------------------------------------- device helpers
+
+// Shared-memory layout of a CTA's 32 * T residues in the plain NTT kernels: position p lives
+// at word pad(p) = p + p / 32 + p / T (the last term only for T > 32). The map is strictly
+// increasing, every access pattern of the kernels' rounds touches 32 distinct banks per warp
+// under it, and for tid < T each pattern is a per-thread base plus a compile-time offset:
+//   p = tid + T e           -> pad(tid) + kSA e
+//   p = T g + lane + 32 e   -> kSA g + lane + 33 e          (e < T / 32)
+//   p = 32 g + e            -> pad(32 g) + e                (e < 32)
+//   p = (c 32T + tid) / C + u T / C -> pad(p at u = 0) + offK(u)   (T / C >= 32)
+// Round C reads p = 32 rev(tid) + e; within a warp rev(tid) = rev5(lane) 2^(log T - 5) + r,
+// so its bank is (rev5(lane) (2^(log T - 5) + 1) + r + e) mod 32: an odd multiple of a
+// permutation of the lanes.
+template <int LOG_T>
+struct PadLayout {
+    static constexpr int T = 1 << LOG_T;
+    static constexpr int kHi = LOG_T > 5 ? 1 : 0;
+    static constexpr int kSA = T + T / 32 + kHi;
+    static constexpr int kWords = 33 * T + 32;
+    __host__ __device__ static constexpr int pad(int p) { return p + (p >> 5) + (kHi ? (p >> LOG_T) : 0); }
+    template <int LOG_C>
+    __host__ __device__ static constexpr int offK(int u) {
+        return u * ((T >> LOG_C) + (T >> (LOG_C + 5))) + kHi * (u >> LOG_C);
+    }
+};
 
 // Shoup multiplication by a constant, lazy: for any x < 2^32 returns x*w mod q in [0, 2q).
 __device__ __forceinline__ uint32_t mul_shoup_lazy(uint32_t x, uint32_t w, uint32_t wq, uint32_t q) {

@@ -233,9 +233,17 @@ int fhe_ctx_create(uint32_t logN_max, const uint32_t* q, int nq, const uint32_t*
     ctx->alpha = alpha;
     ctx->default_path = default_path;
     ctx->mods = mods;
-    // default plain-path shapes: the fastest measured on GB300 for a 44-limb x 64-polynomial
-    // batch (fhe_autotune_ntt re-measures them for the caller's own batch)
-    ctx->ntt_variant[15] = 4;  // 2-CTA clusters, split forward
+    // default plain-path variants (forward, inverse): the fastest measured on GB300 for 44
+    // limbs x (2^22 / N) polynomials; fhe_autotune_ntt re-measures them for the caller's batch
+    static const int kDefaultVariant[3][2] = {
+        {16, 8},  // 2^14: single CTA at 64 registers / single CTA with staged twiddles
+        {20, 7},  // 2^15: 2-CTA split forward at 64 registers / two-pass inverse, 256 threads
+        {4, 7},   // 2^16: 4-CTA split forward / two-pass inverse, 256 threads
+    };
+    for (int l = 14; l <= 16; ++l) {
+        ctx->ntt_variant[0][l] = kDefaultVariant[l - 14][0];
+        ctx->ntt_variant[1][l] = kDefaultVariant[l - 14][1];
+    }
     int rc = FHE_OK;
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
@@ -305,17 +313,19 @@ int fhe_ntt_variant_count(const fhe_ctx* ctx, uint32_t logN) {
     return n;
 }
 
-int fhe_ntt_get_variant(const fhe_ctx* ctx, uint32_t logN) {
+int fhe_ntt_get_variant(const fhe_ctx* ctx, uint32_t logN, int inverse) {
     if (!ctx || logN < FHE_LOGN_MIN || logN > ctx->logN_max) return -1;
-    return ctx->ntt_variant[logN];
+    return ctx->ntt_variant[inverse ? 1 : 0][logN];
 }
 
-int fhe_ntt_set_variant(fhe_ctx* ctx, uint32_t logN, int variant) {
+int fhe_ntt_set_variant(fhe_ctx* ctx, uint32_t logN, int fwd_variant, int inv_variant) {
     FHE_CHECK(ctx != nullptr, "ctx is NULL");
     FHE_CHECK(logN >= FHE_LOGN_MIN && logN <= ctx->logN_max, "logN out of [10, logN_max]");
     int lt, lc;
-    FHE_CHECK(ntt_variant_shape(logN, variant, &lt, &lc), "no such NTT shape for this logN");
-    ctx->ntt_variant[logN] = variant;
+    FHE_CHECK(ntt_variant_shape(logN, fwd_variant, &lt, &lc), "no such forward NTT variant for this logN");
+    FHE_CHECK(ntt_variant_shape(logN, inv_variant, &lt, &lc), "no such inverse NTT variant for this logN");
+    ctx->ntt_variant[0][logN] = fwd_variant;
+    ctx->ntt_variant[1][logN] = inv_variant;
     return FHE_OK;
 }
 
@@ -326,40 +336,49 @@ int fhe_autotune_ntt(fhe_ctx* ctx, uint32_t logN, uint32_t* d, int n_limbs, int 
     FHE_CHECK(batch >= 1 && reps >= 1, "batch and reps must be >= 1");
     cudaStream_t st = (cudaStream_t)stream;
     const LimbMap map = contiguous_map(ctx, 0, n_limbs);
-    const int keep = ctx->ntt_variant[logN];
-    int best = keep;
-    float best_ms = 0;
-    cudaEvent_t e0, e1;
-    FHE_CUDA_TRY(cudaEventCreate(&e0));
-    FHE_CUDA_TRY(cudaEventCreate(&e1));
-    for (int v = 0; v < kNttVariants; ++v) {
+    const int keep[2] = {ctx->ntt_variant[0][logN], ctx->ntt_variant[1][logN]};
+    int best[2] = {keep[0], keep[1]};
+    float best_ms[2] = {-1.0f, -1.0f};
+    const int count = fhe_ntt_variant_count(ctx, logN);
+    cudaEvent_t ev[3];
+    for (int i = 0; i < 3; ++i) FHE_CUDA_TRY(cudaEventCreate(&ev[i]));
+    for (int v = 0; v < count && rc == FHE_OK; ++v) {
         int lt, lc;
         if (!ntt_variant_shape(logN, v, &lt, &lc)) {
-            if (ms_out) ms_out[v] = -1.0f;
+            if (ms_out) ms_out[v] = ms_out[count + v] = -1.0f;
             continue;
         }
-        ctx->ntt_variant[logN] = v;
+        ctx->ntt_variant[0][logN] = ctx->ntt_variant[1][logN] = v;
+        float sum[2] = {0.0f, 0.0f};
+        // one untimed round trip, then `reps` timed ones (forward and inverse timed apart)
         for (int r = 0; r <= reps && rc == FHE_OK; ++r) {
-            if (r == 1) cudaEventRecord(e0, st);
+            cudaEventRecord(ev[0], st);
             rc = ntt_u32(ctx, logN, false, d, n_limbs, batch, map, st);
+            cudaEventRecord(ev[1], st);
             if (rc == FHE_OK) rc = ntt_u32(ctx, logN, true, d, n_limbs, batch, map, st);
+            cudaEventRecord(ev[2], st);
+            cudaError_t ce = cudaEventSynchronize(ev[2]);
+            if (rc == FHE_OK && ce != cudaSuccess) rc = cuda_error(ce, "cudaEventSynchronize");
+            if (rc != FHE_OK || r == 0) continue;
+            float f = 0, i = 0;
+            cudaEventElapsedTime(&f, ev[0], ev[1]);
+            cudaEventElapsedTime(&i, ev[1], ev[2]);
+            sum[0] += f;
+            sum[1] += i;
         }
-        cudaEventRecord(e1, st);
-        cudaError_t ce = cudaEventSynchronize(e1);
-        if (rc == FHE_OK && ce != cudaSuccess) rc = cuda_error(ce, "cudaEventSynchronize");
         if (rc != FHE_OK) break;
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        ms /= reps;
-        if (ms_out) ms_out[v] = ms;
-        if (v == 0 || ms < best_ms) {
-            best_ms = ms;
-            best = v;
+        for (int dir = 0; dir < 2; ++dir) {
+            const float ms = sum[dir] / reps;
+            if (ms_out) ms_out[dir * count + v] = ms;
+            if (best_ms[dir] < 0 || ms < best_ms[dir]) {
+                best_ms[dir] = ms;
+                best[dir] = v;
+            }
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    ctx->ntt_variant[logN] = (rc == FHE_OK) ? best : keep;
+    for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
+    ctx->ntt_variant[0][logN] = (rc == FHE_OK) ? best[0] : keep[0];
+    ctx->ntt_variant[1][logN] = (rc == FHE_OK) ? best[1] : keep[1];
     return rc;
 }
 

@@ -51,10 +51,6 @@ template <int BITS>
 __device__ __forceinline__ uint32_t rbits(uint32_t x) {
     return __brev(x) >> (32 - BITS);
 }
-template <int LOG_T>
-__device__ __forceinline__ int swz2(int p) {
-    return p ^ ((p >> LOG_T) & 31);
-}
 __device__ __forceinline__ void ct2(uint32_t& x, uint32_t& y, uint2 w, uint32_t q) {
     uint32_t x2 = csub(x, 2 * q);
     uint32_t t = mul_shoup_lazy(y, w.x, w.y, q);
@@ -133,6 +129,8 @@ __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_quarter_fwd_kern
     extern __shared__ __align__(128) uint32_t work[];
     const int tid = threadIdx.x, c = blockIdx.x, i = blockIdx.y;
     const int rc = rbits<LOG_C>(c);
+    using L = PadLayout<LOG_T>;
+    const int pA = L::pad(tid);
     uint32_t q;
     int mod;
     uint32_t* row = l2_row<N>(a, a.r0 + i, &q, &mod);
@@ -150,7 +148,7 @@ __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_quarter_fwd_kern
             if ((e & half) == 0) ct2(v[e], v[e + half], __ldg(&tw[(1 << k) * (C + c) + (e >> (5 - k))]), q);
     }
 #pragma unroll
-    for (int e = 0; e < 32; ++e) work[swz2<LOG_T>(tid + T * e)] = v[e];
+    for (int e = 0; e < 32; ++e) work[pA + L::kSA * e] = v[e];
     __syncthreads();
     // round B
     if constexpr (RB > 0) {
@@ -161,7 +159,7 @@ __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_quarter_fwd_kern
             const int g = w_ * GPT + gi;
             uint32_t* vv = v + gi * EG;
 #pragma unroll
-            for (int e = 0; e < EG; ++e) vv[e] = work[swz2<LOG_T>(T * g + lane + 32 * e)];
+            for (int e = 0; e < EG; ++e) vv[e] = work[g * L::kSA + lane + 33 * e];
 #pragma unroll
             for (int k = 0; k < RB; ++k) {
                 const int half = EG >> (k + 1);
@@ -171,15 +169,16 @@ __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_quarter_fwd_kern
                         ct2(vv[e], vv[e + half], __ldg(&tw[(1 << k) * (32 * (C + c) + g) + (e >> (RB - k))]), q);
             }
 #pragma unroll
-            for (int e = 0; e < EG; ++e) work[swz2<LOG_T>(T * g + lane + 32 * e)] = vv[e];
+            for (int e = 0; e < EG; ++e) work[g * L::kSA + lane + 33 * e] = vv[e];
         }
         __syncthreads();
     }
     // round C
     {
         const int gidx = rbits<LOG_T>(tid);
+        const int pC = L::pad(32 * gidx);
 #pragma unroll
-        for (int e = 0; e < 32; ++e) v[e] = work[swz2<LOG_T>(32 * gidx + e)];
+        for (int e = 0; e < 32; ++e) v[e] = work[pC + e];
         const uint2* twc = a.twC + (((size_t)mod * C + c) * 31) * T + tid;
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
@@ -200,6 +199,8 @@ __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_quarter_inv_kern
     extern __shared__ __align__(128) uint32_t work[];
     const int tid = threadIdx.x, c = blockIdx.x, i = blockIdx.y;
     const int rc = rbits<LOG_C>(c);
+    using L = PadLayout<LOG_T>;
+    const int pA = L::pad(tid);
     uint32_t q;
     int mod;
     const uint32_t* row = l2_row<N>(a, a.r0 + i, &q, &mod);
@@ -211,6 +212,7 @@ __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_quarter_inv_kern
     // round C'
     {
         const int gidx = rbits<LOG_T>(tid);
+        const int pC = L::pad(32 * gidx);
         const uint2* twc = a.twC + (((size_t)mod * C + c) * 31) * T + tid;
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
@@ -221,7 +223,7 @@ __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_quarter_inv_kern
                     gs2(v[e], v[e + half], __ldg(&twc[(size_t)((1 << kf) - 1 + (e >> (5 - kf))) * T]), q);
         }
 #pragma unroll
-        for (int e = 0; e < 32; ++e) work[swz2<LOG_T>(32 * gidx + e)] = v[e];
+        for (int e = 0; e < 32; ++e) work[pC + e] = v[e];
         __syncthreads();
     }
     // round B'
@@ -233,7 +235,7 @@ __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_quarter_inv_kern
             const int g = w_ * GPT + gi;
             uint32_t* vv = v + gi * EG;
 #pragma unroll
-            for (int e = 0; e < EG; ++e) vv[e] = work[swz2<LOG_T>(T * g + lane + 32 * e)];
+            for (int e = 0; e < EG; ++e) vv[e] = work[g * L::kSA + lane + 33 * e];
 #pragma unroll
             for (int k = RB - 1; k >= 0; --k) {
                 const int half = EG >> (k + 1);
@@ -243,13 +245,13 @@ __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_quarter_inv_kern
                         gs2(vv[e], vv[e + half], __ldg(&tw[(1 << k) * (32 * (C + c) + g) + (e >> (RB - k))]), q);
             }
 #pragma unroll
-            for (int e = 0; e < EG; ++e) work[swz2<LOG_T>(T * g + lane + 32 * e)] = vv[e];
+            for (int e = 0; e < EG; ++e) work[g * L::kSA + lane + 33 * e] = vv[e];
         }
         __syncthreads();
     }
     // round A'
 #pragma unroll
-    for (int e = 0; e < 32; ++e) v[e] = work[swz2<LOG_T>(tid + T * e)];
+    for (int e = 0; e < 32; ++e) v[e] = work[pA + L::kSA * e];
 #pragma unroll
     for (int k = 4; k >= 0; --k) {
         const int half = 16 >> k;
@@ -265,7 +267,7 @@ template <int LOG_T, int LOG_C>
 int run_l2(const fhe_ctx* ctx, const NttTables& t, int shape, bool inverse, uint32_t* d, int rows, int batch,
            const LimbMap& map, const RowRef* rowtab, cudaStream_t st) {
     constexpr int T = 1 << LOG_T, C = 1 << LOG_C, NC = 32 * T, N = NC * C;
-    constexpr int smem = NC * 4;
+    constexpr int smem = PadLayout<LOG_T>::kWords * 4;
     auto qk = inverse ? ntt_quarter_inv_kernel<LOG_T, LOG_C> : ntt_quarter_fwd_kernel<LOG_T, LOG_C>;
     auto xk = inverse ? ntt_cross_kernel<LOG_T + 5, LOG_C, true> : ntt_cross_kernel<LOG_T + 5, LOG_C, false>;
     FHE_CUDA_TRY(cudaFuncSetAttribute(qk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));

@@ -57,8 +57,8 @@ _SIGS = {
     "fhe_rescale_noalloc": (_i, [_vp, _u32, _i, _i, _vp, _vp, _vp]),
     "fhe_device_status": (_i, [_vp, _i]),
     "fhe_ntt_variant_count": (_i, [_vp, _u32]),
-    "fhe_ntt_get_variant": (_i, [_vp, _u32]),
-    "fhe_ntt_set_variant": (_i, [_vp, _u32, _i]),
+    "fhe_ntt_get_variant": (_i, [_vp, _u32, _i]),
+    "fhe_ntt_set_variant": (_i, [_vp, _u32, _i, _i]),
     "fhe_autotune_ntt": (_i, [_vp, _u32, _vp, _i, _i, _i, ctypes.POINTER(ctypes.c_float), _vp]),
     "fhe_last_error": (_i, [ctypes.c_char_p, _sz]),
     "fhe_batch_create": (_i, [_vp, ctypes.POINTER(FheOp), _i, ctypes.POINTER(_vp)]),
@@ -161,20 +161,23 @@ def fhe_ntt_variant_count(ctx, logN):
     return int(_lib.fhe_ntt_variant_count(ctx, logN))
 
 
-def fhe_ntt_get_variant(ctx, logN):
-    return int(_lib.fhe_ntt_get_variant(ctx, logN))
+def fhe_ntt_get_variant(ctx, logN, inverse=0):
+    return int(_lib.fhe_ntt_get_variant(ctx, logN, 1 if inverse else 0))
 
 
-def fhe_ntt_set_variant(ctx, logN, variant):
-    return _check(_lib.fhe_ntt_set_variant(ctx, logN, variant))
+def fhe_ntt_set_variant(ctx, logN, variant, inv_variant=None):
+    """Select the forward variant and the inverse one (the same unless given)."""
+    inv = variant if inv_variant is None else inv_variant
+    return _check(_lib.fhe_ntt_set_variant(ctx, logN, variant, inv))
 
 
 def fhe_autotune_ntt(ctx, logN, d_ptr, n_limbs, batch, reps=3, stream=0):
-    """Returns the per-shape milliseconds (forward + inverse) measured by the library."""
+    """Returns (forward_ms, inverse_ms): per-variant milliseconds per call measured by the
+    library (-1 where a variant does not apply); the fastest of each is kept."""
     n = max(1, fhe_ntt_variant_count(ctx, logN))
-    ms = (ctypes.c_float * n)()
+    ms = (ctypes.c_float * (2 * n))()
     _check(_lib.fhe_autotune_ntt(ctx, logN, d_ptr, n_limbs, batch, reps, ms, stream))
-    return [float(x) for x in ms]
+    return [float(x) for x in ms[:n]], [float(x) for x in ms[n:]]
 
 
 def fhe_batch_create(ctx, ops):

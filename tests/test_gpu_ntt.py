@@ -37,7 +37,7 @@ def psis(mods, n):
     return [P.psi(m, n) for m in mods]
 
 
-@pytest.mark.parametrize("variant", list(range(8)))
+@pytest.mark.parametrize("variant", list(range(32)))
 @pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("logn", [10, 11, 12, 13, 14, 15, 16])
 def test_fwd_inv_match_oracle(fhe, ctx, logn, path, variant):
@@ -117,6 +117,35 @@ def test_full_size_ckks_batch(fhe, ctx, path):
     assert torch.equal(d, xd)
 
 
+@pytest.mark.parametrize("variant", list(range(32)))
+@pytest.mark.parametrize("logn", [14, 15, 16])
+def test_many_rows_cross_limbs(fhe, ctx, logn, variant):
+    """More rows than resident clusters, a ragged batch, and limb boundaries inside every
+    persistent CTA's row range: the per-modulus twiddle refresh and the row iteration."""
+    import torch
+    keep = fhe.fhe_ntt_get_variant(ctx.handle, logn)
+    try:
+        fhe.fhe_ntt_set_variant(ctx.handle, logn, variant)
+    except fhe.FheError:
+        pytest.skip("no such shape at this N")
+    n = 1 << logn
+    first, nl = 3, 5
+    batch = {14: 61, 15: 29, 16: 23}[logn]
+    mods = MODS[first:first + nl]
+    x = I.uniform_residues(900 + logn, mods, batch, n)
+    d = fhe.to_device(x)
+    ctx.ntt_fwd(d, logn, first_limb=first)
+    torch.cuda.synchronize()
+    got = fhe.to_host(d)
+    ps = psis(mods, n)
+    for l in range(nl):
+        for b in sorted({0, 1, batch // 2, batch - 2, batch - 1}):
+            assert (got[l, b] == ON.ntt(x[l, b], mods[l], ps[l])).all(), (l, b)
+    ctx.ntt_inv(d, logn, first_limb=first)
+    assert torch.equal(d, fhe.to_device(x))
+    fhe.fhe_ntt_set_variant(ctx.handle, logn, keep)
+
+
 @pytest.mark.parametrize("path", PATHS)
 def test_edge_values(fhe, ctx, path):
     import torch
@@ -143,12 +172,22 @@ def test_autotune_keeps_results(fhe, ctx, logn):
     n = 1 << logn
     x = I.uniform_residues(55, QS[:4], 8, n)
     d = fhe.to_device(x)
-    ms = fhe.fhe_autotune_ntt(ctx.handle, logn, d.data_ptr(), 4, 8, reps=2,
-                              stream=torch.cuda.current_stream().cuda_stream)
-    assert len(ms) == fhe.fhe_ntt_variant_count(ctx.handle, logn)
-    valid = [i for i, m in enumerate(ms) if m > 0]
-    assert valid and all(ms[i] == -1 for i in range(len(ms)) if i not in valid)
-    assert fhe.fhe_ntt_get_variant(ctx.handle, logn) == min(valid, key=lambda i: ms[i])
+    fwd, inv = fhe.fhe_autotune_ntt(ctx.handle, logn, d.data_ptr(), 4, 8, reps=2,
+                                    stream=torch.cuda.current_stream().cuda_stream)
+    count = fhe.fhe_ntt_variant_count(ctx.handle, logn)
+    assert len(fwd) == len(inv) == count
+    valid = [i for i in range(count) if fwd[i] > 0]
+    assert valid and valid == [i for i in range(count) if inv[i] > 0]
+    assert all(fwd[i] == -1 and inv[i] == -1 for i in range(count) if i not in valid)
+    for i in valid:                                     # exactly the variants the library accepts
+        fhe.fhe_ntt_set_variant(ctx.handle, logn, i)
+    for i in set(range(count)) - set(valid):
+        with pytest.raises(fhe.FheError):
+            fhe.fhe_ntt_set_variant(ctx.handle, logn, i)
+    fwd, inv = fhe.fhe_autotune_ntt(ctx.handle, logn, d.data_ptr(), 4, 8, reps=2,
+                                    stream=torch.cuda.current_stream().cuda_stream)
+    assert fhe.fhe_ntt_get_variant(ctx.handle, logn, 0) == min(valid, key=lambda i: fwd[i])
+    assert fhe.fhe_ntt_get_variant(ctx.handle, logn, 1) == min(valid, key=lambda i: inv[i])
     assert (fhe.to_host(d) == x).all()          # the round trips restore the input
     ctx.ntt_fwd(d, logn)
     want, _ = ON.ntt_batch(x, QS[:4], psis(QS[:4], n))
