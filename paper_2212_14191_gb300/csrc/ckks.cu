@@ -260,28 +260,72 @@ __global__ void k_rescale_final(const uint32_t* __restrict__ ct, const uint32_t*
 // for the last limb (it feeds the rescale's INTT) and, for the other limbs, directly inside
 // the rescale's final step, so the relinearised ciphertext is never written out.
 // last_c = d_c[l] + (ks_c[l] - y_c[l]) [P^-1]_{q_l}, both components, limb l = nl - 1
+// ---- fused HMULT tail (ModDown combine folded into RESCALE). With rel_i = (ks_i - y^_i) P^-1
+// + d_i the relinearised limb i (NTT domain) and x_i the centred last limb broadcast to q_i,
+// the output is (rel_i - x^_i) q_l^-1 = (ks_i P^-1 + d_i - NTT(y_i P^-1 + x_i)) q_l^-1 by the
+// linearity of the NTT mod q_i, so one forward NTT of z_i = y_i P^-1 + x_i replaces the NTTs
+// of y (ModDown) and of x (RESCALE).
+//
+// u = ks_l P^-1 + d_l, the last limb of both components without the y term (NTT domain).
 __global__ void k_relin_last(const uint32_t* __restrict__ d, const uint32_t* __restrict__ ks,
-                             const uint32_t* __restrict__ y, uint32_t* __restrict__ last, uint2 pinv, uint32_t q,
-                             int nl, int ext, size_t L4) {
+                             uint32_t* __restrict__ last, uint2 pinv, uint32_t q, int nl, int ext, size_t L4) {
     const int c = blockIdx.y, l = nl - 1;
     const uint32_t* dp = d + ((size_t)c * nl + l) * L4 * 4;
     const uint32_t* kp = ks + ((size_t)c * ext + l) * L4 * 4;
-    const uint32_t* yp = y + ((size_t)c * nl + l) * L4 * 4;
     uint32_t* op = last + (size_t)c * L4 * 4;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < L4; n += (size_t)gridDim.x * blockDim.x) {
-        uint4 dv = ld4(dp, n), kv = ld4(kp, n), yv = ld4(yp, n), r;
+        uint4 dv = ld4(dp, n), kv = ld4(kp, n), r;
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-            set(r, k, csub(mul_shoup(get(kv, k) + q - get(yv, k), pinv.x, pinv.y, q) + get(dv, k), q));
+        for (int k = 0; k < 4; ++k) set(r, k, csub(mul_shoup(get(kv, k), pinv.x, pinv.y, q) + get(dv, k), q));
         st4(op, n, r);
     }
 }
 
-// out_c[i] = ((d_c[i] + (ks_c[i] - y_c[i]) [P^-1]_{q_i}) - xb_c[i]) [q_l^-1]_{q_i},  i < nl - 1
+// last = INTT(u) - y_l P^-1 mod q_l: the last relinearised limb in the coefficient domain.
+__global__ void k_last_fix(const uint32_t* __restrict__ y, uint32_t* __restrict__ last, uint2 pinv, uint32_t q,
+                           int nl, size_t L4) {
+    const int c = blockIdx.y, l = nl - 1;
+    const uint32_t* yp = y + ((size_t)c * nl + l) * L4 * 4;
+    uint32_t* op = last + (size_t)c * L4 * 4;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < L4; n += (size_t)gridDim.x * blockDim.x) {
+        uint4 yv = ld4(yp, n), lv = ld4(op, n), r;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) set(r, k, csub(get(lv, k) + q - mul_shoup(get(yv, k), pinv.x, pinv.y, q), q));
+        st4(op, n, r);
+    }
+}
+
+// z_i = y_i P^-1 + [last]_centred mod q_i (coefficient domain), i < l.
+__global__ void k_rescale_prep(const uint32_t* __restrict__ last, const uint32_t* __restrict__ y,
+                               uint32_t* __restrict__ z, const uint2* __restrict__ pinv, uint32_t ql, int nl,
+                               size_t L4, ModVec m) {
+    const int nout = nl - 1;
+    const int c = blockIdx.y / nout, i = blockIdx.y % nout;
+    const uint32_t q = m.q[i];
+    const uint2 pi = __ldg(&pinv[i]);
+    const uint32_t* lp = last + (size_t)c * L4 * 4;
+    const uint32_t* yp = y + ((size_t)c * nl + i) * L4 * 4;
+    uint32_t* zp = z + ((size_t)c * nout + i) * L4 * 4;
+    const uint32_t half = (ql - 1) / 2;
+    const uint32_t ql_mod = ql % q;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < L4; n += (size_t)gridDim.x * blockDim.x) {
+        uint4 lv = ld4(lp, n), yv = ld4(yp, n), r;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t v = get(lv, k);
+            const uint32_t vm = v % q;
+            const uint32_t x = csub(v > half ? (vm + q - ql_mod) : vm, q);  // (v - ql) mod q above half
+            set(r, k, csub(mul_shoup(get(yv, k), pi.x, pi.y, q) + x, q));
+        }
+        st4(zp, n, r);
+    }
+}
+
+// out_i = (ks_i P^-1 + d_i - z^_i) q_l^-1, i < l.
 __global__ void k_hmult_final(const uint32_t* __restrict__ d, const uint32_t* __restrict__ ks,
-                              const uint32_t* __restrict__ y, const uint32_t* __restrict__ xb,
-                              uint32_t* __restrict__ out, const uint2* __restrict__ pinv,
-                              const uint2* __restrict__ qlinv, int nl, int ext, size_t L4, ModVec m) {
+                              const uint32_t* __restrict__ zh, uint32_t* __restrict__ out,
+                              const uint2* __restrict__ pinv, const uint2* __restrict__ qlinv, int nl, int ext,
+                              size_t L4, ModVec m) {
     const int nout = nl - 1;
     const int c = blockIdx.y / nout, i = blockIdx.y % nout;
     const uint32_t q = m.q[i];
@@ -289,15 +333,14 @@ __global__ void k_hmult_final(const uint32_t* __restrict__ d, const uint32_t* __
     const size_t limb = L4 * 4;
     const uint32_t* dp = d + ((size_t)c * nl + i) * limb;
     const uint32_t* kp = ks + ((size_t)c * ext + i) * limb;
-    const uint32_t* yp = y + ((size_t)c * nl + i) * limb;
-    const uint32_t* xp = xb + ((size_t)c * nout + i) * limb;
+    const uint32_t* zp = zh + ((size_t)c * nout + i) * limb;
     uint32_t* op = out + ((size_t)c * nout + i) * limb;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < L4; n += (size_t)gridDim.x * blockDim.x) {
-        uint4 dv = ld4(dp, n), kv = ld4(kp, n), yv = ld4(yp, n), xv = ld4(xp, n), r;
+        uint4 dv = ld4(dp, n), kv = ld4(kp, n), zv = ld4(zp, n), r;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const uint32_t rel = csub(mul_shoup(get(kv, k) + q - get(yv, k), pi.x, pi.y, q) + get(dv, k), q);
-            set(r, k, mul_shoup(rel + q - get(xv, k), qi.x, qi.y, q));
+            const uint32_t rel = csub(mul_shoup(get(kv, k), pi.x, pi.y, q) + get(dv, k), q);
+            set(r, k, mul_shoup(rel + q - get(zv, k), qi.x, qi.y, q));
         }
         st4(op, n, r);
     }
@@ -439,10 +482,11 @@ int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const u
             qm2.mod[c * nl + i] = (uint8_t)i;
             qm2.q[c * nl + i] = ctx->mods[i];
         }
+    // the caller fuses the ModDown combine into RESCALE and takes y in the coefficient domain
+    if (out == nullptr) return FHE_OK;
     if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, false, y, 2 * nl, batch, qm2, st))) return rc;
     int qidx[kMaxLimbs];
     for (int i = 0; i < nl; ++i) qidx[i] = i;
-    if (out == nullptr) return FHE_OK;  // the caller fuses the ModDown combine (see hmult_fused)
     k_moddown_combine<<<stream_grid(ctx, L4, 2 * nl), 256, 0, st>>>(ks, y, out, ctx->p_inv, nl, ext, accumulate,
                                                                   L4, modvec(ctx, qidx, nl));
     FHE_CUDA_TRY(cudaGetLastError());
@@ -496,10 +540,11 @@ int hmult_relin_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const
     return keyswitch_impl(ctx, logN, nl, batch, d2, evk, out, 1, ks_scratch, true, st);
 }
 
-// HMULT + RESCALE with the fused tail. Scratch: relin-d (2 nl limbs: d0, d1), d2 (nl), then
-// the key-switching scratch (d2c, ModUp outputs, ks, y); after the inner product the d2c /
-// ModUp region is reused for the rescale's last limb and broadcast (2 + 2 (nl - 1) limbs,
-// which fit: nl + dnum (nl + K) >= 2 nl).
+// HMULT + RESCALE with the fused tail (k_relin_last .. k_hmult_final above): one forward NTT of
+// 2 (nl - 1) limbs after key switching instead of ModDown's 2 nl and RESCALE's 2 (nl - 1).
+// Scratch: relin-d (2 nl limbs: d0, d1), d2 (nl), then the key-switching scratch (d2c, ModUp
+// outputs, ks, y); after the inner product the d2c / ModUp region is reused for the last limb
+// and z (2 + 2 (nl - 1) limbs, which fit: nl + dnum (nl + K) >= 2 nl).
 int hmult_fused(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint32_t* a, const uint32_t* b,
                 const uint32_t* evk, uint32_t* out, uint32_t* scratch, cudaStream_t st) {
     const size_t N = 1ull << logN, limb = N * batch, L4 = limb / 4;
@@ -521,15 +566,17 @@ int hmult_fused(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint
     if (rc) return rc;
     const uint32_t ql = ctx->mods[nl - 1];
     const uint2 pinv_l = ctx->p_inv_h[nl - 1];
-    k_relin_last<<<stream_grid(ctx, L4, 2), 256, 0, st>>>(dd, ks, y, last, pinv_l, ql, nl, ext, L4);
+    k_relin_last<<<stream_grid(ctx, L4, 2), 256, 0, st>>>(dd, ks, last, pinv_l, ql, nl, ext, L4);
     FHE_CUDA_TRY(cudaGetLastError());
     LimbMap lm;
     lm.mod[0] = lm.mod[1] = (uint8_t)(nl - 1);
     lm.q[0] = lm.q[1] = ql;
     if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, true, last, 2, batch, lm, st))) return rc;
+    k_last_fix<<<stream_grid(ctx, L4, 2), 256, 0, st>>>(y, last, pinv_l, ql, nl, L4);
+    FHE_CUDA_TRY(cudaGetLastError());
     const int nout = nl - 1;
     ModVec qm = modvec(ctx, qidx, nout);
-    k_rescale_broadcast<<<stream_grid(ctx, L4, 2 * nout), 256, 0, st>>>(last, xb, ql, nout, L4, qm);
+    k_rescale_prep<<<stream_grid(ctx, L4, 2 * nout), 256, 0, st>>>(last, y, xb, ctx->p_inv, ql, nl, L4, qm);
     FHE_CUDA_TRY(cudaGetLastError());
     LimbMap qm2;
     for (int c = 0; c < 2; ++c)
@@ -538,7 +585,7 @@ int hmult_fused(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint
             qm2.q[c * nout + i] = ctx->mods[i];
         }
     if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, false, xb, 2 * nout, batch, qm2, st))) return rc;
-    k_hmult_final<<<stream_grid(ctx, L4, 2 * nout), 256, 0, st>>>(dd, ks, y, xb, out, ctx->p_inv,
+    k_hmult_final<<<stream_grid(ctx, L4, 2 * nout), 256, 0, st>>>(dd, ks, xb, out, ctx->p_inv,
                                                                 ctx->ql_inv + (size_t)(nl - 1) * ctx->nq, nl, ext,
                                                                 L4, qm);
     FHE_CUDA_TRY(cudaGetLastError());
