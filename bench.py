@@ -33,6 +33,7 @@ METRIC = "NTT KOPS and HMULT KOPS at N=2^16 (INT8-TC vs plain CUDA), % INT8/HBM 
 LOGN, N = 16, 1 << 16
 NTT_LIMBS, NTT_BATCH = 44, 64
 HM_LIMBS, HM_K, HM_ALPHA, HM_BATCH = 24, 8, 8, 128
+E2E_LIMBS = 4  # limbs per chunk of the pipelined end-to-end step
 
 
 def parse():
@@ -44,6 +45,9 @@ def parse():
     ap.add_argument("--hmult-steps", type=int, default=3)
     ap.add_argument("--no-hmult", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default plain-path variants (for profiling runs)")
+    ap.add_argument("--paths", default="u32,tc", help="NTT paths to time: u32, tc or both")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=2000)
@@ -118,6 +122,14 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def variant_name(v):
+    """Plain-path kernel variant (see ntt_u32.cu) in words."""
+    shape = "512-thread CTAs" if v & 1 == 0 else "256-thread CTAs"
+    ex = ["pull clusters", "push clusters", "split-forward clusters", "two-pass via L2"][(v >> 1) & 3]
+    extra = (", staged twiddles" if v & 8 else "") + (", 64 registers" if v & 16 else "")
+    return "variant %d: %s, %s%s" % (v, shape, ex, extra)
 
 
 def traffic_for(kernel_file, key):
@@ -241,10 +253,13 @@ def ours(args):
         barrier()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
+        # NVTX ranges name the timed regions for profilers (ncu --nvtx --nvtx-include "ntt_u32/")
+        torch.cuda.nvtx.range_push("ntt_u32" if path == fhe.FHE_NTT_U32 else "ntt_tc")
         t0.record(st)
         for i in range(steps):
             step(path, evs[i])
         t1.record(st)
+        torch.cuda.nvtx.range_pop()
         barrier()
         total = t0.elapsed_time(t1) / 1e3
         fwd = statistics.mean(e[0].elapsed_time(e[1]) for e in evs) / 1e3
@@ -252,10 +267,12 @@ def ours(args):
         return max_over_ranks(total), fwd, inv
 
     # the library's autotuner picks the plain-path variant of each direction for this workload
-    tune_fwd, tune_inv = fhe.fhe_autotune_ntt(ctx.handle, LOGN, x.data_ptr(), NTT_LIMBS, NTT_BATCH, reps=2,
-                                              stream=sh)
+    tune_fwd = tune_inv = None
+    if not args.no_autotune:
+        tune_fwd, tune_inv = fhe.fhe_autotune_ntt(ctx.handle, LOGN, x.data_ptr(), NTT_LIMBS, NTT_BATCH, reps=2,
+                                                  stream=sh)
     x.copy_(fhe.to_device(x_host))
-    paths = {"u32": fhe.FHE_NTT_U32, "tc": fhe.FHE_NTT_TC}
+    paths = {k: v for k, v in (("u32", fhe.FHE_NTT_U32), ("tc", fhe.FHE_NTT_TC)) if k in args.paths.split(",")}
     results = {}
     clocks = None
     for name, path in paths.items():
@@ -265,33 +282,68 @@ def ours(args):
             clocks = cs.summary()
         results[name] = {"kops": R.whole_job_rate(ops_per_step * args.steps, ws, total) / 1e3,
                          "fwd_ms": fwd * 1e3, "inv_ms": inv * 1e3}
-    results["u32"]["autotune_ms"] = {"fwd": [round(v, 4) for v in tune_fwd], "inv": [round(v, 4) for v in tune_inv]}
-    results["u32"]["variant"] = {"fwd": fhe.fhe_ntt_get_variant(ctx.handle, LOGN, 0),
-                                 "inv": fhe.fhe_ntt_get_variant(ctx.handle, LOGN, 1)}
+    vf, vi = fhe.fhe_ntt_get_variant(ctx.handle, LOGN, 0), fhe.fhe_ntt_get_variant(ctx.handle, LOGN, 1)
+    if "u32" in results:
+        results["u32"]["autotune_ms"] = None if tune_fwd is None else {
+            "fwd": [round(v, 4) for v in tune_fwd], "inv": [round(v, 4) for v in tune_inv]}
+        results["u32"]["variant"] = {"fwd": vf, "inv": vi}
     fhe.fhe_device_status(ctx.handle, 1)
     head = max(results, key=lambda k: results[k]["kops"])
-    # kernels per step: u32 = one forward + one inverse launch; tensor cores = 3 per chunk of
-    # limbs and direction (split, GEMM 1, GEMM 2)
+    # kernels per step: u32 = one launch per direction, or two per 64 MiB chunk of rows for
+    # the two-pass variants; tensor cores = 3 per chunk of limbs and direction (split, GEMM 1,
+    # GEMM 2)
     chunk_limbs = max(1, min(64, (256 << 20) // (N * 8) // NTT_BATCH))
-    launches_per_step = {"u32": 2, "tc": 2 * 3 * (-(-NTT_LIMBS // chunk_limbs))}
+
+    def u32_launches(v):
+        rows = NTT_LIMBS * NTT_BATCH
+        return 2 * (-(-rows // ((64 << 20) // (N * 4)))) if ((v >> 1) & 3) == 3 else 1
+
+    launches_per_step = {"u32": u32_launches(vf) + u32_launches(vi), "tc": 2 * 3 * (-(-NTT_LIMBS // chunk_limbs))}
     total_head = ops_per_step * args.steps * ws / (results[head]["kops"] * 1e3)
-    # end to end through the C ABI with host buffers: H2D, fwd, inv, D2H every step
+    # end to end through the C ABI with host buffers: every step copies the 44 x 64 batch in
+    # from pinned host memory, transforms it forward and back, and copies it out. The batch
+    # moves in chunks of E2E_LIMBS limbs on three streams (H2D, compute, D2H) so that the two
+    # copy directions and the kernels overlap; every step still moves all of its bytes.
     pinned_in = torch.from_numpy(x_host.view(np.int32)).pin_memory()
     pinned_out = torch.empty_like(pinned_in).pin_memory()
     e2e_steps = max(2, args.steps // 2)
+    s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    chunks = [(l0, min(NTT_LIMBS, l0 + E2E_LIMBS)) for l0 in range(0, NTT_LIMBS, E2E_LIMBS)]
+    ev_in = [torch.cuda.Event() for _ in chunks]
+    ev_cmp = [torch.cuda.Event() for _ in chunks]
+    ev_out = [torch.cuda.Event() for _ in chunks]
+    barrier()
+    for e in ev_out:
+        e.record(s_out)
+
+    def e2e_step(path):
+        for c, (l0, l1) in enumerate(chunks):
+            s_in.wait_event(ev_out[c])          # the previous step's copy-out of this chunk is done
+            with torch.cuda.stream(s_in):
+                x[l0:l1].copy_(pinned_in[l0:l1], non_blocking=True)
+            ev_in[c].record(s_in)
+            s_cmp.wait_event(ev_in[c])
+            fhe.fhe_ntt_fwd(ctx.handle, path, LOGN, x[l0:l1].data_ptr(), l0, l1 - l0, NTT_BATCH, s_cmp.cuda_stream)
+            fhe.fhe_ntt_inv(ctx.handle, path, LOGN, x[l0:l1].data_ptr(), l0, l1 - l0, NTT_BATCH, s_cmp.cuda_stream)
+            ev_cmp[c].record(s_cmp)
+            s_out.wait_event(ev_cmp[c])
+            with torch.cuda.stream(s_out):
+                pinned_out[l0:l1].copy_(x[l0:l1], non_blocking=True)
+            ev_out[c].record(s_out)
+
     for _ in range(2):
-        x.copy_(pinned_in, non_blocking=True)
-        step(paths[head])
-        pinned_out.copy_(x, non_blocking=True)
+        e2e_step(paths[head])
+    torch.cuda.synchronize()
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(st)
+    torch.cuda.nvtx.range_push("e2e")
+    e0.record(s_in)
     for _ in range(e2e_steps):
-        x.copy_(pinned_in, non_blocking=True)
-        step(paths[head])
-        pinned_out.copy_(x, non_blocking=True)
-    e1.record(st)
+        e2e_step(paths[head])
+    e1.record(s_out)                            # after the last copy-out, which follows all work
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
     barrier()
     e2e_t = max_over_ranks(e0.elapsed_time(e1) / 1e3)
     assert np.array_equal(pinned_out.numpy().view(np.uint32), x_host)
@@ -319,10 +371,12 @@ def ours(args):
             barrier()
             h0 = torch.cuda.Event(enable_timing=True)
             h1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.nvtx.range_push("hmult_" + name)
             h0.record(st)
             for _ in range(args.hmult_steps):
                 hctx.hmult(a, b, evk, LOGN, out=out)
             h1.record(st)
+            torch.cuda.nvtx.range_pop()
             barrier()
             fhe.fhe_device_status(hctx.handle, 1)
             ht = max_over_ranks(h0.elapsed_time(h1) / 1e3)
@@ -341,19 +395,32 @@ def ours(args):
         peaks, peak_kind = measured_peaks()
         n1, n2 = 1 << ((LOGN + 1) // 2), 1 << (LOGN // 2)
         rows = NTT_LIMBS * NTT_BATCH
-        u32_bytes = 8 * N * rows   # read + write N u32 per limb transform
-        u32_gbs = u32_bytes / (results["u32"]["fwd_ms"] / 1e3) / 1e9
-        roof_u32 = {"bound": "hbm", "achieved": u32_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": u32_gbs / peaks["hbm_gbs"], "peak_kind": peak_kind,
-                    "kernel": "ntt_fwd_kernel (u32, N=2^16), one launch per call",
-                    "traffic": traffic_for("paper_2212_14191_gb300/csrc/ntt_u32.cu", "ntt_fwd_u32_n65536")}
-        tc_flops = 2 * 16 * N * (n1 + n2) * rows   # 2 GEMMs, 4 x 4 digit products, fused K'
-        tc_tfs = tc_flops / (results["tc"]["fwd_ms"] / 1e3) / 1e12
-        peak_tc = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
-        roof_tc = {"bound": "tensor", "achieved": tc_tfs, "peak": peak_tc, "unit": "TFLOP/s",
-                   "frac": tc_tfs / peak_tc, "peak_kind": peak_kind + " bf16 dense (sustained)",
-                   "kernel": "tensor-core forward NTT call (split + 2 tcgen05 GEMMs per chunk)",
-                   "traffic": None}
+        roof_u32 = roof_imad = roof_tc = None
+        if "u32" in results:
+            u32_bytes = 8 * N * rows   # read + write N u32 per limb transform
+            u32_gbs = u32_bytes / (results["u32"]["fwd_ms"] / 1e3) / 1e9
+            roof_u32 = {"bound": "hbm", "achieved": u32_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": u32_gbs / peaks["hbm_gbs"], "peak_kind": peak_kind,
+                        "kernel": "forward plain NTT launch at N=2^16 (%s), one launch per call" % variant_name(vf),
+                        "traffic": traffic_for("paper_2212_14191_gb300/csrc/ntt_u32_kernels.cuh",
+                                               "ntt_fwd_u32_n65536_v%d" % vf)}
+            # the plain NTT is bound by integer multiplies, not HBM: 3 IMAD per Shoup modmul,
+            # (N/2) log2 N modmuls per limb transform, 64 IMAD lanes per clock per SM
+            sm_mhz = (clocks or {}).get("sm_max_mhz") or 2070
+            imad_peak = 152 * 64 * sm_mhz * 1e6 / 1e12
+            imad_ach = 3 * (N // 2) * LOGN * rows / (results["u32"]["fwd_ms"] / 1e3) / 1e12
+            roof_imad = {"bound": "alu", "achieved": imad_ach, "peak": imad_peak, "unit": "T IMAD/s",
+                         "frac": imad_ach / imad_peak,
+                         "note": "algorithmic IMADs of the butterflies (3 per modmul) of the forward launch; "
+                                 "peak = 152 SMs x 64 IMAD lanes x max SM clock"}
+        if "tc" in results:
+            tc_flops = 2 * 16 * N * (n1 + n2) * rows   # 2 GEMMs, 4 x 4 digit products, fused K'
+            tc_tfs = tc_flops / (results["tc"]["fwd_ms"] / 1e3) / 1e12
+            peak_tc = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+            roof_tc = {"bound": "tensor", "achieved": tc_tfs, "peak": peak_tc, "unit": "TFLOP/s",
+                       "frac": tc_tfs / peak_tc, "peak_kind": peak_kind + " bf16 dense (sustained)",
+                       "kernel": "tensor-core forward NTT call (split + 2 tcgen05 GEMMs per chunk)",
+                       "traffic": None}
         roof = roof_u32 if head == "u32" else roof_tc
         line = {
             "metric": METRIC,
@@ -378,6 +445,7 @@ def ours(args):
             "serving": serve_res,
             "roofline": roof,
             "roofline_u32": roof_u32,
+            "roofline_u32_imad": roof_imad,
             "roofline_tc": roof_tc,
             "e2e": {"value": ops_per_step * e2e_steps * ws / e2e_t / 1e3, "unit": "KOPS",
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},

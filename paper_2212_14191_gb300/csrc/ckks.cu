@@ -161,8 +161,16 @@ __global__ void k_inner_product(const IpArgs a) {
     uint32_t* k1 = a.ks + (size_t)(a.ext + t) * limb;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < a.L4; i += (size_t)gridDim.x * blockDim.x) {
         const size_t n4 = i % a.N4;
-        uint32_t r0[4] = {0, 0, 0, 0}, r1[4] = {0, 0, 0, 0};
+        // products < 2^60: up to 15 of them accumulate exactly in 64 bits, then one reduction
+        uint64_t r0[4] = {0, 0, 0, 0}, r1[4] = {0, 0, 0, 0};
         for (int j = 0; j < a.dnum; ++j) {
+            if (j > 0 && j % 15 == 0) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    r0[k] = reduce_u64(r0[k], mu, q);
+                    r1[k] = reduce_u64(r1[k], mu, q);
+                }
+            }
             const int lo = j * a.alpha, hi = min(a.nl, lo + a.alpha);
             const uint32_t* src = (t >= lo && t < hi)
                                       ? a.d2 + (size_t)t * limb
@@ -172,12 +180,14 @@ __global__ void k_inner_product(const IpArgs a) {
             const uint4 w1 = ld4(a.evk + ((size_t)(j * 2 + 1) * a.nmod + mod) * a.N4 * 4, n4);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                r0[k] = reduce_u64((uint64_t)get(x, k) * get(w0, k) + r0[k], mu, q);
-                r1[k] = reduce_u64((uint64_t)get(x, k) * get(w1, k) + r1[k], mu, q);
+                r0[k] += (uint64_t)get(x, k) * get(w0, k);
+                r1[k] += (uint64_t)get(x, k) * get(w1, k);
             }
         }
-        st4(k0, i, make_uint4(r0[0], r0[1], r0[2], r0[3]));
-        st4(k1, i, make_uint4(r1[0], r1[1], r1[2], r1[3]));
+        st4(k0, i, make_uint4(reduce_u64(r0[0], mu, q), reduce_u64(r0[1], mu, q), reduce_u64(r0[2], mu, q),
+                              reduce_u64(r0[3], mu, q)));
+        st4(k1, i, make_uint4(reduce_u64(r1[0], mu, q), reduce_u64(r1[1], mu, q), reduce_u64(r1[2], mu, q),
+                              reduce_u64(r1[3], mu, q)));
     }
 }
 
