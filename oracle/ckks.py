@@ -20,7 +20,10 @@ Han and Ki that Sec. II-B and Sec. IV-A name, in this reading:
 * HMULT (Sec. II-B) = (d0 + ks0, d1 + ks1) with (d0, d1, d2) the tensor product
   and (ks0, ks1) = KeySwitch(d2);
 * RESCALE (Sec. II-B) divides by the last prime q_l with rounding to nearest:
-  the last limb is centred to (-q_l/2, q_l/2] before it is subtracted.
+  the last limb is centred to (-q_l/2, q_l/2] before it is subtracted;
+* HROTATE / conjugation (Sec. II-B's operation table, FrobeniusMap) applies the
+  automorphism X -> X^k to both components and key-switches c1(X^k) from
+  s(X^k) back to s; CMULT and HADD are limbwise Hada-Mult and Ele-Add.
 
 Arrays are numpy uint64 holding canonical residues; products of two residues
 below 2^30 fit in 64 bits, and every step reduces with '%'. The NTTs run in the
@@ -131,36 +134,52 @@ def conv(x, src, dst):
 # key generation and encryption (host test harness; random draws are inputs)
 
 
-def keygen_evk(prm, s_coeff, a_rand, e_rand):
-    """Relinearisation key for s^2, one key pair per slice (Han-Ki hybrid form).
+def keygen_ksk(prm, s_coeff, target_ntt, a_rand, e_rand):
+    """Key-switching key from `target` to s (Han-Ki hybrid form), one pair per slice.
 
-    s_coeff : (N,) small signed ints (the secret key).
-    a_rand  : (dnum, L+K, N) uniform residues, limb t uniform in [0, mod_t); used
-              directly as NTT-domain values (a uniform polynomial is uniform in
-              either domain).
-    e_rand  : (dnum, N) small signed ints (coefficient domain).
-    Returns evk (dnum, 2, L+K, N) uint64, NTT domain, limbs q_0..q_{L-1}, p_0..p_{K-1}.
+    s_coeff    : (N,) small signed ints (the secret key).
+    target_ntt : (L+K, N) NTT-domain residues of the key being switched away from, over
+                 q_0..q_{L-1}, p_0..p_{K-1} (s^2 for relinearisation, s(X^k) for a
+                 rotation or conjugation).
+    a_rand     : (dnum, L+K, N) uniform residues, limb t uniform in [0, mod_t); used
+                 directly as NTT-domain values (a uniform polynomial is uniform in
+                 either domain).
+    e_rand     : (dnum, N) small signed ints (coefficient domain).
+    Returns (dnum, 2, L+K, N) uint64, NTT domain, limbs q_0..q_{L-1}, p_0..p_{K-1}.
 
-    Slice j encrypts P * (Q/Q_j) * [(Q/Q_j)^-1]_{Q_j} * s^2, whose residue is
-    [P]_{q_i} * s^2 for q_i in slice j and 0 for every other limb.
+    Slice j encrypts P * (Q/Q_j) * [(Q/Q_j)^-1]_{Q_j} * target, whose residue is
+    [P]_{q_i} * target for q_i in slice j and 0 for every other limb.
     """
     mods = prm.qs + prm.ps
     psis = prm.psi_q + prm.psi_p
     L = len(prm.qs)
     dnum = prm.dnum(L)
     s = ntt(small_to_residues(s_coeff, mods), mods, psis)
-    s2 = hada(s, s, mods)
-    evk = np.zeros((dnum, 2, len(mods), prm.N), dtype=U64)
+    ksk = np.zeros((dnum, 2, len(mods), prm.N), dtype=U64)
     for j in range(dnum):
         a = np.asarray(a_rand[j], dtype=U64) % _mods_col(mods)
         e = ntt(small_to_residues(e_rand[j], mods), mods, psis)
         b = add(sub(np.zeros_like(a), hada(a, s, mods), mods), e, mods)
         for i in prm.slice_limbs(j, L):
             q = prm.qs[i]
-            b[i] = (b[i] + (s2[i] * U64(prm.P % q)) % U64(q)) % U64(q)
-        evk[j, 0] = b
-        evk[j, 1] = a
-    return evk
+            b[i] = (b[i] + (target_ntt[i] * U64(prm.P % q)) % U64(q)) % U64(q)
+        ksk[j, 0] = b
+        ksk[j, 1] = a
+    return ksk
+
+
+def keygen_evk(prm, s_coeff, a_rand, e_rand):
+    """Relinearisation key: keygen_ksk for the target s^2."""
+    mods = prm.qs + prm.ps
+    s = ntt(small_to_residues(s_coeff, mods), mods, prm.psi_q + prm.psi_p)
+    return keygen_ksk(prm, s_coeff, hada(s, s, mods), a_rand, e_rand)
+
+
+def keygen_rot(prm, s_coeff, k, a_rand, e_rand):
+    """Rotation / conjugation key for the Galois element k: keygen_ksk for s(X^k)."""
+    mods = prm.qs + prm.ps
+    sk = automorph_coeff(small_to_residues(s_coeff, mods), mods, k)
+    return keygen_ksk(prm, s_coeff, ntt(sk, mods, prm.psi_q + prm.psi_p), a_rand, e_rand)
 
 
 def encrypt(prm, nl, m_coeff, s_coeff, a_rand, e_coeff):
@@ -293,6 +312,64 @@ def rescale(prm, ct):
 def hmult(prm, nl, ct_a, ct_b, evk):
     """HMULT followed by RESCALE: (2, nl, N) x2 -> (2, nl - 1, N)."""
     return rescale(prm, hmult_relin(prm, nl, ct_a, ct_b, evk))
+
+
+# --------------------------------------------------------------------------
+# FrobeniusMap / HROTATE, CMULT, HADD (the other operations of Sec. II-B's table)
+
+
+def galois_rotation(r, N):
+    """Galois element 5^r mod 2N of a rotation of the N/2 slots by r (left for r > 0)."""
+    return pow(5, r % (N // 2), 2 * N)
+
+
+def galois_conjugation(N):
+    """Galois element 2N - 1 (X -> X^-1): complex conjugation of every slot."""
+    return 2 * N - 1
+
+
+def automorph_coeff(a, mods, k):
+    """a(X) -> a(X^k) in Z_q[X]/(X^N + 1), k odd: coefficient n moves to n k mod 2N and is
+    negated when that index lies in [N, 2N) (X^N = -1). a is (len(mods), N) residues."""
+    a = np.asarray(a, dtype=U64)
+    N = a.shape[1]
+    assert k % 2 == 1 and 0 < k < 2 * N
+    out = np.zeros_like(a)
+    m = _mods_col(mods)
+    for n in range(N):
+        t = (n * k) % (2 * N)
+        if t < N:
+            out[:, t] = a[:, n]
+        else:
+            out[:, t - N] = (m[:, 0] - a[:, n]) % m[:, 0]
+    return out
+
+
+def automorph(x_ntt, mods, psis, k):
+    """The same map on NTT-domain limbs, by its definition: INTT, automorph_coeff, NTT."""
+    return ntt(automorph_coeff(intt(x_ntt, mods, psis), mods, k), mods, psis)
+
+
+def hrotate(prm, nl, ct, ksk, k):
+    """HROTATE (FrobeniusMap + key switching): (c0(X^k) + ks0, ks1) with
+    (ks0, ks1) = KeySwitch(c1(X^k)) under the key from s(X^k) to s; nl limbs, NTT domain."""
+    mods, psis = prm.qs[:nl], prm.psi_q[:nl]
+    c0 = automorph(ct[0], mods, psis, k)
+    c1 = automorph(ct[1], mods, psis, k)
+    k0, k1 = keyswitch(prm, nl, c1, ksk)
+    return np.stack([add(c0, k0, mods), k1 % _mods_col(mods)])
+
+
+def cmult(prm, nl, ct, pt_ntt):
+    """CMULT: both components times a plaintext, limbwise in the NTT domain (no rescale)."""
+    mods = prm.qs[:nl]
+    return np.stack([hada(ct[0], pt_ntt, mods), hada(ct[1], pt_ntt, mods)])
+
+
+def hadd(prm, nl, ct_a, ct_b):
+    """HADD: componentwise sum mod q_i."""
+    mods = prm.qs[:nl]
+    return np.stack([add(ct_a[0], ct_b[0], mods), add(ct_a[1], ct_b[1], mods)])
 
 
 # --------------------------------------------------------------------------

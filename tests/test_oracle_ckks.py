@@ -8,7 +8,12 @@ mathematics, not against itself:
 * KeySwitch(d2) decrypts to d2 s^2 plus an error within the analytic bound;
 * the canonical embedding agrees with direct complex evaluation and is a ring
   homomorphism for the product in R[X]/(X^N+1);
-* decrypt(HMULT(enc a, enc b)) = a*b within 1e-5 (sparse ternary secret).
+* decrypt(HMULT(enc a, enc b)) = a*b within 1e-5 (sparse ternary secret);
+* the automorphism X -> X^k agrees with term-by-term evaluation at the roots
+  through the brute-force Eq. (4) transform, obeys the group law, permutes
+  NTT slots, and rotates / conjugates the canonical-embedding slots;
+* decrypt(HROTATE(enc m)) = m(X^k) within the key-switching bound, and
+  CMULT / HADD decrypt exactly to the schoolbook product / the sum.
 """
 import math
 
@@ -206,3 +211,121 @@ def test_hmult_constant():
     out = C.hmult(prm, nl, cts[0], cts[1], evk)
     dec = C.decode(np.array(C.decrypt_coeffs(prm, out, s), dtype=float), delta * delta / qs[nl - 1])
     assert np.abs(dec - (-0.375)).max() < 1e-6
+
+
+# --------------------------------------------------------------------------
+# FrobeniusMap / HROTATE, CMULT, HADD
+
+
+def test_automorph_is_substitution_x_to_xk():
+    """NTT(a(X^k))[j] equals sum_n a_n psi^((2j+1) n k), evaluated term by term with python
+    ints through the brute-force Eq. (4) transform (not through automorph_coeff's index map)."""
+    from oracle import ntt as ON
+    N = 32
+    q = P.ntt_primes(1, logn_max=5, bits=12)[0]
+    psi = P.psi(q, N)
+    a = I.uniform_residues(3, [q], 1, N, dtype=np.uint64)[:, 0]
+    for k in (3, 5, 25, 2 * N - 1, 2 * N - 3):
+        b = C.automorph_coeff(a, [q], k)[0]
+        got = ON.ntt_brute(b.astype(np.uint32), q, psi)
+        for j in range(N):
+            x = pow(psi, 2 * j + 1, q)
+            want = sum(int(a[0, n]) * pow(x, n * k, q) for n in range(N)) % q
+            assert int(got[j]) == want, (k, j)
+
+
+def test_automorph_group_law_and_ntt_permutation():
+    N = 64
+    qs = P.ntt_primes(2, logn_max=6, bits=20)
+    psis = [P.psi(q, N) for q in qs]
+    a = I.uniform_residues(4, qs, 1, N, dtype=np.uint64)[:, 0]
+    assert (C.automorph_coeff(a, qs, 1) == a).all()
+    for k, l in ((3, 5), (5, 2 * N - 1), (7, 77)):
+        lhs = C.automorph_coeff(C.automorph_coeff(a, qs, l), qs, k)
+        assert (lhs == C.automorph_coeff(a, qs, (k * l) % (2 * N))).all()
+    # in the NTT domain the map only permutes: output j takes input j' with
+    # 2j' + 1 = (2j + 1) k mod 2N
+    A = C.ntt(a, qs, psis)
+    for k in (3, 5, 2 * N - 1):
+        B = C.automorph(A, qs, psis, k)
+        perm = [(((2 * j + 1) * k) % (2 * N) - 1) // 2 for j in range(N)]
+        assert (B == A[:, perm]).all()
+
+
+def _int_automorph(coeffs, k, mods):
+    """Integer polynomial through automorph_coeff on residues and a CRT lift (centred)."""
+    res = C.small_to_residues(np.asarray(coeffs, dtype=np.int64), mods)
+    return C.crt_centered(C.automorph_coeff(res, mods, k), mods)
+
+
+@pytest.mark.parametrize("r", [1, 3, -2])
+def test_rotation_rotates_slots(r):
+    N = 128
+    mods = P.ntt_primes(3, logn_max=7, bits=30)
+    z = I.uniform_reals(5 + r % 7, N // 2) + 1j * I.uniform_reals(9 + r % 5, N // 2)
+    m = C.encode(z, N, 2.0 ** 30)
+    k = C.galois_rotation(r, N)
+    out = C.decode(np.array(_int_automorph(m, k, mods), dtype=float), 2.0 ** 30)
+    assert np.abs(out - np.roll(z, -r)).max() < 1e-6
+
+
+def test_conjugation_conjugates_slots():
+    N = 128
+    mods = P.ntt_primes(3, logn_max=7, bits=30)
+    z = I.uniform_reals(6, N // 2) + 1j * I.uniform_reals(7, N // 2)
+    m = C.encode(z, N, 2.0 ** 30)
+    out = C.decode(np.array(_int_automorph(m, C.galois_conjugation(N), mods), dtype=float), 2.0 ** 30)
+    assert np.abs(out - np.conj(z)).max() < 1e-6
+
+
+@pytest.mark.parametrize("nl,r", [(4, 1), (9, -3), (12, 5)])
+def test_hrotate_decrypts_to_rotation(small, nl, r):
+    """decrypt(HROTATE(enc m)) = m(X^k) + e(X^k) + key-switching error (same bound as the
+    key-switching test plus the fresh error), and its slots are the rotated slots."""
+    prm, s, _ = small
+    k = C.galois_rotation(r, prm.N)
+    L = len(prm.qs)
+    arand = I.uniform_residues(60 + nl, prm.qs + prm.ps, prm.dnum(L), prm.N, dtype=np.uint64).transpose(1, 0, 2)
+    ksk = C.keygen_rot(prm, s, k, arand, I.gaussian_error(61 + nl, (prm.dnum(L), prm.N)))
+    z = I.uniform_reals(62 + nl, prm.N // 2)
+    delta = 2.0 ** 25
+    m = C.encode(z, prm.N, delta)
+    a = I.uniform_residues(63 + nl, prm.qs[:nl], 1, prm.N, dtype=np.uint64)[:, 0]
+    ct = C.encrypt(prm, nl, m, s, a, I.gaussian_error(64 + nl, prm.N))
+    out = C.hrotate(prm, nl, ct, ksk, k)
+    dec = C.decrypt_coeffs(prm, out, s, n_crt=min(nl, 3))
+    want = _int_automorph(m, k, prm.qs[:3])
+    bound = 19.0
+    for j in range(prm.dnum(nl)):
+        Qj = math.prod(prm.qs[i] for i in prm.slice_limbs(j, nl))
+        bound += prm.N * (prm.alpha + 1) * Qj / prm.P * 19
+    bound += (1 + int(np.abs(s).sum())) * (prm.K + 1)
+    assert max(abs(x - y) for x, y in zip(dec, want)) <= bound
+    slots = C.decode(np.array(dec, dtype=float), delta)
+    assert np.abs(slots - np.roll(z, -r)).max() < 1e-2
+
+
+def test_cmult_and_hadd_decrypt_exactly(small):
+    """decrypt(CMULT(enc m, p)) = (m + e) p and decrypt(HADD(enc m1, enc m2)) = m1 + e1 + m2 + e2
+    exactly, with the negacyclic product from the schoolbook oracle."""
+    from oracle import ntt as ON
+    prm, s, _ = small
+    nl = 3
+    mods, psis = prm.qs[:nl], prm.psi_q[:nl]
+    g = np.random.default_rng(71)
+    m1 = g.integers(-1000, 1000, prm.N)
+    m2 = g.integers(-1000, 1000, prm.N)
+    p = g.integers(-50, 50, prm.N)
+    e1, e2 = I.gaussian_error(72, prm.N), I.gaussian_error(73, prm.N)
+    a1 = I.uniform_residues(74, mods, 1, prm.N, dtype=np.uint64)[:, 0]
+    a2 = I.uniform_residues(75, mods, 1, prm.N, dtype=np.uint64)[:, 0]
+    ct1 = C.encrypt(prm, nl, m1, s, a1, e1)
+    ct2 = C.encrypt(prm, nl, m2, s, a2, e2)
+    q0 = prm.qs[0]
+    pt = C.ntt(C.small_to_residues(p, mods), mods, psis)
+    dec = C.decrypt_coeffs(prm, C.cmult(prm, nl, ct1, pt), s)
+    want = ON.negacyclic_mul(np.mod(m1 + e1, q0).astype(np.uint32), np.mod(p, q0).astype(np.uint32), q0)
+    want = [int(w) - q0 if int(w) > q0 // 2 else int(w) for w in want]
+    assert dec == want
+    dec = C.decrypt_coeffs(prm, C.hadd(prm, nl, ct1, ct2), s)
+    assert dec == [int(v) for v in (m1 + e1 + m2 + e2)]
