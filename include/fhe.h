@@ -129,6 +129,7 @@ int fhe_autotune_ntt(fhe_ctx* ctx, uint32_t logN, uint32_t* d, int n_limbs, int 
 #define FHE_OP_KEYSWITCH 2
 #define FHE_OP_RESCALE 3
 #define FHE_OP_HMULT_RELIN 4
+#define FHE_OP_HROTATE 5
 
 /*
  * fhe_scratch_bytes -- device scratch (bytes) that fhe_hmult / fhe_keyswitch /
@@ -180,6 +181,34 @@ int fhe_rescale(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const
 int fhe_hmult(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const uint32_t* ct_a,
               const uint32_t* ct_b, const uint32_t* evk, uint32_t* ct_out, void* scratch,
               size_t scratch_bytes, void* stream);
+
+/*
+ * The other ciphertext operations of Sec. II-B's table (HROTATE with its FrobeniusMap,
+ * CMULT, HADD). Ciphertexts are (2, n_limbs, batch, N) in the NTT domain over q_0.., as for
+ * fhe_hmult; device pointers 16-byte aligned; asynchronous on `stream`.
+ *
+ * fhe_automorph -- FrobeniusMap a(X) -> a(X^galois) of `rows` NTT-domain rows of length N
+ *   (any moduli: in the NTT domain the map is the permutation out[j] = in[j'] with
+ *   2j' + 1 = (2j + 1) galois mod 2N). galois odd and < 2N; in and out must not overlap.
+ * fhe_hrotate -- HROTATE: (c0(X^k) + ks0, ks1) with (ks0, ks1) = KeySwitch(c1(X^k)) and
+ *   k = galois (5^r mod 2N rotates the slots by r, 2N - 1 conjugates them). `ksk` is the
+ *   key from s(X^k) to s in the layout of `evk` above. Scratch: fhe_scratch_bytes(
+ *   FHE_OP_HROTATE); ct_out must not overlap ct_in. No rescale.
+ * fhe_cmult -- CMULT: both components times the plaintext `pt` ((n_limbs, batch, N), NTT
+ *   domain, one plaintext per ciphertext), limbwise mod q_i. No rescale. May run in place.
+ * fhe_hadd -- HADD: ct_a + ct_b limbwise mod q_i. May run in place.
+ * Errors: FHE_EINVAL for bad sizes, pointers or galois elements; FHE_ENOMEM for a short
+ * scratch; FHE_ECUDA for launch failures.
+ */
+int fhe_automorph(const fhe_ctx* ctx, uint32_t logN, long long rows, uint32_t galois, const uint32_t* in,
+                  uint32_t* out, void* stream);
+int fhe_hrotate(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, uint32_t galois,
+                const uint32_t* ct_in, const uint32_t* ksk, uint32_t* ct_out, void* scratch,
+                size_t scratch_bytes, void* stream);
+int fhe_cmult(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const uint32_t* ct,
+              const uint32_t* pt, uint32_t* ct_out, void* stream);
+int fhe_hadd(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const uint32_t* ct_a,
+             const uint32_t* ct_b, uint32_t* ct_out, void* stream);
 
 /*
  * Operation-level batching (Sec. IV-D) of many independent operations with uneven ring

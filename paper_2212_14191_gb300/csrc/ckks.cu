@@ -602,6 +602,89 @@ int hmult_fused(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint
     return FHE_OK;
 }
 
+// ---- FrobeniusMap (X -> X^k, k odd) in the NTT domain, where it only permutes: Eq. (4)
+// evaluates at psi^(2j+1), and a(X^k) at psi^(2j+1) is a at psi^((2j+1) k), so output j takes
+// input j' with 2j' + 1 = (2j + 1) k mod 2N. The product is taken mod 2^32, a multiple of
+// 2N, so its wrap-around does not change it mod 2N. Rows are independent of the modulus.
+__global__ void k_automorph(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, uint32_t k, int logN,
+                            size_t rows) {
+    const uint32_t N = 1u << logN, mask = 2 * N - 1;
+    for (size_t r = blockIdx.y; r < rows; r += gridDim.y) {
+        const uint32_t* src = in + (r << logN);
+        uint32_t* dst = out + (r << logN);
+        for (uint32_t j4 = blockIdx.x * blockDim.x + threadIdx.x; j4 < N / 4; j4 += gridDim.x * blockDim.x) {
+            uint4 v;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint32_t j = 4 * j4 + kk;
+                set(v, kk, __ldg(&src[(((2 * j + 1) * k) & mask) >> 1]));
+            }
+            st4(dst, j4, v);
+        }
+    }
+}
+
+int launch_automorph(const fhe_ctx* ctx, const uint32_t* in, uint32_t* out, uint32_t k, uint32_t logN, size_t rows,
+                     cudaStream_t st) {
+    if (rows == 0) return FHE_OK;
+    const size_t L4 = ((size_t)1 << logN) / 4;
+    const unsigned gy = (unsigned)std::min<size_t>(rows, 65535);
+    dim3 g = stream_grid(ctx, L4, (int)std::min<size_t>(rows, 1 << 20));
+    g.y = gy;
+    k_automorph<<<g, 256, 0, st>>>(in, out, k, (int)logN, rows);
+    FHE_CUDA_TRY(cudaGetLastError());
+    return FHE_OK;
+}
+
+// ---- CMULT (Hada-Mult of both components by a plaintext) and HADD (Ele-Add), NTT domain.
+__global__ void k_cmult(const uint32_t* __restrict__ ct, const uint32_t* __restrict__ pt, uint32_t* __restrict__ out,
+                        size_t L4, size_t comp4, ModVec m) {
+    const int l = blockIdx.y;
+    const uint32_t q = m.q[l];
+    const uint64_t mu = m.mu[l];
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < L4; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t idx = (size_t)l * L4 + i;
+        const uint4 p = ld4(pt, idx), c0 = ld4(ct, idx), c1 = ld4(ct, comp4 + idx);
+        uint4 r0, r1;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            set(r0, k, reduce_u64((uint64_t)get(c0, k) * get(p, k), mu, q));
+            set(r1, k, reduce_u64((uint64_t)get(c1, k) * get(p, k), mu, q));
+        }
+        st4(out, idx, r0);
+        st4(out, comp4 + idx, r1);
+    }
+}
+
+__global__ void k_hadd(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b, uint32_t* __restrict__ out,
+                       size_t L4, size_t comp4, ModVec m) {
+    const int l = blockIdx.y % (gridDim.y / 2), c = blockIdx.y / (gridDim.y / 2);
+    const uint32_t q = m.q[l];
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < L4; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t idx = c * comp4 + (size_t)l * L4 + i;
+        const uint4 x = ld4(a, idx), y = ld4(b, idx);
+        uint4 r;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) set(r, k, csub(get(x, k) + get(y, k), q));
+        st4(out, idx, r);
+    }
+}
+
+// HROTATE / conjugation: out = (c0(X^k) + ks0, ks1), (ks0, ks1) = KeySwitch(c1(X^k)) under the
+// key from s(X^k) to s. Scratch: c1(X^k) (nl limbs), then the key-switching scratch.
+size_t hrotate_scratch_limbs(int nl, int K, int alpha) { return (size_t)nl + ks_scratch_limbs(nl, K, alpha); }
+
+int hrotate_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, uint32_t k, const uint32_t* ct,
+                 const uint32_t* ksk, uint32_t* out, uint32_t* scratch, cudaStream_t st) {
+    const size_t limb = ((size_t)1 << logN) * batch, rows = (size_t)nl * batch;
+    uint32_t* c1k = scratch;
+    int rc;
+    if ((rc = launch_automorph(ctx, ct, out, k, logN, rows, st))) return rc;
+    if ((rc = launch_automorph(ctx, ct + (size_t)nl * limb, c1k, k, logN, rows, st))) return rc;
+    FHE_CUDA_TRY(cudaMemsetAsync(out + (size_t)nl * limb, 0, (size_t)nl * limb * 4, st));
+    return keyswitch_impl(ctx, logN, nl, batch, c1k, ksk, out, 1, c1k + (size_t)nl * limb, false, st);
+}
+
 bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 int check_ckks(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, int min_nl) {
@@ -625,6 +708,7 @@ size_t scratch_limbs(const fhe_ctx* ctx, int op, int nl) {
         case FHE_OP_HMULT_RELIN: return (size_t)nl + ks_scratch_limbs(nl, K, ctx->alpha);
         case FHE_OP_RESCALE: return rescale_scratch_limbs(nl);
         case FHE_OP_HMULT: return 2 * (size_t)nl + (size_t)nl + ks_scratch_limbs(nl, K, ctx->alpha);
+        case FHE_OP_HROTATE: return hrotate_scratch_limbs(nl, K, ctx->alpha);
         default: return 0;
     }
 }
@@ -686,6 +770,69 @@ int fhe_hmult(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const u
     if (scratch_bytes < fhe_scratch_bytes(ctx, FHE_OP_HMULT, logN, n_limbs, batch))
         return set_error(FHE_ENOMEM, "scratch too small");
     return hmult_fused(ctx, logN, n_limbs, batch, ct_a, ct_b, evk, ct_out, (uint32_t*)scratch, (cudaStream_t)stream);
+}
+
+int fhe_automorph(const fhe_ctx* ctx, uint32_t logN, long long rows, uint32_t galois, const uint32_t* in,
+                  uint32_t* out, void* stream) {
+    FHE_CHECK(ctx != nullptr, "ctx is NULL");
+    FHE_CHECK(logN >= FHE_LOGN_MIN && logN <= ctx->logN_max, "logN out of [10, logN_max]");
+    FHE_CHECK(rows >= 0, "rows < 0");
+    FHE_CHECK((galois & 1u) == 1u && galois < (2u << logN), "galois element must be odd and below 2N");
+    if (rows == 0) return FHE_OK;
+    int rc = check_ptrs({in, out});
+    if (rc) return rc;
+    FHE_CHECK(in != out, "fhe_automorph cannot run in place");
+    return launch_automorph(ctx, in, out, galois, logN, (size_t)rows, (cudaStream_t)stream);
+}
+
+int fhe_hrotate(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, uint32_t galois, const uint32_t* ct_in,
+                const uint32_t* ksk, uint32_t* ct_out, void* scratch, size_t scratch_bytes, void* stream) {
+    int rc = check_ckks(ctx, logN, n_limbs, batch, 1);
+    if (rc || batch == 0) return rc;
+    FHE_CHECK((galois & 1u) == 1u && galois < (2u << logN), "galois element must be odd and below 2N");
+    if ((rc = check_ptrs({ct_in, ksk, ct_out, scratch}))) return rc;
+    FHE_CHECK(ct_in != ct_out, "fhe_hrotate cannot run in place");
+    if (scratch_bytes < fhe_scratch_bytes(ctx, FHE_OP_HROTATE, logN, n_limbs, batch))
+        return set_error(FHE_ENOMEM, "scratch too small");
+    return hrotate_impl(ctx, logN, n_limbs, batch, galois, ct_in, ksk, ct_out, (uint32_t*)scratch,
+                        (cudaStream_t)stream);
+}
+
+int fhe_cmult(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const uint32_t* ct, const uint32_t* pt,
+              uint32_t* ct_out, void* stream) {
+    FHE_CHECK(ctx != nullptr, "ctx is NULL");
+    FHE_CHECK(logN >= FHE_LOGN_MIN && logN <= ctx->logN_max, "logN out of [10, logN_max]");
+    FHE_CHECK(n_limbs >= 1 && n_limbs <= ctx->nq, "n_limbs out of range");
+    FHE_CHECK(batch >= 0, "batch < 0");
+    if (batch == 0) return FHE_OK;
+    int rc = check_ptrs({ct, pt, ct_out});
+    if (rc) return rc;
+    const size_t L4 = ((size_t)batch << logN) / 4;
+    int qidx[kMaxLimbs];
+    for (int i = 0; i < n_limbs; ++i) qidx[i] = i;
+    k_cmult<<<stream_grid(ctx, L4, n_limbs), 256, 0, (cudaStream_t)stream>>>(ct, pt, ct_out, L4, (size_t)n_limbs * L4,
+                                                                           modvec(ctx, qidx, n_limbs));
+    FHE_CUDA_TRY(cudaGetLastError());
+    return FHE_OK;
+}
+
+int fhe_hadd(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const uint32_t* ct_a, const uint32_t* ct_b,
+             uint32_t* ct_out, void* stream) {
+    FHE_CHECK(ctx != nullptr, "ctx is NULL");
+    FHE_CHECK(logN >= FHE_LOGN_MIN && logN <= ctx->logN_max, "logN out of [10, logN_max]");
+    FHE_CHECK(n_limbs >= 1 && n_limbs <= ctx->nq, "n_limbs out of range");
+    FHE_CHECK(batch >= 0, "batch < 0");
+    if (batch == 0) return FHE_OK;
+    int rc = check_ptrs({ct_a, ct_b, ct_out});
+    if (rc) return rc;
+    const size_t L4 = ((size_t)batch << logN) / 4;
+    int qidx[kMaxLimbs];
+    for (int i = 0; i < n_limbs; ++i) qidx[i] = i;
+    k_hadd<<<stream_grid(ctx, L4, 2 * n_limbs), 256, 0, (cudaStream_t)stream>>>(ct_a, ct_b, ct_out, L4,
+                                                                              (size_t)n_limbs * L4,
+                                                                              modvec(ctx, qidx, n_limbs));
+    FHE_CUDA_TRY(cudaGetLastError());
+    return FHE_OK;
 }
 
 }  // extern "C"

@@ -18,7 +18,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "fhe.h")
 
 FHE_OK, FHE_EINVAL, FHE_ENOMEM, FHE_ECUDA, FHE_ETIMEOUT = 0, 1, 2, 3, 4
 FHE_NTT_DEFAULT, FHE_NTT_U32, FHE_NTT_TC = 0, 1, 2
-FHE_OP_HMULT, FHE_OP_KEYSWITCH, FHE_OP_RESCALE, FHE_OP_HMULT_RELIN = 1, 2, 3, 4
+FHE_OP_HMULT, FHE_OP_KEYSWITCH, FHE_OP_RESCALE, FHE_OP_HMULT_RELIN, FHE_OP_HROTATE = 1, 2, 3, 4, 5
 FHE_RESCALE_NOALLOC_MAX_BYTES = 32 << 20
 
 if not os.path.exists(LIB_PATH):
@@ -55,6 +55,10 @@ _SIGS = {
     "fhe_rescale": (_i, [_vp, _u32, _i, _i, _vp, _vp, _vp, _sz, _vp]),
     "fhe_hmult": (_i, [_vp, _u32, _i, _i, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "fhe_rescale_noalloc": (_i, [_vp, _u32, _i, _i, _vp, _vp, _vp]),
+    "fhe_automorph": (_i, [_vp, _u32, ctypes.c_longlong, _u32, _vp, _vp, _vp]),
+    "fhe_hrotate": (_i, [_vp, _u32, _i, _i, _u32, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "fhe_cmult": (_i, [_vp, _u32, _i, _i, _vp, _vp, _vp, _vp]),
+    "fhe_hadd": (_i, [_vp, _u32, _i, _i, _vp, _vp, _vp, _vp]),
     "fhe_device_status": (_i, [_vp, _i]),
     "fhe_ntt_variant_count": (_i, [_vp, _u32]),
     "fhe_ntt_get_variant": (_i, [_vp, _u32, _i]),
@@ -151,6 +155,23 @@ def fhe_rescale_noalloc(ctx, logN, n_limbs, batch, ct_in, ct_out, stream=0):
 
 def fhe_hmult(ctx, logN, n_limbs, batch, a, b, evk, out, scratch, scratch_bytes, stream=0):
     return _check(_lib.fhe_hmult(ctx, logN, n_limbs, batch, a, b, evk, out, scratch, scratch_bytes, stream))
+
+
+def fhe_automorph(ctx, logN, rows, galois, d_in, d_out, stream=0):
+    return _check(_lib.fhe_automorph(ctx, logN, rows, galois, d_in, d_out, stream))
+
+
+def fhe_hrotate(ctx, logN, n_limbs, batch, galois, ct_in, ksk, ct_out, scratch, scratch_bytes, stream=0):
+    return _check(_lib.fhe_hrotate(ctx, logN, n_limbs, batch, galois, ct_in, ksk, ct_out, scratch, scratch_bytes,
+                                   stream))
+
+
+def fhe_cmult(ctx, logN, n_limbs, batch, ct, pt, ct_out, stream=0):
+    return _check(_lib.fhe_cmult(ctx, logN, n_limbs, batch, ct, pt, ct_out, stream))
+
+
+def fhe_hadd(ctx, logN, n_limbs, batch, ct_a, ct_b, ct_out, stream=0):
+    return _check(_lib.fhe_hadd(ctx, logN, n_limbs, batch, ct_a, ct_b, ct_out, stream))
 
 
 def fhe_device_status(ctx, clear=1):
@@ -299,6 +320,39 @@ class Context:
             out = torch.empty((2, nl - 1, batch, 1 << logN), dtype=torch.int32, device=ct.device)
         s, n = self.scratch(FHE_OP_RESCALE, logN, nl, batch)
         fhe_rescale(self.handle, logN, nl, batch, _ptr(ct), _ptr(out), _ptr(s), n, _stream())
+        return out
+
+    def automorph(self, x, logN, galois, out=None):
+        """FrobeniusMap of every row of x (..., N), NTT domain."""
+        import torch
+        if out is None:
+            out = torch.empty_like(x)
+        fhe_automorph(self.handle, logN, x.numel() >> logN, galois, _ptr(x), _ptr(out), _stream())
+        return out
+
+    def hrotate(self, ct, ksk, logN, galois, out=None):
+        import torch
+        nl, batch = ct.shape[1], ct.shape[2]
+        if out is None:
+            out = torch.empty_like(ct)
+        s, n = self.scratch(FHE_OP_HROTATE, logN, nl, batch)
+        fhe_hrotate(self.handle, logN, nl, batch, galois, _ptr(ct), _ptr(ksk), _ptr(out), _ptr(s), n, _stream())
+        return out
+
+    def cmult(self, ct, pt, logN, out=None):
+        import torch
+        nl, batch = ct.shape[1], ct.shape[2]
+        if out is None:
+            out = torch.empty_like(ct)
+        fhe_cmult(self.handle, logN, nl, batch, _ptr(ct), _ptr(pt), _ptr(out), _stream())
+        return out
+
+    def hadd(self, a, b, logN, out=None):
+        import torch
+        nl, batch = a.shape[1], a.shape[2]
+        if out is None:
+            out = torch.empty_like(a)
+        fhe_hadd(self.handle, logN, nl, batch, _ptr(a), _ptr(b), _ptr(out), _stream())
         return out
 
 

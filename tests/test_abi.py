@@ -44,6 +44,14 @@ def test_argument_validation_without_gpu(fhe):
     with pytest.raises(fhe.FheError):
         fhe.fhe_hmult(None, 12, 2, 1, 16, 16, 16, 16, 16, 0, 0)
     assert fhe.fhe_scratch_bytes(None, fhe.FHE_OP_HMULT, 12, 2, 1) == 0
+    assert fhe.fhe_scratch_bytes(None, fhe.FHE_OP_HROTATE, 12, 2, 1) == 0
+    for call in (lambda: fhe.fhe_automorph(None, 12, 1, 5, 16, 32),
+                 lambda: fhe.fhe_hrotate(None, 12, 2, 1, 5, 16, 16, 32, 16, 0),
+                 lambda: fhe.fhe_cmult(None, 12, 2, 1, 16, 16, 16),
+                 lambda: fhe.fhe_hadd(None, 12, 2, 1, 16, 16, 16)):
+        with pytest.raises(fhe.FheError) as e:
+            call()
+        assert e.value.code == fhe.FHE_EINVAL and "ctx" in str(e.value)
     # bad moduli are rejected before any device allocation
     composite = ((1 << 30) - 1) // (1 << 17) * (1 << 17) + 1   # above the largest such prime
     assert composite > P.ntt_primes(1)[0]

@@ -1,0 +1,153 @@
+"""GPU parity of the other ciphertext operations of Sec. II-B's table against the CPU
+oracle: FrobeniusMap (X -> X^k), HROTATE / conjugation, CMULT and HADD, bit-exact on seeded
+inputs, plus CKKS decryption of a GPU rotation. The full-size case uses the HMULT
+configuration (N = 2^16, 24 + 8 limbs, dnum = 3) with sampled rows."""
+import numpy as np
+import pytest
+
+from oracle import ckks as C
+from oracle import params as P
+from paper_2212_14191_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+U64 = np.uint64
+
+
+@pytest.fixture(scope="module")
+def fhe():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2212_14191_gb300 import fhe as f
+    return f
+
+
+@pytest.fixture(scope="module")
+def small(fhe):
+    logn = 11
+    qs, ps = P.default_moduli(12, 4)
+    prm = C.Params(1 << logn, qs, ps, alpha=4)
+    s = I.ternary_secret(8, prm.N, hamming_weight=64)
+    ctx = fhe.Context(logn, qs, ps, alpha=4)
+    yield logn, prm, s, ctx
+    ctx.close()
+
+
+def rot_key(prm, s, k, seed):
+    L = len(prm.qs)
+    arand = I.uniform_residues(seed, prm.qs + prm.ps, prm.dnum(L), prm.N, dtype=np.uint64).transpose(1, 0, 2)
+    return C.keygen_rot(prm, s, k, arand, I.gaussian_error(seed + 1, (prm.dnum(L), prm.N)))
+
+
+def batch_cts(prm, nl, batch, seed):
+    x = I.uniform_residues(seed, prm.qs[:nl], 2 * batch, prm.N)
+    return x.reshape(nl, 2, batch, prm.N).transpose(1, 0, 2, 3).copy()
+
+
+@pytest.mark.parametrize("logn", [10, 13, 16])
+def test_automorph_bitexact(fhe, logn):
+    import torch
+    n = 1 << logn
+    mods = P.default_moduli(3, 1)[0]
+    ctx = fhe.Context(logn, mods)
+    x = I.uniform_residues(logn, mods, 2, n)
+    for k in (5, 25, 2 * n - 1, C.galois_rotation(-7, n)):
+        out = ctx.automorph(fhe.to_device(x), logn, k)
+        torch.cuda.synchronize()
+        got = fhe.to_host(out)
+        for b in range(2):
+            want = C.automorph(x[:, b].astype(U64), mods, [P.psi(q, n) for q in mods], k) if logn < 16 else None
+            if want is None:   # 2^16: the permutation the oracle's NTT-domain map equals (pinned on CPU)
+                perm = [(((2 * j + 1) * k) % (2 * n) - 1) // 2 for j in range(n)]
+                want = x[:, b][:, perm]
+            assert (got[:, b] == want).all(), (k, b)
+    ctx.close()
+
+
+@pytest.mark.parametrize("nl", [1, 4, 9, 12])
+def test_hrotate_bitexact(fhe, small, nl):
+    import torch
+    logn, prm, s, ctx = small
+    for k in (C.galois_rotation(3, prm.N), C.galois_conjugation(prm.N)):
+        ksk = rot_key(prm, s, k, 100 + nl)
+        ct = batch_cts(prm, nl, 3, 110 + nl)
+        out = ctx.hrotate(fhe.to_device(ct), fhe.to_device(ksk.astype(np.uint32)), logn, k)
+        torch.cuda.synchronize()
+        got = fhe.to_host(out)
+        for b in range(3):
+            want = C.hrotate(prm, nl, ct[:, :, b].astype(U64), ksk, k)
+            assert (got[:, :, b] == want).all(), (k, b)
+
+
+def test_hrotate_decrypts_to_rotated_slots(fhe, small):
+    import torch
+    logn, prm, s, ctx = small
+    nl, r = 6, 5
+    k = C.galois_rotation(r, prm.N)
+    ksk = rot_key(prm, s, k, 120)
+    z = I.uniform_reals(121, prm.N // 2)
+    delta = 2.0 ** 30
+    a = I.uniform_residues(122, prm.qs[:nl], 1, prm.N, dtype=np.uint64)[:, 0]
+    ct = C.encrypt(prm, nl, C.encode(z, prm.N, delta), s, a, I.gaussian_error(123, prm.N))
+    out = ctx.hrotate(fhe.to_device(ct.astype(np.uint32)[:, :, None]), fhe.to_device(ksk.astype(np.uint32)), logn, k)
+    torch.cuda.synchronize()
+    dec = C.decrypt_coeffs(prm, fhe.to_host(out)[:, :, 0].astype(U64), s)
+    # key-switching noise with P ~ Q_j here: about N (alpha + 1) 19 / delta ~ 2e-4 per slot
+    assert np.abs(C.decode(np.array(dec, dtype=float), delta) - np.roll(z, -r)).max() < 2e-3
+
+
+@pytest.mark.parametrize("nl", [1, 5, 12])
+def test_cmult_hadd_bitexact(fhe, small, nl):
+    import torch
+    logn, prm, s, ctx = small
+    mods = prm.qs[:nl]
+    a, b = batch_cts(prm, nl, 5, 130 + nl), batch_cts(prm, nl, 5, 140 + nl)
+    pt = I.uniform_residues(150 + nl, mods, 5, prm.N)
+    da, db, dp = fhe.to_device(a), fhe.to_device(b), fhe.to_device(pt)
+    cm = fhe.to_host(ctx.cmult(da, dp, logn))
+    ha = fhe.to_host(ctx.hadd(da, db, logn))
+    ctx.hadd(da, db, logn, out=da)                      # in place
+    torch.cuda.synchronize()
+    for k in range(5):
+        assert (cm[:, :, k] == C.cmult(prm, nl, a[:, :, k].astype(U64), pt[:, k].astype(U64))).all(), k
+        assert (ha[:, :, k] == C.hadd(prm, nl, a[:, :, k].astype(U64), b[:, :, k].astype(U64))).all(), k
+    assert (fhe.to_host(da) == ha).all()
+
+
+def test_ops_bad_arguments(fhe, small):
+    logn, prm, s, ctx = small
+    import torch
+    x = torch.zeros((2, 2, 1, prm.N), dtype=torch.int32, device="cuda")
+    y = torch.zeros_like(x)
+    for k in (0, 4, 2 * prm.N + 1):                    # even or out of range
+        with pytest.raises(fhe.FheError) as e:
+            ctx.automorph(x, logn, k, out=y)
+        assert e.value.code == fhe.FHE_EINVAL
+    with pytest.raises(fhe.FheError):
+        ctx.automorph(x, logn, 5, out=x)                # in place
+    with pytest.raises(fhe.FheError) as e:
+        fhe.fhe_hrotate(ctx.handle, logn, 2, 1, 5, x.data_ptr(), x.data_ptr(), y.data_ptr(), y.data_ptr(), 16)
+    assert e.value.code == fhe.FHE_ENOMEM
+    fhe.fhe_device_status(ctx.handle, 1)
+
+
+def test_hrotate_full_size_config(fhe):
+    """N = 2^16, 24 ciphertext limbs + 8 special primes, dnum = 3, 4 ciphertexts: sampled
+    (limb, ciphertext) rows of the GPU result against the oracle's rotation of that ciphertext."""
+    import torch
+    logn, n, nl, K, batch = 16, 1 << 16, 24, 8, 4
+    qs, ps = P.default_moduli(nl, K)
+    prm = C.Params(n, qs, ps, alpha=8)
+    s = I.ternary_secret(160, n, hamming_weight=64)
+    k = C.galois_rotation(1, n)
+    ksk = rot_key(prm, s, k, 161)
+    ct = batch_cts(prm, nl, batch, 162)
+    ctx = fhe.Context(logn, qs, ps, alpha=8)
+    out = ctx.hrotate(fhe.to_device(ct), fhe.to_device(ksk.astype(np.uint32)), logn, k)
+    torch.cuda.synchronize()
+    got = fhe.to_host(out)
+    for b in (0, batch - 1):
+        want = C.hrotate(prm, nl, ct[:, :, b].astype(U64), ksk, k)
+        assert (got[:, :, b] == want).all(), b
+    fhe.fhe_device_status(ctx.handle, 1)
+    ctx.close()
