@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--paths", default="u32,tc", help="NTT paths to time: u32, tc or both")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-heax", action="store_true", help="skip the HEAX comparison parameter sets")
     ap.add_argument("--serving-requests", type=int, default=2000)
     ap.add_argument("--batch-ops", type=int, default=1000)
     return ap.parse_args()
@@ -350,7 +351,7 @@ def ours(args):
     nbytes = x_host.nbytes
 
     # HMULT (N = 2^16, 24 + 8 limbs, dnum = 3, 128 pairs): uniform ciphertexts and key
-    hm = None
+    hm = ops = None
     if not args.no_hmult:
         a = fhe.to_device(I.uniform_residues(11, qs[:HM_LIMBS], 2 * HM_BATCH, N))
         b = fhe.to_device(I.uniform_residues(12, qs[:HM_LIMBS], 2 * HM_BATCH, N))
@@ -382,6 +383,8 @@ def ours(args):
             ht = max_over_ranks(h0.elapsed_time(h1) / 1e3)
             hm[name] = {"kops": HM_BATCH * args.hmult_steps * ws / ht / 1e3,
                         "ms_per_call": ht / args.hmult_steps * 1e3}
+            if path == fhe.FHE_NTT_U32:
+                ops = other_ops(args, fhe, hctx, a, b, evk, st, barrier, max_over_ranks, ws)
             hctx.close()
             del hctx
             torch.cuda.empty_cache()
@@ -390,6 +393,8 @@ def ours(args):
     batch_res = None if args.no_batch else mixed_batch(args, fhe, ctx, qs, ps, st, barrier, max_over_ranks, ws)
 
     serve_res = None if args.no_serving else serving_bench(args, fhe, qs, ps)
+
+    heax_res = None if args.no_heax else heax_sets(args, fhe, st, barrier, max_over_ranks, ws)
 
     if rank == 0:
         peaks, peak_kind = measured_peaks()
@@ -441,6 +446,8 @@ def ours(args):
                        "parallelism": "replicas" if ws > 1 else "1 GPU"},
             "paths": results,
             "hmult": hm,
+            "ops": ops,
+            "heax_sets": heax_res,
             "mixed_batch": batch_res,
             "serving": serve_res,
             "roofline": roof,
@@ -457,6 +464,105 @@ def ours(args):
         print(json.dumps(line))
     ctx.close()
     R.finish(ws)
+
+
+def other_ops(args, fhe, hctx, a, b, evk, st, barrier, max_over_ranks, ws):
+    """HROTATE (rotation by one slot; the relinearisation key stands in for the rotation key,
+    which has the same layout), CMULT and HADD on the HMULT workload: 128 ciphertexts of
+    24 limbs at N = 2^16. CMULT and HADD are HBM streams; their fraction is of the measured
+    HBM bandwidth."""
+    import torch
+    peaks, _ = measured_peaks()
+    res = {"config": "N=2^16, 24 ciphertext limbs (+ 8 special primes for HROTATE), 128 ciphertexts per call"}
+    galois = 5                                   # 5^1 mod 2N: rotation of the slots by one
+    pt = b[0]                                    # any (24, 128, N) residues serve as a plaintext
+    out = torch.empty_like(a)
+    limb_bytes = N * HM_BATCH * 4
+    cases = (("hrotate", lambda: hctx.hrotate(a, evk, LOGN, galois, out=out), None, args.hmult_steps),
+             ("cmult", lambda: hctx.cmult(a, pt, LOGN, out=out), 5 * HM_LIMBS * limb_bytes, 10),
+             ("hadd", lambda: hctx.hadd(a, b, LOGN, out=out), 6 * HM_LIMBS * limb_bytes, 10))
+    for name, fn, nbytes, reps in cases:
+        fn()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push(name)
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        torch.cuda.nvtx.range_pop()
+        barrier()
+        t = max_over_ranks(e0.elapsed_time(e1) / 1e3) / reps
+        res[name] = {"kops": HM_BATCH * ws / t / 1e3, "ms_per_call": t * 1e3}
+        if nbytes:
+            res[name]["hbm_frac"] = nbytes / t / 1e9 / peaks["hbm_gbs"]
+    fhe.fhe_device_status(hctx.handle, 1)
+    del out
+    return res
+
+
+# Table (HEAX comparison) parameter sets in 30-bit primes: log PQ / 30 rounded up, split
+# into L ciphertext limbs and K special primes with P > Q (one key-switching slice, dnum = 1).
+HEAX_SETS = (("Set_A", 12, 2, 2), ("Set_B", 13, 4, 4), ("Set_C", 14, 7, 8))
+HEAX_BATCH = 1024
+PAPER_A100 = {"Set_A": (910134, 913267, 88048), "Set_B": (449974, 449084, 27564), "Set_C": (209337, 209178, 3825)}
+
+
+def heax_sets(args, fhe, st, barrier, max_over_ranks, ws):
+    """#NTT/s, #INTT/s (one op = one limb transform) and #HMULT/s (HMULT + relinearisation +
+    rescale, one op = one ciphertext pair) at the paper's HEAX comparison sets, 1024
+    ciphertexts per call, on the plain path with autotuned variants. The paper's A100 numbers
+    are context, not targets."""
+    import torch
+    from paper_2212_14191_gb300 import inputs as I
+    allp = fhe.fhe_gen_primes(16, 30, 16)
+    res = {"config": "L ciphertext limbs + K special primes of 30 bits, dnum=1, %d ciphertexts per call" % HEAX_BATCH}
+    for name, logn, L, K in HEAX_SETS:
+        n = 1 << logn
+        ps, qs = allp[:K], allp[K:K + L]
+        c = fhe.Context(logn, qs, ps, alpha=L, default_path=fhe.FHE_NTT_U32)
+        rows_b = 4 * HEAX_BATCH                      # limb transforms: 4 limbs x batch polynomials
+        x = fhe.to_device(I.uniform_residues(200 + logn, (qs + ps)[:4], HEAX_BATCH, n))   # L + K >= 4
+        r = {"N": n, "L": L, "K": K}
+        fhe.fhe_autotune_ntt(c.handle, logn, x.data_ptr(), 4, HEAX_BATCH, reps=2, stream=st.cuda_stream)
+        for key, inv in (("ntt_per_s", False), ("intt_per_s", True)):
+            fn = fhe.fhe_ntt_inv if inv else fhe.fhe_ntt_fwd
+            for _ in range(3):
+                fn(c.handle, fhe.FHE_NTT_U32, logn, x.data_ptr(), 0, 4, HEAX_BATCH, st.cuda_stream)
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(20):
+                fn(c.handle, fhe.FHE_NTT_U32, logn, x.data_ptr(), 0, 4, HEAX_BATCH, st.cuda_stream)
+            e1.record(st)
+            barrier()
+            t = max_over_ranks(e0.elapsed_time(e1) / 1e3) / 20
+            r[key] = rows_b * ws / t
+        a = fhe.to_device(I.uniform_residues(210 + logn, qs, 2 * HEAX_BATCH, n)).view(L, 2, HEAX_BATCH, n) \
+            .permute(1, 0, 2, 3).contiguous()
+        b = fhe.to_device(I.uniform_residues(211 + logn, qs, 2 * HEAX_BATCH, n)).view(L, 2, HEAX_BATCH, n) \
+            .permute(1, 0, 2, 3).contiguous()
+        evk = fhe.to_device(I.uniform_residues(212 + logn, qs + ps, 2, n)).view(L + K, 1, 2, n) \
+            .permute(1, 2, 0, 3).contiguous()
+        out = torch.empty((2, L - 1, HEAX_BATCH, n), dtype=torch.int32, device="cuda")
+        for _ in range(3):
+            c.hmult(a, b, evk, logn, out=out)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(10):
+            c.hmult(a, b, evk, logn, out=out)
+        e1.record(st)
+        barrier()
+        t = max_over_ranks(e0.elapsed_time(e1) / 1e3) / 10
+        r["hmult_per_s"] = HEAX_BATCH * ws / t
+        r["paper_a100"] = dict(zip(("ntt_per_s", "intt_per_s", "hmult_per_s"), PAPER_A100[name]))
+        fhe.fhe_device_status(c.handle, 1)
+        res[name] = r
+        c.close()
+        del a, b, evk, out, x
+        torch.cuda.empty_cache()
+    return res
 
 
 def mixed_batch(args, fhe, ctx, qs, ps, st, barrier, max_over_ranks, ws):

@@ -163,3 +163,34 @@ def test_hmult_tensor_core_path(fhe):
         want = C.hmult(prm, nl, a[:, :, k].astype(U64), b[:, :, k].astype(U64), evk)
         assert (got[:, :, k] == want).all(), k
     ctx.close()
+
+
+@pytest.mark.parametrize("logn,L,K", [(12, 2, 2), (13, 4, 4), (14, 7, 8)])
+def test_hmult_heax_sets_bitexact(fhe, logn, L, K):
+    """The paper's HEAX comparison sets in 30-bit primes (L ciphertext limbs + K special
+    primes, one key-switching slice): HMULT + relinearisation + rescale bit-exact, plus the
+    relinearised product decrypting to a*b."""
+    import torch
+    n = 1 << logn
+    allp = P.ntt_primes(L + K)
+    ps, qs = allp[:K], allp[K:]
+    prm = C.Params(n, qs, ps, alpha=L)
+    s, evk = make_key(prm, 300 + logn)
+    a, b = batch_cts(prm, L, 2, 310 + logn), batch_cts(prm, L, 2, 320 + logn)
+    ctx = fhe.Context(logn, qs, ps, alpha=L)
+    out = ctx.hmult(fhe.to_device(a), fhe.to_device(b), fhe.to_device(evk.astype(np.uint32)), logn)
+    torch.cuda.synchronize()
+    got = fhe.to_host(out)
+    for k in range(2):
+        want = C.hmult(prm, L, a[:, :, k].astype(U64), b[:, :, k].astype(U64), evk)
+        assert (got[:, :, k] == want).all(), k
+    za, ca = encrypt_pair(prm, L, s, 330 + logn, delta=2.0 ** 25)
+    zb, cb = encrypt_pair(prm, L, s, 340 + logn, delta=2.0 ** 25)
+    rel = ctx.hmult_relin(fhe.to_device(ca.astype(np.uint32)[:, :, None]),
+                          fhe.to_device(cb.astype(np.uint32)[:, :, None]), fhe.to_device(evk.astype(np.uint32)), logn)
+    torch.cuda.synchronize()
+    dec = C.decrypt_coeffs(prm, fhe.to_host(rel)[:, :, 0].astype(U64), s, n_crt=L)
+    zz = C.decode(np.array(dec, dtype=float), 2.0 ** 50)
+    assert np.abs(zz - za * zb).max() < 1e-3
+    fhe.fhe_device_status(ctx.handle, 1)
+    ctx.close()
