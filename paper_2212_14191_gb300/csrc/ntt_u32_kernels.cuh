@@ -529,6 +529,64 @@ ntt_inv_kernel(const NttArgs a) {
     if constexpr (C > 1) ptx::cluster_sync();
 }
 
+// Cross stages of the split forward for quarter CC of a row: thread tid loads position
+// p = tid + T e of all C quarters, runs the first log2(C) Cooley-Tukey stages on them and
+// keeps quarter CC. With CC a compile-time constant only the butterflies that feed it are
+// computed (3 modmuls per position instead of 4 for C = 4); CC = -1 keeps quarter c_rt.
+template <int LOG_T, int LOG_C, int CC>
+__device__ __forceinline__ void split_cross(uint32_t (&v)[32], const uint32_t* data, const uint2* tw, uint32_t q,
+                                            int tid, int c_rt = 0) {
+    constexpr int T = 1 << LOG_T, C = 1 << LOG_C, NC = 32 * T;
+#pragma unroll
+    for (int e0 = 0; e0 < 32; e0 += 8) {
+        uint32_t x[8][C];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int qq = 0; qq < C; ++qq) x[i][qq] = __ldg(&data[tid + T * (e0 + i) + qq * NC]);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+#pragma unroll
+            for (int s = 0; s < LOG_C; ++s) {
+                const int tq = C >> (s + 1);
+#pragma unroll
+                for (int qq = 0; qq < C; ++qq) {
+                    if ((qq / tq) % 2 == 0) {
+                        uint2 w = __ldg(&tw[(1 << s) + qq / (2 * tq)]);
+                        ct_bfly(x[i][qq], x[i][qq + tq], w, q);
+                    }
+                }
+            }
+            if constexpr (CC >= 0) {
+                v[e0 + i] = x[i][CC];
+            } else {  // quarter chosen at run time
+                uint32_t r = x[i][0];
+#pragma unroll
+                for (int qq = 1; qq < C; ++qq)
+                    if (qq == c_rt) r = x[i][qq];
+                v[e0 + i] = r;
+            }
+        }
+    }
+}
+
+template <int LOG_T, int LOG_C>
+__device__ __forceinline__ void split_cross_dispatch(int c, uint32_t (&v)[32], const uint32_t* data, const uint2* tw,
+                                                     uint32_t q, int tid) {
+    constexpr int C = 1 << LOG_C;
+    static_assert(C <= 8, "split cross stages are specialised for clusters of up to 8 CTAs");
+    switch (c) {
+        case 0: split_cross<LOG_T, LOG_C, 0>(v, data, tw, q, tid); break;
+        case 1: split_cross<LOG_T, LOG_C, 1 % C>(v, data, tw, q, tid); break;
+        case 2: if constexpr (C > 2) split_cross<LOG_T, LOG_C, 2 % C>(v, data, tw, q, tid); break;
+        case 3: if constexpr (C > 2) split_cross<LOG_T, LOG_C, 3 % C>(v, data, tw, q, tid); break;
+        case 4: if constexpr (C > 4) split_cross<LOG_T, LOG_C, 4 % C>(v, data, tw, q, tid); break;
+        case 5: if constexpr (C > 4) split_cross<LOG_T, LOG_C, 5 % C>(v, data, tw, q, tid); break;
+        case 6: if constexpr (C > 4) split_cross<LOG_T, LOG_C, 6 % C>(v, data, tw, q, tid); break;
+        default: if constexpr (C > 4) split_cross<LOG_T, LOG_C, 7 % C>(v, data, tw, q, tid); break;
+    }
+}
+
 // Forward transform with independent quarters (exchange mode "split", C > 1): every CTA of
 // the cluster reads its positions p in all C quarters of the row (the C reads of a position
 // hit L2 after the first), runs the cross stages itself and keeps its own output quarter c,
@@ -563,34 +621,12 @@ ntt_fwd_split_kernel(const NttArgs a) {
             ptx::prefetch_l2(row_ptr<N>(a, row + ri.step) + c * NC, NC * 4);
         uint32_t v[32];
 
-        // ---- cross stages for this CTA's quarter, 8 positions at a time
-#pragma unroll
-        for (int e0 = 0; e0 < 32; e0 += 8) {
-            uint32_t x[8][C];
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int qq = 0; qq < C; ++qq) x[i][qq] = __ldg(&data[tid + T * (e0 + i) + qq * NC]);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-#pragma unroll
-                for (int s = 0; s < LOG_C; ++s) {
-                    const int tq = C >> (s + 1);
-#pragma unroll
-                    for (int qq = 0; qq < C; ++qq) {
-                        if ((qq / tq) % 2 == 0) {
-                            uint2 w = __ldg(&tw[(1 << s) + qq / (2 * tq)]);
-                            ct_bfly(x[i][qq], x[i][qq + tq], w, q);
-                        }
-                    }
-                }
-                uint32_t r = x[i][0];
-#pragma unroll
-                for (int qq = 1; qq < C; ++qq)
-                    if (qq == c) r = x[i][qq];
-                v[e0 + i] = r;
-            }
-        }
+        // ---- cross stages for this CTA's quarter: specialised on c (only the butterflies that
+        // feed quarter c) where registers allow, generic under the 64-register budget
+        if constexpr (OCC == 1)
+            split_cross_dispatch<LOG_T, LOG_C>(c, v, data, tw, q, tid);
+        else
+            split_cross<LOG_T, LOG_C, -1>(v, data, tw, q, tid, c);
         __syncwarp();
         ptx::cluster_arrive_relaxed();  // this CTA has read everything it needs from the row
 
