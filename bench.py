@@ -381,8 +381,14 @@ def ours(args):
             barrier()
             fhe.fhe_device_status(hctx.handle, 1)
             ht = max_over_ranks(h0.elapsed_time(h1) / 1e3)
-            hm[name] = {"kops": HM_BATCH * args.hmult_steps * ws / ht / 1e3,
-                        "ms_per_call": ht / args.hmult_steps * 1e3}
+            # fully fused HBM floor per op: both input ciphertexts, the output, evk / batch
+            dnum_h = -(-HM_LIMBS // HM_ALPHA)
+            op_bytes = (16 * HM_LIMBS + 8 * (HM_LIMBS - 1)) * N + dnum_h * 2 * (HM_LIMBS + HM_K) * N * 4 / HM_BATCH
+            kops = HM_BATCH * args.hmult_steps * ws / ht / 1e3
+            ceil_kops = measured_peaks()[0]["hbm_gbs"] * 1e9 / op_bytes / 1e3
+            hm[name] = {"kops": kops, "ms_per_call": ht / args.hmult_steps * 1e3,
+                        "hbm_floor_bytes_per_op": op_bytes, "hbm_ceiling_kops": ceil_kops,
+                        "frac_of_hbm_ceiling": kops / ceil_kops}
             if path == fhe.FHE_NTT_U32:
                 ops = other_ops(args, fhe, hctx, a, b, evk, st, barrier, max_over_ranks, ws)
             hctx.close()
