@@ -200,9 +200,24 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const uint32_t q = a.q[z];
     const uint64_t mu = a.mu[z], off = a.off[z];
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    // mode 1: this thread's twiddles for column block cb (16 columns, stride Y), loaded one
+    // block ahead so their L2 latency overlaps the TMEM loads and the previous block's work
+    const uint2* twp = a.tw + ((size_t)a.mod[z] * a.cols + n0) * a.Y + y;
+    uint2 wnext[16];
+    if (a.mode == 1 && valid) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) wnext[j] = __ldg(&twp[(size_t)j * a.Y]);
+    }
 #pragma unroll 1
     for (int cb = 0; cb < NT / 16; ++cb) {
         uint32_t r[4][16];
+        uint2 wcur[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) wcur[j] = wnext[j];
+        if (a.mode == 1 && valid && cb + 1 < NT / 16) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) wnext[j] = __ldg(&twp[(size_t)((cb + 1) * 16 + j) * a.Y]);
+        }
 #pragma unroll
         for (int i = 0; i < 4; ++i) ptx::tmem_ld16(lane_base + i * NT + cb * 16, r[i]);
         ptx::tmem_wait_ld();
@@ -217,7 +232,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             const long long yv = a0 + 255 * a1 + 65025 * a2 + 16581375 * a3;
             uint32_t v = reduce_u64((uint64_t)(yv + (long long)off), mu, q);
             if (a.mode == 1) {
-                const uint2 w = __ldg(&a.tw[((size_t)a.mod[z] * a.cols + col) * a.Y + y]);
+                const uint2 w = wcur[j];
                 v = mul_shoup(v, w.x, w.y, q);
                 a.planes[(((size_t)z * a.rows + poly) * a.cols + col) * a.Y + y] = split_bf16x4(v);
             } else {
