@@ -61,7 +61,11 @@ struct GemmCfg {
     static constexpr int kABytes = kTileM * 128;
     static constexpr int kBBytes = 4 * NT * 128;
     static constexpr int kStageBytes = kABytes + kBBytes;
-    static constexpr int kStages = (200 * 1024) / kStageBytes > 4 ? 4 : (200 * 1024) / kStageBytes;
+    // two CTAs per SM (each with its own TMEM accumulators), so one CTA's epilogue overlaps the
+    // other's loads and MMAs; each gets half of the shared memory for its pipeline
+    static constexpr int kCtasPerSm = 2;
+    static constexpr int kBudget = (226 * 1024) / kCtasPerSm - 2048;
+    static constexpr int kStages = kBudget / kStageBytes > 4 ? 4 : kBudget / kStageBytes;
     static constexpr int kSmem = kStages * kStageBytes + 1024;
     static constexpr int kTmemCols = 4 * NT;
 };
@@ -107,7 +111,7 @@ __global__ void __launch_bounds__(256) tc_split_kernel(const uint32_t* __restric
 // Stages 2-5: one 128 x NT output tile of one limb per CTA; 4 warps.
 // thread 0 drives TMA, thread 32 issues the MMAs, all four warps run the epilogue.
 template <int NT>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128, GemmCfg<NT>::kCtasPerSm)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmArgs a) {
     using Cfg = GemmCfg<NT>;
     constexpr int S = Cfg::kStages;
@@ -392,6 +396,7 @@ int launch_gemm(const fhe_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb
                 cudaStream_t st) {
     using Cfg = GemmCfg<NT>;
     FHE_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem));
+    FHE_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<NT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     dim3 grid((g.rows * g.Y + kTileM - 1) / kTileM, g.cols / NT, nl);
     tc_gemm_kernel<NT><<<grid, 128, Cfg::kSmem, st>>>(ma, mb, g);
     FHE_CUDA_TRY(cudaGetLastError());
