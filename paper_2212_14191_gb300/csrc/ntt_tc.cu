@@ -84,28 +84,34 @@ __device__ __forceinline__ uint2 split_bf16x4(uint32_t v) {
 }
 
 // Stage 1: in[limb][poly] viewed as X x Y (row-major) -> planes[limb][poly][Y][X] of four
-// bf16 digits each. Block (32, 8) handles a 32 x 32 tile.
+// bf16 digits each. Block (32, 8) transposes a TS x TS tile (TS = 32 or 64; each thread has
+// TS * TS / 256 loads in flight) through shared memory; every thread then writes whole
+// 32-byte groups of four consecutive x.
+template <int TS>
 __global__ void __launch_bounds__(256) tc_split_kernel(const uint32_t* __restrict__ in, uint2* __restrict__ planes,
                                                        int X, int Y, int rows, size_t in_limb_stride, int N) {
-    __shared__ uint32_t tile[32][33];
+    __shared__ uint32_t tile[TS][TS + 1];
     const int z = blockIdx.z;
     const int limb = z / rows, poly = z % rows;
     const uint32_t* src = in + limb * in_limb_stride + (size_t)poly * N;
-    const int x0 = blockIdx.y * 32, y0 = blockIdx.x * 32;
+    const int x0 = blockIdx.y * TS, y0 = blockIdx.x * TS;
     const int tx = threadIdx.x, ty = threadIdx.y;
 #pragma unroll
-    for (int i = ty; i < 32; i += 8) tile[i][tx] = __ldg(&src[(size_t)(x0 + i) * Y + y0 + tx]);
+    for (int i = ty; i < TS; i += 8)
+#pragma unroll
+        for (int h = 0; h < TS / 32; ++h) tile[i][tx + 32 * h] = __ldg(&src[(size_t)(x0 + i) * Y + y0 + tx + 32 * h]);
     __syncthreads();
+    constexpr int XG = TS / 4;  // groups of four x per y
     const int t = ty * 32 + tx;
-    const int yy = t >> 3, xg = t & 7;
-    uint2* dst = planes + ((size_t)z * Y + y0 + yy) * X + x0 + xg * 4;
-    uint4 o0, o1;
-    uint2 p0 = split_bf16x4(tile[xg * 4 + 0][yy]), p1 = split_bf16x4(tile[xg * 4 + 1][yy]);
-    uint2 p2 = split_bf16x4(tile[xg * 4 + 2][yy]), p3 = split_bf16x4(tile[xg * 4 + 3][yy]);
-    o0 = make_uint4(p0.x, p0.y, p1.x, p1.y);
-    o1 = make_uint4(p2.x, p2.y, p3.x, p3.y);
-    reinterpret_cast<uint4*>(dst)[0] = o0;
-    reinterpret_cast<uint4*>(dst)[1] = o1;
+#pragma unroll
+    for (int u = t; u < TS * XG; u += 256) {
+        const int yy = u / XG, xg = u % XG;
+        uint2* dst = planes + ((size_t)z * Y + y0 + yy) * X + x0 + xg * 4;
+        const uint2 p0 = split_bf16x4(tile[xg * 4 + 0][yy]), p1 = split_bf16x4(tile[xg * 4 + 1][yy]);
+        const uint2 p2 = split_bf16x4(tile[xg * 4 + 2][yy]), p3 = split_bf16x4(tile[xg * 4 + 3][yy]);
+        reinterpret_cast<uint4*>(dst)[0] = make_uint4(p0.x, p0.y, p1.x, p1.y);
+        reinterpret_cast<uint4*>(dst)[1] = make_uint4(p2.x, p2.y, p3.x, p3.y);
+    }
 }
 
 // Stages 2-5: one 128 x NT output tile of one limb per CTA; 4 warps.
@@ -432,9 +438,15 @@ int ntt_tc(const fhe_ctx* cctx, uint32_t logN, bool inverse, uint32_t* d, int n_
             const int rows = std::min(nb, batch - b0);
             uint32_t* base = d + ((size_t)l0 * batch + b0) * N;
             // Stage 1
-            dim3 sg(Y1 / 32, X1 / 32, nl * rows);
-            tc_split_kernel<<<sg, dim3(32, 8), 0, st>>>(base, (uint2*)ctx->tc_planes[0], X1, Y1, rows,
-                                                        (size_t)batch * N, (int)N);
+            if (X1 >= 64 && Y1 >= 64) {
+                dim3 sg(Y1 / 64, X1 / 64, nl * rows);
+                tc_split_kernel<64><<<sg, dim3(32, 8), 0, st>>>(base, (uint2*)ctx->tc_planes[0], X1, Y1, rows,
+                                                                (size_t)batch * N, (int)N);
+            } else {
+                dim3 sg(Y1 / 32, X1 / 32, nl * rows);
+                tc_split_kernel<32><<<sg, dim3(32, 8), 0, st>>>(base, (uint2*)ctx->tc_planes[0], X1, Y1, rows,
+                                                                (size_t)batch * N, (int)N);
+            }
             FHE_CUDA_TRY(cudaGetLastError());
             GemmArgs g;
             memset(&g, 0, sizeof(g));
