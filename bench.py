@@ -128,7 +128,8 @@ class ClockSampler:
 def variant_name(v):
     """Plain-path kernel variant (see ntt_u32.cu) in words."""
     shape = "512-thread CTAs" if v & 1 == 0 else "256-thread CTAs"
-    ex = ["pull clusters", "push clusters", "split-forward clusters", "two-pass via L2"][(v >> 1) & 3]
+    ex = ["pull clusters", "push clusters", "split-forward clusters",
+          "two-pass via L2 (decimation-in-time forward)"][(v >> 1) & 3]
     extra = (", staged twiddles" if v & 8 else "") + (", 64 registers" if v & 16 else "")
     return "variant %d: %s, %s%s" % (v, shape, ex, extra)
 
@@ -297,7 +298,7 @@ def ours(args):
 
     def u32_launches(v):
         rows = NTT_LIMBS * NTT_BATCH
-        return 2 * (-(-rows // ((64 << 20) // (N * 4)))) if ((v >> 1) & 3) == 3 else 1
+        return 2 * (-(-rows // ((1 << 30) // (N * 4)))) if ((v >> 1) & 3) == 3 else 1   # 1 GiB chunks
 
     launches_per_step = {"u32": u32_launches(vf) + u32_launches(vi), "tc": 2 * 3 * (-(-NTT_LIMBS // chunk_limbs))}
     total_head = ops_per_step * args.steps * ws / (results[head]["kops"] * 1e3)
@@ -412,7 +413,8 @@ def ours(args):
             u32_gbs = u32_bytes / (results["u32"]["fwd_ms"] / 1e3) / 1e9
             roof_u32 = {"bound": "hbm", "achieved": u32_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                         "frac": u32_gbs / peaks["hbm_gbs"], "peak_kind": peak_kind,
-                        "kernel": "forward plain NTT launch at N=2^16 (%s), one launch per call" % variant_name(vf),
+                        "kernel": "forward plain NTT call at N=2^16 (%s), %d launch(es) per call"
+                                  % (variant_name(vf), u32_launches(vf)),
                         "traffic": traffic_for("paper_2212_14191_gb300/csrc/ntt_u32_kernels.cuh",
                                                "ntt_fwd_u32_n65536_v%d" % vf)}
             # the plain NTT is bound by integer multiplies, not HBM: 3 IMAD per Shoup modmul,

@@ -71,7 +71,8 @@ int fhe_gen_primes(uint32_t logN_max, int bits, int count, uint32_t* out);
  * Every prime must be distinct, prime, < 2^30 and = 1 mod 2^(logN_max+1); nq + np <= 64;
  * 1 <= alpha <= 15; np <= 15. The context owns its device tables and is immutable after
  * creation, so concurrent calls on different streams may share it.
- * Allocates device memory (cudaMalloc) on the current device; *out = NULL on failure.
+ * Allocates device memory (cudaMalloc) on the current device: the tables, and for
+ * logN_max >= 15 a 1 GiB scratch for the two-pass plain NTT; *out = NULL on failure.
  */
 int fhe_ctx_create(uint32_t logN_max, const uint32_t* q, int nq, const uint32_t* p, int np,
                    int alpha, int default_path, fhe_ctx** out);

@@ -47,7 +47,14 @@ uint32_t root_2n(uint32_t q, uint32_t logN);  // primitive 2N-th root from the s
 // Plain-path kernel shapes per ring degree: threads per CTA T = 2^log_t and CTAs per
 // cluster C = 2^log_c with 32 * T * C = N (see ntt_u32.cu).
 constexpr int kNttVariants = 32;
-constexpr size_t kNttTempBytes = 64ull << 20;
+#ifndef FHE_NTT_CHUNK_MIB
+#define FHE_NTT_CHUNK_MIB 1024
+#endif
+// scratch of the two-pass NTT, one chunk of rows at a time. Large chunks pay: each chunk is
+// two launches, and on GB300 a 1 GiB chunk (the whole 44 x 64 batch at 2^16 in one chunk)
+// measured 1.68 ms per forward + inverse against 1.97 ms with 64 MiB chunks; the scratch
+// spills from L2 either way.
+constexpr size_t kNttTempBytes = (size_t)FHE_NTT_CHUNK_MIB << 20;
 bool ntt_variant_shape(uint32_t logN, int variant, int* log_t, int* log_c);
 int ntt_variant_exchange(int variant);
 bool ntt_variant_tws(int variant);
@@ -60,6 +67,11 @@ struct NttTables {
     uint2* fwdC[2] = {};  // per shape: [nmod][C][31][T] last-round twiddles, per-thread order
     uint2* invC[2] = {};
     uint2* ninv = nullptr;  // [nmod] (N^-1 mod q, shoup)
+    // decimation-in-time two-pass forward (N >= 2^15), per shape with C = N / NC sub-NTTs of
+    // NC points: twist[nmod][C-1][NC] = psi^((2k'+1) j) for j = 1..C-1, and omega[nmod][C/2] =
+    // (psi^(2 NC))^m, the C-th roots of unity of the C-point DFT (all with Shoup quotients)
+    uint2* dit_twist[2] = {};
+    uint2* dit_omega[2] = {};
 };
 
 // Tensor-core path tables for one ring degree (device memory); see ntt_tc.cu. Built on the

@@ -238,7 +238,7 @@ int fhe_ctx_create(uint32_t logN_max, const uint32_t* q, int nq, const uint32_t*
     static const int kDefaultVariant[3][2] = {
         {16, 8},  // 2^14: single CTA at 64 registers / single CTA with staged twiddles
         {20, 7},  // 2^15: 2-CTA split forward at 64 registers / two-pass inverse, 256 threads
-        {4, 7},   // 2^16: 4-CTA split forward / two-pass inverse, 256 threads
+        {7, 7},   // 2^16: two-pass (decimation-in-time forward), 256 threads, both directions
     };
     for (int l = 14; l <= 16; ++l) {
         ctx->ntt_variant[0][l] = kDefaultVariant[l - 14][0];

@@ -99,6 +99,35 @@ int build_ntt_tables(fhe_ctx* ctx, uint32_t logN) {
     if ((rc = dev_upload(ctx, &t.fwd, fwd))) return rc;
     if ((rc = dev_upload(ctx, &t.inv, inv))) return rc;
     if ((rc = dev_upload(ctx, &t.ninv, ninv))) return rc;
+    // two-pass decimation-in-time forward: twists and C-th roots of unity per shape
+    for (int v = 0; v < 2 && logN >= 15; ++v) {
+        int log_t, log_c;
+        if (!ntt_variant_shape(logN, v, &log_t, &log_c)) continue;
+        const uint32_t C = 1u << log_c, NC = N >> log_c;
+        std::vector<uint2> twist((size_t)nmod * (C - 1) * NC), omega((size_t)nmod * (C / 2));
+        for (int m = 0; m < nmod; ++m) {
+            const uint32_t q = ctx->mods[m];
+            const uint32_t psi = root_2n(q, logN);
+            const uint32_t psi2 = mulmod_h(psi, psi, q);
+            uint32_t base = psi;  // psi^(2k'+1)
+            for (uint32_t k = 0; k < NC; ++k) {
+                uint32_t w = base;
+                for (uint32_t j = 1; j < C; ++j) {
+                    twist[((size_t)m * (C - 1) + (j - 1)) * NC + k] = make_uint2(w, shoup_h(w, q));
+                    w = mulmod_h(w, base, q);
+                }
+                base = mulmod_h(base, psi2, q);
+            }
+            const uint32_t om = powmod_h(psi, 2ull * NC, q);
+            uint32_t w = 1;
+            for (uint32_t j = 0; j < C / 2; ++j) {
+                omega[(size_t)m * (C / 2) + j] = make_uint2(w, shoup_h(w, q));
+                w = mulmod_h(w, om, q);
+            }
+        }
+        if ((rc = dev_upload(ctx, &t.dit_twist[v], twist))) return rc;
+        if ((rc = dev_upload(ctx, &t.dit_omega[v], omega))) return rc;
+    }
     return FHE_OK;
 }
 

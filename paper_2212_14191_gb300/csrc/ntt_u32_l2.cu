@@ -1,21 +1,24 @@
 // Plain 32-bit NTT for N >= 2^15 in two passes through L2 (no thread-block clusters).
 //
-// The merged Cooley-Tukey transform of ntt_u32.cu is split at the quarter boundary
-// (C = N / 2^14 quarters of NC = 2^14 residues, or 2 x 2^13 .. per kernel shape):
-//   forward: cross pass  -- the first log2(C) stages couple the C quarters of a row; a
-//                           streaming kernel applies them and writes the row to a scratch
-//                           buffer sized to stay in L2;
-//            quarter pass -- every quarter finishes its remaining stages in one CTA (the same
-//                           register/shared-memory rounds as the single-CTA kernel) and stores
-//                           its outputs k = k_local * C + rev(c) back into the row (in place:
-//                           the cross pass has already read the whole chunk);
-//   inverse: the same two passes in reverse order (quarter pass from the row into scratch,
-//            cross pass from scratch back into the row, with the N^-1 scaling).
-// Rows are processed in chunks whose scratch fits in L2, so the intermediate never reaches
-// HBM: each residue is read and written in HBM once, as in the cluster kernels, but every CTA
-// is independent and all SMs are usable.
+// A row of N = C * NC residues (NC = 2^14, or 2^13 for the 256-thread shape) is transformed
+// as C sub-transforms of NC points plus a C-point combination:
+//   forward (decimation in time): local pass -- every CTA runs the single-CTA NC-point
+//            transform (root psi^C, the library's root for that ring degree) on the
+//            decimated sequence a[j + C m] and writes it in natural order to a scratch buffer;
+//            cross pass -- a streaming kernel twists B_j[k'] by psi^((2k'+1) j), runs a
+//            C-point cyclic DFT and writes A[k' + NC t] back into the row;
+//   inverse (decimation in frequency): quarter pass -- every CTA gathers the outputs
+//            k = k_local * C + rev(c) of its quarter, runs the Gentleman-Sande stages of the
+//            quarter and writes the scratch; cross pass -- the last log2(C) stages couple the
+//            quarters and apply N^-1, writing the row.
+// Rows go through in chunks of up to 1 GiB of scratch (two launches per chunk); the scratch
+// round trip costs HBM traffic (it does not stay in L2 at these sizes), but every CTA is
+// independent, all SMs are usable and no cluster barrier is needed, which on GB300 outweighs
+// it. The strided side of both forms is a read (the C CTAs of a row share every sector
+// through L2): stores stay contiguous.
 #include "common.cuh"
 #include "ptx.cuh"
+
 
 namespace fhe {
 namespace {
@@ -30,6 +33,10 @@ struct L2Args {
     const uint2* tw;     // [nmod][N]
     const uint2* twC;    // [nmod][C][31][T]
     const uint2* ninv;   // [nmod]
+    const uint2* tw_sub;     // decimation-in-time forward: tables of the NC-point ring degree
+    const uint2* twC_sub;    // [nmod][1][31][T]
+    const uint2* twist;      // [nmod][C-1][NC]
+    const uint2* omega;      // [nmod][C/2]
     LimbMap map;
 };
 
@@ -64,133 +71,50 @@ __device__ __forceinline__ void gs2(uint32_t& x, uint32_t& y, uint2 w, uint32_t 
     y = mul_shoup_lazy(d, w.x, w.y, q);
 }
 
-// ---- cross pass: grid (blocks over NC/4 quad positions, chunk rows); 4 positions per thread
-template <int LOG_NC, int LOG_C, bool INV>
-__global__ void __launch_bounds__(256) ntt_cross_kernel(const L2Args a) {
+// ---- inverse cross pass: grid (blocks over NC/4 quad positions, chunk rows); 4 positions per
+// thread; the last log2(C) Gentleman-Sande stages and the N^-1 scaling
+template <int LOG_NC, int LOG_C>
+__global__ void __launch_bounds__(256) ntt_cross_inv_kernel(const L2Args a) {
     constexpr int NC = 1 << LOG_NC, C = 1 << LOG_C, N = NC * C;
     const int i = blockIdx.y;
     uint32_t q;
     int mod;
     uint32_t* row = l2_row<N>(a, a.r0 + i, &q, &mod);
-    uint32_t* tmp = a.temp + (size_t)i * N;
+    const uint32_t* tmp = a.temp + (size_t)i * N;
     const uint2* tw = a.tw + (size_t)mod * N;
-    const uint32_t* src = INV ? tmp : row;
-    uint32_t* dst = INV ? row : tmp;
-    uint2 ni = make_uint2(0, 0);
-    if (INV) ni = __ldg(&a.ninv[mod]);
+    const uint2 ni = __ldg(&a.ninv[mod]);
     for (int p4 = blockIdx.x * blockDim.x + threadIdx.x; p4 < NC / 4; p4 += gridDim.x * blockDim.x) {
         uint4 x[C];
 #pragma unroll
-        for (int qq = 0; qq < C; ++qq) x[qq] = __ldg(reinterpret_cast<const uint4*>(src + qq * NC) + p4);
+        for (int qq = 0; qq < C; ++qq) x[qq] = __ldcg(reinterpret_cast<const uint4*>(tmp + qq * NC) + p4);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             uint32_t y[C];
 #pragma unroll
             for (int qq = 0; qq < C; ++qq) y[qq] = k == 0 ? x[qq].x : k == 1 ? x[qq].y : k == 2 ? x[qq].z : x[qq].w;
-            if (!INV) {
 #pragma unroll
-                for (int s = 0; s < LOG_C; ++s) {
-                    const int tq = C >> (s + 1);
+            for (int s = LOG_C - 1; s >= 0; --s) {
+                const int tq = C >> (s + 1);
 #pragma unroll
-                    for (int qq = 0; qq < C; ++qq)
-                        if ((qq / tq) % 2 == 0) ct2(y[qq], y[qq + tq], __ldg(&tw[(1 << s) + qq / (2 * tq)]), q);
-                }
-            } else {
-#pragma unroll
-                for (int s = LOG_C - 1; s >= 0; --s) {
-                    const int tq = C >> (s + 1);
-#pragma unroll
-                    for (int qq = 0; qq < C; ++qq)
-                        if ((qq / tq) % 2 == 0) gs2(y[qq], y[qq + tq], __ldg(&tw[(1 << s) + qq / (2 * tq)]), q);
-                }
-#pragma unroll
-                for (int qq = 0; qq < C; ++qq) y[qq] = mul_shoup(y[qq], ni.x, ni.y, q);
+                for (int qq = 0; qq < C; ++qq)
+                    if ((qq / tq) % 2 == 0) gs2(y[qq], y[qq + tq], __ldg(&tw[(1 << s) + qq / (2 * tq)]), q);
             }
 #pragma unroll
             for (int qq = 0; qq < C; ++qq) {
-                if (k == 0) x[qq].x = y[qq];
-                else if (k == 1) x[qq].y = y[qq];
-                else if (k == 2) x[qq].z = y[qq];
-                else x[qq].w = y[qq];
+                const uint32_t v = mul_shoup(y[qq], ni.x, ni.y, q);
+                if (k == 0) x[qq].x = v;
+                else if (k == 1) x[qq].y = v;
+                else if (k == 2) x[qq].z = v;
+                else x[qq].w = v;
             }
         }
 #pragma unroll
-        for (int qq = 0; qq < C; ++qq) reinterpret_cast<uint4*>(dst + qq * NC)[p4] = x[qq];
+        for (int qq = 0; qq < C; ++qq) reinterpret_cast<uint4*>(row + qq * NC)[p4] = x[qq];
     }
 }
 
 template <int LOG_T>
 constexpr int kMinB = (1 << (14 - LOG_T)) / 32 > 0 ? (1 << (14 - LOG_T)) / 32 : 1;
-
-// ---- quarter pass, forward: scratch quarter c -> remaining stages -> row (stride C)
-template <int LOG_T, int LOG_C>
-__global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_quarter_fwd_kernel(const L2Args a) {
-    constexpr int T = 1 << LOG_T, C = 1 << LOG_C, NC = 32 * T, N = NC * C, RB = LOG_T - 5;
-    extern __shared__ __align__(128) uint32_t work[];
-    const int tid = threadIdx.x, c = blockIdx.x, i = blockIdx.y;
-    const int rc = rbits<LOG_C>(c);
-    using L = PadLayout<LOG_T>;
-    const int pA = L::pad(tid);
-    uint32_t q;
-    int mod;
-    uint32_t* row = l2_row<N>(a, a.r0 + i, &q, &mod);
-    const uint32_t* tmp = a.temp + (size_t)i * N + c * NC;
-    const uint2* tw = a.tw + (size_t)mod * N;
-    uint32_t v[32];
-#pragma unroll
-    for (int e = 0; e < 32; ++e) v[e] = __ldcg(&tmp[tid + T * e]);
-    // round A
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        const int half = 16 >> k;
-#pragma unroll
-        for (int e = 0; e < 32; ++e)
-            if ((e & half) == 0) ct2(v[e], v[e + half], __ldg(&tw[(1 << k) * (C + c) + (e >> (5 - k))]), q);
-    }
-#pragma unroll
-    for (int e = 0; e < 32; ++e) work[pA + L::kSA * e] = v[e];
-    __syncthreads();
-    // round B
-    if constexpr (RB > 0) {
-        constexpr int GPT = 32 >> RB, EG = 1 << RB;
-        const int lane = tid & 31, w_ = tid >> 5;
-#pragma unroll
-        for (int gi = 0; gi < GPT; ++gi) {
-            const int g = w_ * GPT + gi;
-            uint32_t* vv = v + gi * EG;
-#pragma unroll
-            for (int e = 0; e < EG; ++e) vv[e] = work[g * L::kSA + lane + 33 * e];
-#pragma unroll
-            for (int k = 0; k < RB; ++k) {
-                const int half = EG >> (k + 1);
-#pragma unroll
-                for (int e = 0; e < EG; ++e)
-                    if ((e & half) == 0)
-                        ct2(vv[e], vv[e + half], __ldg(&tw[(1 << k) * (32 * (C + c) + g) + (e >> (RB - k))]), q);
-            }
-#pragma unroll
-            for (int e = 0; e < EG; ++e) work[g * L::kSA + lane + 33 * e] = vv[e];
-        }
-        __syncthreads();
-    }
-    // round C
-    {
-        const int gidx = rbits<LOG_T>(tid);
-        const int pC = L::pad(32 * gidx);
-#pragma unroll
-        for (int e = 0; e < 32; ++e) v[e] = work[pC + e];
-        const uint2* twc = a.twC + (((size_t)mod * C + c) * 31) * T + tid;
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            const int half = 16 >> k;
-#pragma unroll
-            for (int e = 0; e < 32; ++e)
-                if ((e & half) == 0) ct2(v[e], v[e + half], __ldg(&twc[(size_t)((1 << k) - 1 + (e >> (5 - k))) * T]), q);
-        }
-    }
-#pragma unroll
-    for (int e = 0; e < 32; ++e) row[(rbits<5>(e) * T + tid) * C + rc] = csub(csub(v[e], 2 * q), q);
-}
 
 // ---- quarter pass, inverse: row (stride C, quarter c's bit-reversed share) -> GS stages -> scratch
 template <int LOG_T, int LOG_C>
@@ -263,16 +187,169 @@ __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_quarter_inv_kern
     for (int e = 0; e < 32; ++e) __stcg(&tmp[tid + T * e], v[e]);
 }
 
+// ---- decimation-in-time forward (the two-pass forward): with n = C m + j and
+// k = k' + NC t,
+//   A_k = sum_j omega^(t j) psi^((2k'+1) j) B_j[k'],   B_j = NTT_NC(a[j + C m], psi^C),
+// omega = psi^(2 NC) a C-th root of unity. psi^C is the NC-point root the library uses for
+// that ring degree, so pass 1 is the single-CTA NC-point transform (its tables, natural-
+// order output) of a decimated row; pass 2 twists and runs a C-point cyclic DFT, reading C
+// contiguous streams and writing C contiguous streams. Pass 1 reads at stride C (the C CTAs
+// of a row share every sector through L2), where the decimation-in-frequency order would
+// store at stride C.
+template <int LOG_T, int LOG_C>
+__global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_dit_local_kernel(const L2Args a) {
+    constexpr int T = 1 << LOG_T, C = 1 << LOG_C, NC = 32 * T, N = NC * C, RB = LOG_T - 5;
+    extern __shared__ __align__(128) uint32_t work[];
+    const int tid = threadIdx.x, j = blockIdx.x, i = blockIdx.y;
+    using L = PadLayout<LOG_T>;
+    const int pA = L::pad(tid);
+    uint32_t q;
+    int mod;
+    const uint32_t* row = l2_row<N>(a, a.r0 + i, &q, &mod);
+    uint32_t* tmp = a.temp + (size_t)i * N + (size_t)j * NC;
+    const uint2* tw = a.tw_sub + (size_t)mod * NC;
+    uint32_t v[32];
+#pragma unroll
+    for (int e = 0; e < 32; ++e) v[e] = __ldg(&row[(size_t)(tid + T * e) * C + j]);
+    // round A: stages 0..4 of the NC-point transform
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int half = 16 >> k;
+#pragma unroll
+        for (int e = 0; e < 32; ++e)
+            if ((e & half) == 0) ct2(v[e], v[e + half], __ldg(&tw[(1 << k) + (e >> (5 - k))]), q);
+    }
+#pragma unroll
+    for (int e = 0; e < 32; ++e) work[pA + L::kSA * e] = v[e];
+    __syncthreads();
+    // round B
+    if constexpr (RB > 0) {
+        constexpr int GPT = 32 >> RB, EG = 1 << RB;
+        const int lane = tid & 31, w_ = tid >> 5;
+#pragma unroll
+        for (int gi = 0; gi < GPT; ++gi) {
+            const int g = w_ * GPT + gi;
+            uint32_t* vv = v + gi * EG;
+#pragma unroll
+            for (int e = 0; e < EG; ++e) vv[e] = work[g * L::kSA + lane + 33 * e];
+#pragma unroll
+            for (int k = 0; k < RB; ++k) {
+                const int half = EG >> (k + 1);
+#pragma unroll
+                for (int e = 0; e < EG; ++e)
+                    if ((e & half) == 0)
+                        ct2(vv[e], vv[e + half], __ldg(&tw[(1 << k) * (32 + g) + (e >> (RB - k))]), q);
+            }
+#pragma unroll
+            for (int e = 0; e < EG; ++e) work[g * L::kSA + lane + 33 * e] = vv[e];
+        }
+        __syncthreads();
+    }
+    // round C: last five stages, per-thread twiddle columns of the single-CTA shape
+    {
+        const int gidx = rbits<LOG_T>(tid);
+        const int pC = L::pad(32 * gidx);
+#pragma unroll
+        for (int e = 0; e < 32; ++e) v[e] = work[pC + e];
+        const uint2* twc = a.twC_sub + ((size_t)mod * 31) * T + tid;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const int half = 16 >> k;
+#pragma unroll
+            for (int e = 0; e < 32; ++e)
+                if ((e & half) == 0) ct2(v[e], v[e + half], __ldg(&twc[(size_t)((1 << k) - 1 + (e >> (5 - k))) * T]), q);
+        }
+    }
+    // natural order: thread tid holds k' = rev5(e) T + tid
+#pragma unroll
+    for (int e = 0; e < 32; ++e) __stcg(&tmp[rbits<5>(e) * T + tid], csub(csub(v[e], 2 * q), q));
+}
+
+template <int LOG_NC, int LOG_C>
+__global__ void __launch_bounds__(256) ntt_dit_cross_kernel(const L2Args a) {
+    constexpr int NC = 1 << LOG_NC, C = 1 << LOG_C, N = NC * C;
+    const int i = blockIdx.y;
+    uint32_t q;
+    int mod;
+    uint32_t* row = l2_row<N>(a, a.r0 + i, &q, &mod);
+    const uint32_t* tmp = a.temp + (size_t)i * N;
+    const uint2* twist = a.twist + (size_t)mod * (C - 1) * NC;
+    const uint2* om = a.omega + (size_t)mod * (C / 2);
+    uint2 omv[C / 2];
+#pragma unroll
+    for (int m = 0; m < C / 2; ++m) omv[m] = __ldg(&om[m]);
+    for (int p4 = blockIdx.x * blockDim.x + threadIdx.x; p4 < NC / 4; p4 += gridDim.x * blockDim.x) {
+        uint4 x[C];
+#pragma unroll
+        for (int jj = 0; jj < C; ++jj) x[jj] = __ldcg(reinterpret_cast<const uint4*>(tmp + jj * NC) + p4);
+        uint4 tw2[C > 1 ? 2 * (C - 1) : 1];  // four twist pairs of every j >= 1: two uint4 each
+#pragma unroll
+        for (int jj = 1; jj < C; ++jj) {
+            const uint4* tp = reinterpret_cast<const uint4*>(twist + (size_t)(jj - 1) * NC + 4 * p4);
+            tw2[2 * (jj - 1)] = __ldg(tp);
+            tw2[2 * (jj - 1) + 1] = __ldg(tp + 1);
+        }
+        uint4 o[C];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t y[C];
+#pragma unroll
+            for (int jj = 0; jj < C; ++jj) y[jj] = k == 0 ? x[jj].x : k == 1 ? x[jj].y : k == 2 ? x[jj].z : x[jj].w;
+#pragma unroll
+            for (int jj = 1; jj < C; ++jj) {
+                const uint4 t4 = tw2[2 * (jj - 1) + (k >> 1)];
+                const uint2 w = (k & 1) ? make_uint2(t4.z, t4.w) : make_uint2(t4.x, t4.y);
+                y[jj] = mul_shoup(y[jj], w.x, w.y, q);  // [0, q)
+            }
+            // C-point cyclic DFT, radix-2 decimation in frequency: position p ends up holding
+            // output t = rev(p); values stay in [0, 2q)
+#pragma unroll
+            for (int s = 0; s < LOG_C; ++s) {
+                const int h = C >> (s + 1);
+#pragma unroll
+                for (int b = 0; b < C; b += 2 * h)
+#pragma unroll
+                    for (int jj = 0; jj < h; ++jj) {
+                        const int m = jj << s;  // omega^m
+                        if (m == 0) {
+                            const uint32_t su = csub(y[b + jj] + y[b + jj + h], 2 * q);
+                            const uint32_t di = csub(y[b + jj] - y[b + jj + h] + 2 * q, 2 * q);
+                            y[b + jj] = su;
+                            y[b + jj + h] = di;
+                        } else {
+                            gs2(y[b + jj], y[b + jj + h], omv[m], q);
+                        }
+                    }
+            }
+#pragma unroll
+            for (int p = 0; p < C; ++p) {
+                const int t = rbits<LOG_C>(p);
+                const uint32_t val = csub(y[p], q);
+                if (k == 0) o[t].x = val;
+                else if (k == 1) o[t].y = val;
+                else if (k == 2) o[t].z = val;
+                else o[t].w = val;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < C; ++t) reinterpret_cast<uint4*>(row + t * NC)[p4] = o[t];
+    }
+}
+
 template <int LOG_T, int LOG_C>
 int run_l2(const fhe_ctx* ctx, const NttTables& t, int shape, bool inverse, uint32_t* d, int rows, int batch,
            const LimbMap& map, const RowRef* rowtab, cudaStream_t st) {
     constexpr int T = 1 << LOG_T, C = 1 << LOG_C, NC = 32 * T, N = NC * C;
     constexpr int smem = PadLayout<LOG_T>::kWords * 4;
-    auto qk = inverse ? ntt_quarter_inv_kernel<LOG_T, LOG_C> : ntt_quarter_fwd_kernel<LOG_T, LOG_C>;
-    auto xk = inverse ? ntt_cross_kernel<LOG_T + 5, LOG_C, true> : ntt_cross_kernel<LOG_T + 5, LOG_C, false>;
+    // forward: decimation in time (local NC-point transforms, then twist + C-point DFT);
+    // inverse: decimation in frequency (quarter pass, then cross stages with N^-1)
+    auto qk = inverse ? ntt_quarter_inv_kernel<LOG_T, LOG_C> : ntt_dit_local_kernel<LOG_T, LOG_C>;
     FHE_CUDA_TRY(cudaFuncSetAttribute(qk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int carve = (int)((kMinB<LOG_T> * (smem + 1024) * 100 + 228 * 1024 - 1) / (228 * 1024));
     FHE_CUDA_TRY(cudaFuncSetAttribute(qk, cudaFuncAttributePreferredSharedMemoryCarveout, carve > 100 ? 100 : carve));
+    const NttTables& ts = ctx->ntt[LOG_T + 5];  // the NC-point ring degree of the local passes
+    if (!inverse && (!ts.fwd || !ts.fwdC[0] || !t.dit_twist[shape] || !t.dit_omega[shape]))
+        return set_error(FHE_EINVAL, "two-pass forward tables missing");
     L2Args a;
     a.data = d;
     a.batch = batch;
@@ -282,22 +359,23 @@ int run_l2(const fhe_ctx* ctx, const NttTables& t, int shape, bool inverse, uint
     a.tw = inverse ? t.inv : t.fwd;
     a.twC = inverse ? t.invC[shape] : t.fwdC[shape];
     a.ninv = t.ninv;
+    a.tw_sub = ts.fwd;
+    a.twC_sub = ts.fwdC[0];
+    a.twist = t.dit_twist[shape];
+    a.omega = t.dit_omega[shape];
     a.map = map;
     const int chunk = (int)(kNttTempBytes / ((size_t)N * 4));
     const int gx = (NC / 4 + 255) / 256;
     for (int r0 = 0; r0 < rows; r0 += chunk) {
         a.r0 = r0;
         a.nrows = rows - r0 < chunk ? rows - r0 : chunk;
-        if (!inverse) {
-            xk<<<dim3(gx, a.nrows), 256, 0, st>>>(a);
-            FHE_CUDA_TRY(cudaGetLastError());
-        }
         qk<<<dim3(C, a.nrows), T, smem, st>>>(a);
         FHE_CUDA_TRY(cudaGetLastError());
-        if (inverse) {
-            xk<<<dim3(gx, a.nrows), 256, 0, st>>>(a);
-            FHE_CUDA_TRY(cudaGetLastError());
-        }
+        if (inverse)
+            ntt_cross_inv_kernel<LOG_T + 5, LOG_C><<<dim3(gx, a.nrows), 256, 0, st>>>(a);
+        else
+            ntt_dit_cross_kernel<LOG_T + 5, LOG_C><<<dim3(gx, a.nrows), 256, 0, st>>>(a);
+        FHE_CUDA_TRY(cudaGetLastError());
     }
     return FHE_OK;
 }
