@@ -93,6 +93,11 @@ int fhe_ntt_fwd(const fhe_ctx* ctx, int path, uint32_t logN, uint32_t* d, int fi
                 int n_limbs, int batch, void* stream);
 
 /*
+ * Plain-path variants that run in two passes (and the tensor-core path) use buffers owned
+ * by the context: fhe_ntt_fwd / fhe_ntt_inv calls on one context must not overlap in time on
+ * different streams. The CKKS calls below take the two-pass buffer from the caller's
+ * scratch and may overlap freely on the plain path.
+ *
  * fhe_ntt_inv -- in-place inverse of fhe_ntt_fwd (Sec. II-A, Eq. (2) with the psi^-n
  * post-twist of Eq. (3); Sec. IV-C Stage 5 names the N^-1 factor):
  *     a_n = N^-1 * psi^-n * sum_{k<N} A_k * psi^(-2nk) mod q.

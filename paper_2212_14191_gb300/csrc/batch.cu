@@ -89,9 +89,14 @@ bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 int run_batch(const fhe_batch* b, void* scratch, cudaStream_t st) {
     const fhe_ctx* ctx = b->ctx;
     int rc;
-    for (const NttGroup& g : b->ntt)
-        if ((rc = ntt_u32_rows(ctx, g.logN, g.inverse, g.d_rows, g.nrows, st))) return rc;
     uint8_t* base = (uint8_t*)scratch;
+    // the NTT groups run first and use the start of the scratch for their two-pass chunks
+    for (const NttGroup& g : b->ntt) {
+        NttScratch ns;
+        ns.bytes = ntt_region_bytes(g.logN, (size_t)g.nrows);
+        if (ns.bytes) ns.p = (uint32_t*)base;
+        if ((rc = ntt_u32_rows(ctx, g.logN, g.inverse, g.d_rows, g.nrows, st, ns))) return rc;
+    }
     for (const HmGroup& g : b->hm) {
         const unsigned gx = (unsigned)std::min<uint64_t>((g.max_seg4 + 255) / 256, 1024);
         k_segcopy<<<dim3(gx, g.nin), 256, 0, st>>>(g.d_in, base);
@@ -149,6 +154,7 @@ int fhe_batch_create(const fhe_ctx* ctx, const fhe_op* ops, int n, fhe_batch** o
         g.inverse = kv.first.second != 0;
         g.nrows = (int)kv.second.size();
         if ((rc = upload(b, &g.d_rows, kv.second))) break;
+        b->scratch_bytes = std::max(b->scratch_bytes, ntt_region_bytes(g.logN, (size_t)g.nrows));
         b->ntt.push_back(g);
         b->n_launch += 1;
     }

@@ -382,7 +382,7 @@ size_t ks_scratch_limbs(int nl, int K, int alpha) {
 // d2c (nl limbs of scratch) may already hold a copy of d2 when d2c_ready != 0.
 int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint32_t* d2,
                    const uint32_t* evk, uint32_t* out, int accumulate, uint32_t* scratch,
-                   bool d2c_ready, cudaStream_t st) {
+                   bool d2c_ready, cudaStream_t st, NttScratch ns) {
     const size_t N = 1ull << logN, limb = N * batch, L4 = limb / 4;
     const int K = ctx->np, ext = nl + K, alpha = ctx->alpha, nq = ctx->nq;
     const int nmod = (int)ctx->mods.size();
@@ -394,7 +394,7 @@ int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const u
     int rc;
     if (!d2c_ready) FHE_CUDA_TRY(cudaMemcpyAsync(d2c, d2, (size_t)nl * limb * 4, cudaMemcpyDeviceToDevice, st));
     // KS-1: INTT(d2)
-    if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, true, d2c, nl, batch, contiguous_map(ctx, 0, nl), st))) return rc;
+    if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, true, d2c, nl, batch, contiguous_map(ctx, 0, nl), st, ns))) return rc;
     int ext_mod[kMaxLimbs];
     for (int t = 0; t < ext; ++t) ext_mod[t] = t < nl ? t : nq + (t - nl);
     ModVec ext_m = modvec(ctx, ext_mod, ext);
@@ -434,7 +434,7 @@ int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const u
             lm.mod[t] = (uint8_t)dmod[t];
             lm.q[t] = ctx->mods[dmod[t]];
         }
-        if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, false, tmp, nd, batch, lm, st))) return rc;
+        if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, false, tmp, nd, batch, lm, st, ns))) return rc;
     }
     // KS-4: inner product over all slices
     {
@@ -458,7 +458,7 @@ int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const u
     // KS-5: ModDown of ks0, ks1
     LimbMap pm = contiguous_map(ctx, nq, K);
     for (int c = 0; c < 2; ++c)
-        if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, true, ks + ((size_t)c * ext + nl) * limb, K, batch, pm, st)))
+        if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, true, ks + ((size_t)c * ext + nl) * limb, K, batch, pm, st, ns)))
             return rc;
     for (int c = 0; c < 2; ++c) {
         ConvArgs ca;
@@ -494,7 +494,7 @@ int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const u
         }
     // the caller fuses the ModDown combine into RESCALE and takes y in the coefficient domain
     if (out == nullptr) return FHE_OK;
-    if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, false, y, 2 * nl, batch, qm2, st))) return rc;
+    if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, false, y, 2 * nl, batch, qm2, st, ns))) return rc;
     int qidx[kMaxLimbs];
     for (int i = 0; i < nl; ++i) qidx[i] = i;
     k_moddown_combine<<<stream_grid(ctx, L4, 2 * nl), 256, 0, st>>>(ks, y, out, ctx->p_inv, nl, ext, accumulate,
@@ -505,19 +505,27 @@ int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const u
 
 size_t rescale_scratch_limbs(int nl) { return 2 + 2 * (size_t)(nl - 1); }
 
+// RESCALE needs no extra NTT region: the INTT of the last limb chunks through the (still
+// unused) broadcast buffer, and the NTT of the broadcast through the last-limb buffer once
+// the broadcast has consumed it.
 int rescale_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint32_t* ct, uint32_t* out,
                  uint32_t* scratch, cudaStream_t st) {
     const size_t N = 1ull << logN, limb = N * batch, L4 = limb / 4;
     const int nout = nl - 1;
     uint32_t* last = scratch;
     uint32_t* xb = last + 2 * limb;
+    NttScratch ns_last, ns_xb;
+    ns_last.p = xb;
+    ns_last.bytes = 2 * (size_t)nout * limb * 4;
+    ns_xb.p = last;
+    ns_xb.bytes = 2 * limb * 4;
     int rc;
     k_copy_limb<<<stream_grid(ctx, L4, 2), 256, 0, st>>>(ct, last, nl, L4);
     FHE_CUDA_TRY(cudaGetLastError());
     LimbMap lm;
     lm.mod[0] = lm.mod[1] = (uint8_t)(nl - 1);
     lm.q[0] = lm.q[1] = ctx->mods[nl - 1];
-    if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, true, last, 2, batch, lm, st))) return rc;
+    if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, true, last, 2, batch, lm, st, ns_last))) return rc;
     int qidx[kMaxLimbs];
     for (int i = 0; i < nout; ++i) qidx[i] = i;
     ModVec qm = modvec(ctx, qidx, nout);
@@ -530,7 +538,7 @@ int rescale_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uin
             qm2.mod[c * nout + i] = (uint8_t)i;
             qm2.q[c * nout + i] = ctx->mods[i];
         }
-    if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, false, xb, 2 * nout, batch, qm2, st))) return rc;
+    if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, false, xb, 2 * nout, batch, qm2, st, ns_xb))) return rc;
     k_rescale_final<<<stream_grid(ctx, L4, 2 * nout), 256, 0, st>>>(ct, xb, out, ctx->ql_inv + (size_t)(nl - 1) * ctx->nq,
                                                                    nl, L4, qm);
     FHE_CUDA_TRY(cudaGetLastError());
@@ -538,7 +546,7 @@ int rescale_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uin
 }
 
 int hmult_relin_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint32_t* a, const uint32_t* b,
-                     const uint32_t* evk, uint32_t* out, uint32_t* scratch, cudaStream_t st) {
+                     const uint32_t* evk, uint32_t* out, uint32_t* scratch, cudaStream_t st, NttScratch ns) {
     const size_t N = 1ull << logN, limb = N * batch, L4 = limb / 4;
     uint32_t* d2 = scratch;
     uint32_t* ks_scratch = d2 + (size_t)nl * limb;  // begins with d2c
@@ -547,7 +555,7 @@ int hmult_relin_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const
     k_tensor<<<stream_grid(ctx, L4, nl), 256, 0, st>>>(a, b, out, out + (size_t)nl * limb, d2, ks_scratch, L4,
                                                      (size_t)nl * L4, modvec(ctx, qidx, nl));
     FHE_CUDA_TRY(cudaGetLastError());
-    return keyswitch_impl(ctx, logN, nl, batch, d2, evk, out, 1, ks_scratch, true, st);
+    return keyswitch_impl(ctx, logN, nl, batch, d2, evk, out, 1, ks_scratch, true, st, ns);
 }
 
 // HMULT + RESCALE with the fused tail (k_relin_last .. k_hmult_final above): one forward NTT of
@@ -556,7 +564,7 @@ int hmult_relin_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const
 // outputs, ks, y); after the inner product the d2c / ModUp region is reused for the last limb
 // and z (2 + 2 (nl - 1) limbs, which fit: nl + dnum (nl + K) >= 2 nl).
 int hmult_fused(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint32_t* a, const uint32_t* b,
-                const uint32_t* evk, uint32_t* out, uint32_t* scratch, cudaStream_t st) {
+                const uint32_t* evk, uint32_t* out, uint32_t* scratch, cudaStream_t st, NttScratch ns) {
     const size_t N = 1ull << logN, limb = N * batch, L4 = limb / 4;
     const int K = ctx->np, ext = nl + K, alpha = ctx->alpha;
     const int dnum = (nl + alpha - 1) / alpha;
@@ -572,7 +580,7 @@ int hmult_fused(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint
     k_tensor<<<stream_grid(ctx, L4, nl), 256, 0, st>>>(a, b, dd, dd + (size_t)nl * limb, d2, ksx, L4,
                                                      (size_t)nl * L4, modvec(ctx, qidx, nl));
     FHE_CUDA_TRY(cudaGetLastError());
-    int rc = keyswitch_impl(ctx, logN, nl, batch, d2, evk, nullptr, 0, ksx, true, st);
+    int rc = keyswitch_impl(ctx, logN, nl, batch, d2, evk, nullptr, 0, ksx, true, st, ns);
     if (rc) return rc;
     const uint32_t ql = ctx->mods[nl - 1];
     const uint2 pinv_l = ctx->p_inv_h[nl - 1];
@@ -581,7 +589,7 @@ int hmult_fused(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint
     LimbMap lm;
     lm.mod[0] = lm.mod[1] = (uint8_t)(nl - 1);
     lm.q[0] = lm.q[1] = ql;
-    if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, true, last, 2, batch, lm, st))) return rc;
+    if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, true, last, 2, batch, lm, st, ns))) return rc;
     k_last_fix<<<stream_grid(ctx, L4, 2), 256, 0, st>>>(y, last, pinv_l, ql, nl, L4);
     FHE_CUDA_TRY(cudaGetLastError());
     const int nout = nl - 1;
@@ -594,7 +602,7 @@ int hmult_fused(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint
             qm2.mod[c * nout + i] = (uint8_t)i;
             qm2.q[c * nout + i] = ctx->mods[i];
         }
-    if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, false, xb, 2 * nout, batch, qm2, st))) return rc;
+    if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, false, xb, 2 * nout, batch, qm2, st, ns))) return rc;
     k_hmult_final<<<stream_grid(ctx, L4, 2 * nout), 256, 0, st>>>(dd, ks, xb, out, ctx->p_inv,
                                                                 ctx->ql_inv + (size_t)(nl - 1) * ctx->nq, nl, ext,
                                                                 L4, qm);
@@ -675,14 +683,14 @@ __global__ void k_hadd(const uint32_t* __restrict__ a, const uint32_t* __restric
 size_t hrotate_scratch_limbs(int nl, int K, int alpha) { return (size_t)nl + ks_scratch_limbs(nl, K, alpha); }
 
 int hrotate_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, uint32_t k, const uint32_t* ct,
-                 const uint32_t* ksk, uint32_t* out, uint32_t* scratch, cudaStream_t st) {
+                 const uint32_t* ksk, uint32_t* out, uint32_t* scratch, cudaStream_t st, NttScratch ns) {
     const size_t limb = ((size_t)1 << logN) * batch, rows = (size_t)nl * batch;
     uint32_t* c1k = scratch;
     int rc;
     if ((rc = launch_automorph(ctx, ct, out, k, logN, rows, st))) return rc;
     if ((rc = launch_automorph(ctx, ct + (size_t)nl * limb, c1k, k, logN, rows, st))) return rc;
     FHE_CUDA_TRY(cudaMemsetAsync(out + (size_t)nl * limb, 0, (size_t)nl * limb * 4, st));
-    return keyswitch_impl(ctx, logN, nl, batch, c1k, ksk, out, 1, c1k + (size_t)nl * limb, false, st);
+    return keyswitch_impl(ctx, logN, nl, batch, c1k, ksk, out, 1, c1k + (size_t)nl * limb, false, st, ns);
 }
 
 bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -701,6 +709,10 @@ int check_ptrs(std::initializer_list<const void*> ps) {
     return FHE_OK;
 }
 
+// Rows of the largest NTT call an operation makes, per ciphertext of the batch.
+// RESCALE chunks through its own buffers (rescale_impl) and needs none.
+size_t ntt_rows(const fhe_ctx* ctx, int op, int nl) { return op == FHE_OP_RESCALE ? 0 : 2 * ((size_t)nl + ctx->np); }
+
 size_t scratch_limbs(const fhe_ctx* ctx, int op, int nl) {
     const int K = ctx->np;
     switch (op) {
@@ -711,6 +723,14 @@ size_t scratch_limbs(const fhe_ctx* ctx, int op, int nl) {
         case FHE_OP_HROTATE: return hrotate_scratch_limbs(nl, K, ctx->alpha);
         default: return 0;
     }
+}
+
+// The two-pass NTT region of an operation's caller scratch (after the operation's limbs).
+NttScratch op_ntt_scratch(const fhe_ctx* ctx, int op, uint32_t logN, int nl, int batch, void* scratch) {
+    NttScratch s;
+    s.bytes = ntt_region_bytes(logN, ntt_rows(ctx, op, nl) * batch);
+    if (s.bytes) s.p = (uint32_t*)((uint8_t*)scratch + scratch_limbs(ctx, op, nl) * ((size_t)batch << logN) * 4);
+    return s;
 }
 
 }  // namespace
@@ -725,7 +745,10 @@ size_t fhe_scratch_bytes(const fhe_ctx* ctx, int op, uint32_t logN, int n_limbs,
         n_limbs > ctx->nq || batch < 0)
         return 0;
     if ((op == FHE_OP_RESCALE || op == FHE_OP_HMULT) && n_limbs < 2) return 0;
-    return scratch_limbs(ctx, op, n_limbs) * ((size_t)batch << logN) * 4;
+    const size_t limbs = scratch_limbs(ctx, op, n_limbs);
+    if (limbs == 0) return 0;
+    // the operation's limbs, then the two-pass NTT region of its NTT calls
+    return limbs * ((size_t)batch << logN) * 4 + ntt_region_bytes(logN, ntt_rows(ctx, op, n_limbs) * batch);
 }
 
 int fhe_keyswitch(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const uint32_t* d2,
@@ -736,7 +759,7 @@ int fhe_keyswitch(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, con
     if (scratch_bytes < fhe_scratch_bytes(ctx, FHE_OP_KEYSWITCH, logN, n_limbs, batch))
         return set_error(FHE_ENOMEM, "scratch too small");
     return keyswitch_impl(ctx, logN, n_limbs, batch, d2, evk, ks_out, 0, (uint32_t*)scratch, false,
-                          (cudaStream_t)stream);
+                          (cudaStream_t)stream, op_ntt_scratch(ctx, FHE_OP_KEYSWITCH, logN, n_limbs, batch, scratch));
 }
 
 int fhe_hmult_relin(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const uint32_t* ct_a,
@@ -748,7 +771,8 @@ int fhe_hmult_relin(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, c
     if (scratch_bytes < fhe_scratch_bytes(ctx, FHE_OP_HMULT_RELIN, logN, n_limbs, batch))
         return set_error(FHE_ENOMEM, "scratch too small");
     return hmult_relin_impl(ctx, logN, n_limbs, batch, ct_a, ct_b, evk, out, (uint32_t*)scratch,
-                            (cudaStream_t)stream);
+                            (cudaStream_t)stream,
+                            op_ntt_scratch(ctx, FHE_OP_HMULT_RELIN, logN, n_limbs, batch, scratch));
 }
 
 int fhe_rescale(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const uint32_t* ct_in,
@@ -769,7 +793,8 @@ int fhe_hmult(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const u
     if ((rc = check_ptrs({ct_a, ct_b, evk, ct_out, scratch}))) return rc;
     if (scratch_bytes < fhe_scratch_bytes(ctx, FHE_OP_HMULT, logN, n_limbs, batch))
         return set_error(FHE_ENOMEM, "scratch too small");
-    return hmult_fused(ctx, logN, n_limbs, batch, ct_a, ct_b, evk, ct_out, (uint32_t*)scratch, (cudaStream_t)stream);
+    return hmult_fused(ctx, logN, n_limbs, batch, ct_a, ct_b, evk, ct_out, (uint32_t*)scratch, (cudaStream_t)stream,
+                       op_ntt_scratch(ctx, FHE_OP_HMULT, logN, n_limbs, batch, scratch));
 }
 
 int fhe_automorph(const fhe_ctx* ctx, uint32_t logN, long long rows, uint32_t galois, const uint32_t* in,
@@ -795,7 +820,7 @@ int fhe_hrotate(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, uint3
     if (scratch_bytes < fhe_scratch_bytes(ctx, FHE_OP_HROTATE, logN, n_limbs, batch))
         return set_error(FHE_ENOMEM, "scratch too small");
     return hrotate_impl(ctx, logN, n_limbs, batch, galois, ct_in, ksk, ct_out, (uint32_t*)scratch,
-                        (cudaStream_t)stream);
+                        (cudaStream_t)stream, op_ntt_scratch(ctx, FHE_OP_HROTATE, logN, n_limbs, batch, scratch));
 }
 
 int fhe_cmult(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const uint32_t* ct, const uint32_t* pt,

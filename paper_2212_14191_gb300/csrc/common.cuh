@@ -137,18 +137,29 @@ struct RowRef {
     uint32_t pad;
 };
 
+// Device scratch of the two-pass plain NTT for one call: `bytes` (a multiple of N * 4 is
+// used) at `p`. p == nullptr selects the context's own scratch, which calls on different
+// streams must not use at the same time; library operations that take a caller scratch pass
+// a region of it instead (ntt_region_bytes).
+struct NttScratch {
+    uint32_t* p = nullptr;
+    size_t bytes = 0;
+};
+// Bytes of that region for NTT calls of up to `rows` rows at 2^logN (0 below 2^15).
+size_t ntt_region_bytes(uint32_t logN, size_t rows);
+
 // Plain-path NTT over rows listed in a device table (operation-level batching of rows
 // that live in different buffers).
 int ntt_u32_rows(const fhe_ctx* ctx, uint32_t logN, bool inverse, const RowRef* d_rows, int nrows,
-                 cudaStream_t stream);
+                 cudaStream_t stream, NttScratch scr = NttScratch());
 
-// Plain-path NTT for N >= 2^15 in two passes through an L2-resident scratch (ntt_u32_l2.cu).
+// Plain-path NTT for N >= 2^15 in two passes through a scratch buffer (ntt_u32_l2.cu).
 int ntt_u32_l2(const fhe_ctx* ctx, uint32_t logN, int shape, bool inverse, uint32_t* d, int rows, int batch,
-               const LimbMap& map, const RowRef* rowtab, cudaStream_t st);
+               const LimbMap& map, const RowRef* rowtab, cudaStream_t st, NttScratch scr);
 
 // Plain-path batched NTT over `n_limbs` limbs whose moduli are map.mod[l].
 int ntt_u32(const fhe_ctx* ctx, uint32_t logN, bool inverse, uint32_t* d, int n_limbs,
-            int batch, const LimbMap& map, cudaStream_t stream);
+            int batch, const LimbMap& map, cudaStream_t stream, NttScratch scr = NttScratch());
 // Tensor-core path.
 int ntt_tc(const fhe_ctx* ctx, uint32_t logN, bool inverse, uint32_t* d, int n_limbs,
            int batch, const LimbMap& map, cudaStream_t stream);
@@ -157,7 +168,7 @@ int build_ntt_tables(fhe_ctx* ctx, uint32_t logN);
 
 // Dispatch on path.
 int ntt_any(const fhe_ctx* ctx, int path, uint32_t logN, bool inverse, uint32_t* d, int n_limbs,
-            int batch, const LimbMap& map, cudaStream_t stream);
+            int batch, const LimbMap& map, cudaStream_t stream, NttScratch scr = NttScratch());
 
 LimbMap contiguous_map(const fhe_ctx* ctx, int first, int n);
 

@@ -80,10 +80,16 @@ LimbMap contiguous_map(const fhe_ctx* ctx, int first, int n) {
 }
 
 int ntt_any(const fhe_ctx* ctx, int path, uint32_t logN, bool inverse, uint32_t* d, int n_limbs,
-            int batch, const LimbMap& map, cudaStream_t stream) {
+            int batch, const LimbMap& map, cudaStream_t stream, NttScratch scr) {
     if (path == FHE_NTT_DEFAULT) path = ctx->default_path;
     if (path == FHE_NTT_TC) return ntt_tc(ctx, logN, inverse, d, n_limbs, batch, map, stream);
-    return ntt_u32(ctx, logN, inverse, d, n_limbs, batch, map, stream);
+    return ntt_u32(ctx, logN, inverse, d, n_limbs, batch, map, stream, scr);
+}
+
+size_t ntt_region_bytes(uint32_t logN, size_t rows) {
+    if (logN < 15 || rows == 0) return 0;
+    const size_t b = (rows << logN) * 4;
+    return b < kNttTempBytes ? b : kNttTempBytes;
 }
 
 static int build_conv(fhe_ctx* ctx, const std::vector<int>& src, ConvTable* out) {

@@ -133,24 +133,24 @@ int build_ntt_tables(fhe_ctx* ctx, uint32_t logN) {
 
 namespace {
 int ntt_u32_dispatch(const fhe_ctx* ctx, uint32_t logN, bool inverse, uint32_t* d, long long rows, int batch,
-                     const LimbMap& map, const RowRef* rowtab, cudaStream_t stream);
+                     const LimbMap& map, const RowRef* rowtab, cudaStream_t stream, NttScratch scr);
 }
 
 int ntt_u32(const fhe_ctx* ctx, uint32_t logN, bool inverse, uint32_t* d, int n_limbs, int batch,
-            const LimbMap& map, cudaStream_t stream) {
-    return ntt_u32_dispatch(ctx, logN, inverse, d, (long long)n_limbs * batch, batch, map, nullptr, stream);
+            const LimbMap& map, cudaStream_t stream, NttScratch scr) {
+    return ntt_u32_dispatch(ctx, logN, inverse, d, (long long)n_limbs * batch, batch, map, nullptr, stream, scr);
 }
 
 int ntt_u32_rows(const fhe_ctx* ctx, uint32_t logN, bool inverse, const RowRef* d_rows, int nrows,
-                 cudaStream_t stream) {
+                 cudaStream_t stream, NttScratch scr) {
     LimbMap unused;
     memset(&unused, 0, sizeof(unused));
-    return ntt_u32_dispatch(ctx, logN, inverse, nullptr, nrows, 1, unused, d_rows, stream);
+    return ntt_u32_dispatch(ctx, logN, inverse, nullptr, nrows, 1, unused, d_rows, stream, scr);
 }
 
 namespace {
 int ntt_u32_dispatch(const fhe_ctx* ctx, uint32_t logN, bool inverse, uint32_t* d, long long rows_ll, int batch,
-                     const LimbMap& map, const RowRef* rowtab, cudaStream_t stream) {
+                     const LimbMap& map, const RowRef* rowtab, cudaStream_t stream, NttScratch scr) {
     const NttTables& t = ctx->ntt[logN];
     if (!t.fwd) return set_error(FHE_EINVAL, "no NTT tables for this logN");
     if (rows_ll == 0) return FHE_OK;
@@ -159,7 +159,8 @@ int ntt_u32_dispatch(const fhe_ctx* ctx, uint32_t logN, bool inverse, uint32_t* 
     const int v = ctx->ntt_variant[inverse ? 1 : 0][logN];
     int log_t, log_c;
     if (!ntt_variant_shape(logN, v, &log_t, &log_c)) return set_error(FHE_EINVAL, "logN out of range");
-    if (log_c >= 2) return ntt_u32_launch_wide(ctx, t, logN, log_t, log_c, v, inverse, d, rows, batch, map, rowtab, stream);
+    if (log_c >= 2)
+        return ntt_u32_launch_wide(ctx, t, logN, log_t, log_c, v, inverse, d, rows, batch, map, rowtab, stream, scr);
     FHE_NTT_CASE(5, 0)
     FHE_NTT_CASE(6, 0)
     FHE_NTT_CASE(7, 0)

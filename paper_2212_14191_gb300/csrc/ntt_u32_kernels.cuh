@@ -768,7 +768,7 @@ int launch(const fhe_ctx* ctx, const NttTables& t, int variant, bool inverse, ui
         const int ex = LC > 0 ? ntt_variant_exchange(v) : 0;                                          \
         const bool tws = ntt_variant_tws(v), occ = ntt_variant_occ2(v);                               \
         if constexpr (LC > 0) {                                                                       \
-            if (ex == 3) return ntt_u32_l2(ctx, logN, v & 1, inverse, d, rows, batch, map, rowtab, stream); \
+            if (ex == 3) return ntt_u32_l2(ctx, logN, v & 1, inverse, d, rows, batch, map, rowtab, stream, scr); \
             if (ex == 1) return launch<LT, LC, 1, false, 1>(ctx, t, v, inverse, d, rows, batch, map, rowtab, stream); \
             if (ex == 2)                                                                              \
                 return tws ? launch<LT, LC, 2, true, 1>(ctx, t, v, inverse, d, rows, batch, map, rowtab, stream) \
@@ -785,6 +785,6 @@ int launch(const fhe_ctx* ctx, const NttTables& t, int variant, bool inverse, ui
 // Launches for the shapes with clusters of 4 or more CTAs (ntt_u32_wide.cu).
 int ntt_u32_launch_wide(const fhe_ctx* ctx, const NttTables& t, uint32_t logN, int log_t, int log_c, int v,
                         bool inverse, uint32_t* d, int rows, int batch, const LimbMap& map, const RowRef* rowtab,
-                        cudaStream_t stream);
+                        cudaStream_t stream, NttScratch scr);
 
 }  // namespace fhe

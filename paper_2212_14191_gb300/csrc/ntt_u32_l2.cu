@@ -16,6 +16,8 @@
 // independent, all SMs are usable and no cluster barrier is needed, which on GB300 outweighs
 // it. The strided side of both forms is a read (the C CTAs of a row share every sector
 // through L2): stores stay contiguous.
+#include <algorithm>
+
 #include "common.cuh"
 #include "ptx.cuh"
 
@@ -338,7 +340,7 @@ __global__ void __launch_bounds__(256) ntt_dit_cross_kernel(const L2Args a) {
 
 template <int LOG_T, int LOG_C>
 int run_l2(const fhe_ctx* ctx, const NttTables& t, int shape, bool inverse, uint32_t* d, int rows, int batch,
-           const LimbMap& map, const RowRef* rowtab, cudaStream_t st) {
+           const LimbMap& map, const RowRef* rowtab, cudaStream_t st, uint32_t* temp, size_t temp_bytes) {
     constexpr int T = 1 << LOG_T, C = 1 << LOG_C, NC = 32 * T, N = NC * C;
     constexpr int smem = PadLayout<LOG_T>::kWords * 4;
     // forward: decimation in time (local NC-point transforms, then twist + C-point DFT);
@@ -355,7 +357,7 @@ int run_l2(const fhe_ctx* ctx, const NttTables& t, int shape, bool inverse, uint
     a.batch = batch;
     a.rowtab = rowtab;
     a.mod_q = ctx->d_mods;
-    a.temp = ctx->ntt_temp;
+    a.temp = temp;
     a.tw = inverse ? t.inv : t.fwd;
     a.twC = inverse ? t.invC[shape] : t.fwdC[shape];
     a.ninv = t.ninv;
@@ -364,7 +366,9 @@ int run_l2(const fhe_ctx* ctx, const NttTables& t, int shape, bool inverse, uint
     a.twist = t.dit_twist[shape];
     a.omega = t.dit_omega[shape];
     a.map = map;
-    const int chunk = (int)(kNttTempBytes / ((size_t)N * 4));
+    const size_t chunk_rows = temp_bytes / ((size_t)N * 4);
+    if (chunk_rows < 1) return set_error(FHE_EINVAL, "two-pass NTT scratch smaller than one row");
+    const int chunk = (int)std::min<size_t>(chunk_rows, (size_t)1 << 30);
     const int gx = (NC / 4 + 255) / 256;
     for (int r0 = 0; r0 < rows; r0 += chunk) {
         a.r0 = r0;
@@ -383,16 +387,22 @@ int run_l2(const fhe_ctx* ctx, const NttTables& t, int shape, bool inverse, uint
 }  // namespace
 
 int ntt_u32_l2(const fhe_ctx* ctx, uint32_t logN, int shape, bool inverse, uint32_t* d, int rows, int batch,
-               const LimbMap& map, const RowRef* rowtab, cudaStream_t st) {
+               const LimbMap& map, const RowRef* rowtab, cudaStream_t st, NttScratch scr) {
     const NttTables& t = ctx->ntt[logN];
-    if (!ctx->ntt_temp) return set_error(FHE_EINVAL, "no two-pass scratch in this context");
+    uint32_t* temp = scr.p ? scr.p : ctx->ntt_temp;
+    const size_t temp_bytes = scr.p ? scr.bytes : kNttTempBytes;
+    if (!temp) return set_error(FHE_EINVAL, "no two-pass scratch in this context");
     int log_t, log_c;
     if (!ntt_variant_shape(logN, shape, &log_t, &log_c) || log_c == 0)
         return set_error(FHE_EINVAL, "two-pass NTT needs N >= 2^15");
-    if (log_t == 9 && log_c == 2) return run_l2<9, 2>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st);
-    if (log_t == 9 && log_c == 1) return run_l2<9, 1>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st);
-    if (log_t == 8 && log_c == 3) return run_l2<8, 3>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st);
-    if (log_t == 8 && log_c == 2) return run_l2<8, 2>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st);
+    if (log_t == 9 && log_c == 2)
+        return run_l2<9, 2>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes);
+    if (log_t == 9 && log_c == 1)
+        return run_l2<9, 1>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes);
+    if (log_t == 8 && log_c == 3)
+        return run_l2<8, 3>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes);
+    if (log_t == 8 && log_c == 2)
+        return run_l2<8, 2>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes);
     return set_error(FHE_EINVAL, "no two-pass kernel for this shape");
 }
 

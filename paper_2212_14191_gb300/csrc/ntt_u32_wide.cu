@@ -6,7 +6,7 @@ namespace fhe {
 
 int ntt_u32_launch_wide(const fhe_ctx* ctx, const NttTables& t, uint32_t logN, int log_t, int log_c, int v,
                         bool inverse, uint32_t* d, int rows, int batch, const LimbMap& map, const RowRef* rowtab,
-                        cudaStream_t stream) {
+                        cudaStream_t stream, NttScratch scr) {
     FHE_NTT_CASE(9, 2)
     FHE_NTT_CASE(8, 2)
     FHE_NTT_CASE(8, 3)

@@ -194,3 +194,40 @@ def test_hmult_heax_sets_bitexact(fhe, logn, L, K):
     assert np.abs(zz - za * zb).max() < 1e-3
     fhe.fhe_device_status(ctx.handle, 1)
     ctx.close()
+
+
+def test_concurrent_streams_share_a_context(fhe):
+    """HMULTs of one context on eight streams at once, with the two-pass NTT variants (whose
+    chunk buffer each call takes from its own scratch): every result equals the result of the
+    same inputs run alone."""
+    import torch
+    logn, nl, K, batch = 15, 6, 2, 4
+    n = 1 << logn
+    qs, ps = P.default_moduli(nl, K)
+    prm = C.Params(n, qs, ps, alpha=2)
+    s, evk = make_key(prm, 400)
+    ctx = fhe.Context(logn, qs, ps, alpha=2)
+    fhe.fhe_ntt_set_variant(ctx.handle, logn, 7, 7)            # two-pass both ways
+    dev_evk = fhe.to_device(evk.astype(np.uint32))
+    ins = [(fhe.to_device(batch_cts(prm, nl, batch, 410 + 2 * k)), fhe.to_device(batch_cts(prm, nl, batch, 411 + 2 * k)))
+           for k in range(8)]
+    alone = []
+    for a, b in ins:                                          # one at a time, default stream
+        alone.append(ctx.hmult(a, b, dev_evk, logn).clone())
+    torch.cuda.synchronize()
+    nbytes = fhe.fhe_scratch_bytes(ctx.handle, fhe.FHE_OP_HMULT, logn, nl, batch)
+    streams = [torch.cuda.Stream() for _ in ins]
+    scratch = [torch.empty(nbytes // 4 + 4, dtype=torch.int32, device="cuda") for _ in ins]
+    outs = [torch.empty_like(x) for x in alone]
+    for rep in range(3):
+        for k, (a, b) in enumerate(ins):
+            fhe.fhe_hmult(ctx.handle, logn, nl, batch, a.data_ptr(), b.data_ptr(), dev_evk.data_ptr(),
+                          outs[k].data_ptr(), scratch[k].data_ptr(), nbytes, streams[k].cuda_stream)
+        torch.cuda.synchronize()
+        for k in range(len(ins)):
+            assert torch.equal(outs[k], alone[k]), (rep, k)
+    got = fhe.to_host(alone[0])
+    a0, b0 = fhe.to_host(ins[0][0]), fhe.to_host(ins[0][1])
+    assert (got[:, :, 0] == C.hmult(prm, nl, a0[:, :, 0].astype(U64), b0[:, :, 0].astype(U64), evk)).all()
+    fhe.fhe_device_status(ctx.handle, 1)
+    ctx.close()
