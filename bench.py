@@ -291,14 +291,14 @@ def ours(args):
         results["u32"]["variant"] = {"fwd": vf, "inv": vi}
     fhe.fhe_device_status(ctx.handle, 1)
     head = max(results, key=lambda k: results[k]["kops"])
-    # kernels per step: u32 = one launch per direction, or two per 64 MiB chunk of rows for
-    # the two-pass variants; tensor cores = 3 per chunk of limbs and direction (split, GEMM 1,
+    # kernels per step: u32 = one launch per direction (per 1 GiB chunk of rows for the
+    # two-pass variants); tensor cores = 3 per chunk of limbs and direction (split, GEMM 1,
     # GEMM 2)
     chunk_limbs = max(1, min(64, (256 << 20) // (N * 8) // NTT_BATCH))
 
     def u32_launches(v):
         rows = NTT_LIMBS * NTT_BATCH
-        return 2 * (-(-rows // ((1 << 30) // (N * 4)))) if ((v >> 1) & 3) == 3 else 1   # 1 GiB chunks
+        return (-(-rows // ((1 << 30) // (N * 4 + 4)))) if ((v >> 1) & 3) == 3 else 1   # 1 GiB chunks
 
     launches_per_step = {"u32": u32_launches(vf) + u32_launches(vi), "tc": 2 * 3 * (-(-NTT_LIMBS // chunk_limbs))}
     total_head = ops_per_step * args.steps * ws / (results[head]["kops"] * 1e3)

@@ -88,7 +88,7 @@ int ntt_any(const fhe_ctx* ctx, int path, uint32_t logN, bool inverse, uint32_t*
 
 size_t ntt_region_bytes(uint32_t logN, size_t rows) {
     if (logN < 15 || rows == 0) return 0;
-    const size_t b = (rows << logN) * 4;
+    const size_t b = rows * (((size_t)4 << logN) + 4);  // residues and a completion counter per row
     return b < kNttTempBytes ? b : kNttTempBytes;
 }
 
@@ -243,7 +243,7 @@ int fhe_ctx_create(uint32_t logN_max, const uint32_t* q, int nq, const uint32_t*
     // limbs x (2^22 / N) polynomials; fhe_autotune_ntt re-measures them for the caller's batch
     static const int kDefaultVariant[3][2] = {
         {16, 8},  // 2^14: single CTA at 64 registers / single CTA with staged twiddles
-        {20, 7},  // 2^15: 2-CTA split forward at 64 registers / two-pass inverse, 256 threads
+        {7, 7},   // 2^15: two-pass, 256 threads, both directions
         {7, 7},   // 2^16: two-pass (decimation-in-time forward), 256 threads, both directions
     };
     for (int l = 14; l <= 16; ++l) {

@@ -1,21 +1,21 @@
 // Plain 32-bit NTT for N >= 2^15 in two passes through L2 (no thread-block clusters).
 //
 // A row of N = C * NC residues (NC = 2^14, or 2^13 for the 256-thread shape) is transformed
-// as C sub-transforms of NC points plus a C-point combination:
+// as C sub-transforms of NC points plus a C-point combination, in one launch per chunk of rows:
 //   forward (decimation in time): local pass -- every CTA runs the single-CTA NC-point
 //            transform (root psi^C, the library's root for that ring degree) on the
 //            decimated sequence a[j + C m] and writes it in natural order to a scratch buffer;
-//            cross pass -- a streaming kernel twists B_j[k'] by psi^((2k'+1) j), runs a
-//            C-point cyclic DFT and writes A[k' + NC t] back into the row;
+//            cross pass -- twist B_j[k'] by psi^((2k'+1) j), C-point cyclic DFT, write
+//            A[k' + NC t] back into the row;
 //   inverse (decimation in frequency): quarter pass -- every CTA gathers the outputs
 //            k = k_local * C + rev(c) of its quarter, runs the Gentleman-Sande stages of the
 //            quarter and writes the scratch; cross pass -- the last log2(C) stages couple the
 //            quarters and apply N^-1, writing the row.
-// Rows go through in chunks of up to 1 GiB of scratch (two launches per chunk); the scratch
-// round trip costs HBM traffic (it does not stay in L2 at these sizes), but every CTA is
-// independent, all SMs are usable and no cluster barrier is needed, which on GB300 outweighs
-// it. The strided side of both forms is a read (the C CTAs of a row share every sector
-// through L2): stores stay contiguous.
+// The cross pass of a row is run by whichever of its C CTAs finishes the local pass last
+// (an atomic count per row, no waiting), so it reads the row's scratch from L2 and no second
+// launch is needed. Every CTA is independent, all SMs are usable and no cluster barrier is
+// involved. The strided side of both forms is a read (the C CTAs of a row share every sector
+// through L2): stores stay contiguous. Rows go through in chunks of up to 1 GiB of scratch.
 #include <algorithm>
 
 #include "common.cuh"
@@ -39,8 +39,23 @@ struct L2Args {
     const uint2* twC_sub;    // [nmod][1][31][T]
     const uint2* twist;      // [nmod][C-1][NC]
     const uint2* omega;      // [nmod][C/2]
+    int* cnt;                // per chunk row: local-pass CTAs finished (zeroed before each chunk)
     LimbMap map;
 };
+
+// The C local-pass CTAs of a row each count themselves in cnt[i] once their scratch stores
+// are visible (fence, then atomic); the one that completes the count runs the row's cross
+// pass while the row's scratch is still in L2. Nothing waits: a CTA that is not last exits.
+__device__ __forceinline__ bool last_of_row(const L2Args& a, int i, int C) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&a.cnt[i], 1) == C - 1;
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    return true;
+}
 
 template <int N>
 __device__ __forceinline__ uint32_t* l2_row(const L2Args& a, int row, uint32_t* q, int* mod) {
@@ -76,16 +91,15 @@ __device__ __forceinline__ void gs2(uint32_t& x, uint32_t& y, uint2 w, uint32_t 
 // ---- inverse cross pass: grid (blocks over NC/4 quad positions, chunk rows); 4 positions per
 // thread; the last log2(C) Gentleman-Sande stages and the N^-1 scaling
 template <int LOG_NC, int LOG_C>
-__global__ void __launch_bounds__(256) ntt_cross_inv_kernel(const L2Args a) {
+__device__ __forceinline__ void cross_inv_row(const L2Args& a, int i, int p0, int pstep) {
     constexpr int NC = 1 << LOG_NC, C = 1 << LOG_C, N = NC * C;
-    const int i = blockIdx.y;
     uint32_t q;
     int mod;
     uint32_t* row = l2_row<N>(a, a.r0 + i, &q, &mod);
     const uint32_t* tmp = a.temp + (size_t)i * N;
     const uint2* tw = a.tw + (size_t)mod * N;
     const uint2 ni = __ldg(&a.ninv[mod]);
-    for (int p4 = blockIdx.x * blockDim.x + threadIdx.x; p4 < NC / 4; p4 += gridDim.x * blockDim.x) {
+    for (int p4 = p0; p4 < NC / 4; p4 += pstep) {
         uint4 x[C];
 #pragma unroll
         for (int qq = 0; qq < C; ++qq) x[qq] = __ldcg(reinterpret_cast<const uint4*>(tmp + qq * NC) + p4);
@@ -187,6 +201,7 @@ __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_quarter_inv_kern
     }
 #pragma unroll
     for (int e = 0; e < 32; ++e) __stcg(&tmp[tid + T * e], v[e]);
+    if (last_of_row(a, i, C)) cross_inv_row<LOG_T + 5, LOG_C>(a, i, tid, T);
 }
 
 // ---- decimation-in-time forward (the two-pass forward): with n = C m + j and
@@ -198,6 +213,76 @@ __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_quarter_inv_kern
 // contiguous streams and writing C contiguous streams. Pass 1 reads at stride C (the C CTAs
 // of a row share every sector through L2), where the decimation-in-frequency order would
 // store at stride C.
+template <int LOG_NC, int LOG_C>
+__device__ __forceinline__ void dit_cross_row(const L2Args& a, int i, int p0, int pstep) {
+    constexpr int NC = 1 << LOG_NC, C = 1 << LOG_C, N = NC * C;
+    uint32_t q;
+    int mod;
+    uint32_t* row = l2_row<N>(a, a.r0 + i, &q, &mod);
+    const uint32_t* tmp = a.temp + (size_t)i * N;
+    const uint2* twist = a.twist + (size_t)mod * (C - 1) * NC;
+    const uint2* om = a.omega + (size_t)mod * (C / 2);
+    uint2 omv[C / 2];
+#pragma unroll
+    for (int m = 0; m < C / 2; ++m) omv[m] = __ldg(&om[m]);
+    for (int p4 = p0; p4 < NC / 4; p4 += pstep) {
+        uint4 x[C];
+#pragma unroll
+        for (int jj = 0; jj < C; ++jj) x[jj] = __ldcg(reinterpret_cast<const uint4*>(tmp + jj * NC) + p4);
+        uint4 tw2[C > 1 ? 2 * (C - 1) : 1];  // four twist pairs of every j >= 1: two uint4 each
+#pragma unroll
+        for (int jj = 1; jj < C; ++jj) {
+            const uint4* tp = reinterpret_cast<const uint4*>(twist + (size_t)(jj - 1) * NC + 4 * p4);
+            tw2[2 * (jj - 1)] = __ldg(tp);
+            tw2[2 * (jj - 1) + 1] = __ldg(tp + 1);
+        }
+        uint4 o[C];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t y[C];
+#pragma unroll
+            for (int jj = 0; jj < C; ++jj) y[jj] = k == 0 ? x[jj].x : k == 1 ? x[jj].y : k == 2 ? x[jj].z : x[jj].w;
+#pragma unroll
+            for (int jj = 1; jj < C; ++jj) {
+                const uint4 t4 = tw2[2 * (jj - 1) + (k >> 1)];
+                const uint2 w = (k & 1) ? make_uint2(t4.z, t4.w) : make_uint2(t4.x, t4.y);
+                y[jj] = mul_shoup(y[jj], w.x, w.y, q);  // [0, q)
+            }
+            // C-point cyclic DFT, radix-2 decimation in frequency: position p ends up holding
+            // output t = rev(p); values stay in [0, 2q)
+#pragma unroll
+            for (int s = 0; s < LOG_C; ++s) {
+                const int h = C >> (s + 1);
+#pragma unroll
+                for (int b = 0; b < C; b += 2 * h)
+#pragma unroll
+                    for (int jj = 0; jj < h; ++jj) {
+                        const int m = jj << s;  // omega^m
+                        if (m == 0) {
+                            const uint32_t su = csub(y[b + jj] + y[b + jj + h], 2 * q);
+                            const uint32_t di = csub(y[b + jj] - y[b + jj + h] + 2 * q, 2 * q);
+                            y[b + jj] = su;
+                            y[b + jj + h] = di;
+                        } else {
+                            gs2(y[b + jj], y[b + jj + h], omv[m], q);
+                        }
+                    }
+            }
+#pragma unroll
+            for (int p = 0; p < C; ++p) {
+                const int t = rbits<LOG_C>(p);
+                const uint32_t val = csub(y[p], q);
+                if (k == 0) o[t].x = val;
+                else if (k == 1) o[t].y = val;
+                else if (k == 2) o[t].z = val;
+                else o[t].w = val;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < C; ++t) reinterpret_cast<uint4*>(row + t * NC)[p4] = o[t];
+    }
+}
+
 template <int LOG_T, int LOG_C>
 __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_dit_local_kernel(const L2Args a) {
     constexpr int T = 1 << LOG_T, C = 1 << LOG_C, NC = 32 * T, N = NC * C, RB = LOG_T - 5;
@@ -265,78 +350,9 @@ __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_dit_local_kernel
     // natural order: thread tid holds k' = rev5(e) T + tid
 #pragma unroll
     for (int e = 0; e < 32; ++e) __stcg(&tmp[rbits<5>(e) * T + tid], csub(csub(v[e], 2 * q), q));
+    if (last_of_row(a, i, C)) dit_cross_row<LOG_T + 5, LOG_C>(a, i, tid, T);
 }
 
-template <int LOG_NC, int LOG_C>
-__global__ void __launch_bounds__(256) ntt_dit_cross_kernel(const L2Args a) {
-    constexpr int NC = 1 << LOG_NC, C = 1 << LOG_C, N = NC * C;
-    const int i = blockIdx.y;
-    uint32_t q;
-    int mod;
-    uint32_t* row = l2_row<N>(a, a.r0 + i, &q, &mod);
-    const uint32_t* tmp = a.temp + (size_t)i * N;
-    const uint2* twist = a.twist + (size_t)mod * (C - 1) * NC;
-    const uint2* om = a.omega + (size_t)mod * (C / 2);
-    uint2 omv[C / 2];
-#pragma unroll
-    for (int m = 0; m < C / 2; ++m) omv[m] = __ldg(&om[m]);
-    for (int p4 = blockIdx.x * blockDim.x + threadIdx.x; p4 < NC / 4; p4 += gridDim.x * blockDim.x) {
-        uint4 x[C];
-#pragma unroll
-        for (int jj = 0; jj < C; ++jj) x[jj] = __ldcg(reinterpret_cast<const uint4*>(tmp + jj * NC) + p4);
-        uint4 tw2[C > 1 ? 2 * (C - 1) : 1];  // four twist pairs of every j >= 1: two uint4 each
-#pragma unroll
-        for (int jj = 1; jj < C; ++jj) {
-            const uint4* tp = reinterpret_cast<const uint4*>(twist + (size_t)(jj - 1) * NC + 4 * p4);
-            tw2[2 * (jj - 1)] = __ldg(tp);
-            tw2[2 * (jj - 1) + 1] = __ldg(tp + 1);
-        }
-        uint4 o[C];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            uint32_t y[C];
-#pragma unroll
-            for (int jj = 0; jj < C; ++jj) y[jj] = k == 0 ? x[jj].x : k == 1 ? x[jj].y : k == 2 ? x[jj].z : x[jj].w;
-#pragma unroll
-            for (int jj = 1; jj < C; ++jj) {
-                const uint4 t4 = tw2[2 * (jj - 1) + (k >> 1)];
-                const uint2 w = (k & 1) ? make_uint2(t4.z, t4.w) : make_uint2(t4.x, t4.y);
-                y[jj] = mul_shoup(y[jj], w.x, w.y, q);  // [0, q)
-            }
-            // C-point cyclic DFT, radix-2 decimation in frequency: position p ends up holding
-            // output t = rev(p); values stay in [0, 2q)
-#pragma unroll
-            for (int s = 0; s < LOG_C; ++s) {
-                const int h = C >> (s + 1);
-#pragma unroll
-                for (int b = 0; b < C; b += 2 * h)
-#pragma unroll
-                    for (int jj = 0; jj < h; ++jj) {
-                        const int m = jj << s;  // omega^m
-                        if (m == 0) {
-                            const uint32_t su = csub(y[b + jj] + y[b + jj + h], 2 * q);
-                            const uint32_t di = csub(y[b + jj] - y[b + jj + h] + 2 * q, 2 * q);
-                            y[b + jj] = su;
-                            y[b + jj + h] = di;
-                        } else {
-                            gs2(y[b + jj], y[b + jj + h], omv[m], q);
-                        }
-                    }
-            }
-#pragma unroll
-            for (int p = 0; p < C; ++p) {
-                const int t = rbits<LOG_C>(p);
-                const uint32_t val = csub(y[p], q);
-                if (k == 0) o[t].x = val;
-                else if (k == 1) o[t].y = val;
-                else if (k == 2) o[t].z = val;
-                else o[t].w = val;
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < C; ++t) reinterpret_cast<uint4*>(row + t * NC)[p4] = o[t];
-    }
-}
 
 template <int LOG_T, int LOG_C>
 int run_l2(const fhe_ctx* ctx, const NttTables& t, int shape, bool inverse, uint32_t* d, int rows, int batch,
@@ -366,19 +382,16 @@ int run_l2(const fhe_ctx* ctx, const NttTables& t, int shape, bool inverse, uint
     a.twist = t.dit_twist[shape];
     a.omega = t.dit_omega[shape];
     a.map = map;
-    const size_t chunk_rows = temp_bytes / ((size_t)N * 4);
+    // chunk rows: N residues of scratch and one completion counter each
+    const size_t chunk_rows = temp_bytes / ((size_t)N * 4 + 4);
     if (chunk_rows < 1) return set_error(FHE_EINVAL, "two-pass NTT scratch smaller than one row");
     const int chunk = (int)std::min<size_t>(chunk_rows, (size_t)1 << 30);
-    const int gx = (NC / 4 + 255) / 256;
+    a.cnt = reinterpret_cast<int*>(temp + (size_t)chunk * N);
     for (int r0 = 0; r0 < rows; r0 += chunk) {
         a.r0 = r0;
         a.nrows = rows - r0 < chunk ? rows - r0 : chunk;
+        FHE_CUDA_TRY(cudaMemsetAsync(a.cnt, 0, (size_t)a.nrows * sizeof(int), st));
         qk<<<dim3(C, a.nrows), T, smem, st>>>(a);
-        FHE_CUDA_TRY(cudaGetLastError());
-        if (inverse)
-            ntt_cross_inv_kernel<LOG_T + 5, LOG_C><<<dim3(gx, a.nrows), 256, 0, st>>>(a);
-        else
-            ntt_dit_cross_kernel<LOG_T + 5, LOG_C><<<dim3(gx, a.nrows), 256, 0, st>>>(a);
         FHE_CUDA_TRY(cudaGetLastError());
     }
     return FHE_OK;
