@@ -244,7 +244,7 @@ int fhe_ctx_create(uint32_t logN_max, const uint32_t* q, int nq, const uint32_t*
     static const int kDefaultVariant[3][2] = {
         {16, 8},  // 2^14: single CTA at 64 registers / single CTA with staged twiddles
         {7, 7},   // 2^15: two-pass, 256 threads, both directions
-        {7, 7},   // 2^16: two-pass (decimation-in-time forward), 256 threads, both directions
+        {6, 6},   // 2^16: two-pass (decimation-in-time forward), 512 threads, both directions
     };
     for (int l = 14; l <= 16; ++l) {
         ctx->ntt_variant[0][l] = kDefaultVariant[l - 14][0];

@@ -40,6 +40,7 @@ struct L2Args {
     const uint2* twist;      // [nmod][C-1][NC]
     const uint2* omega;      // [nmod][C/2]
     int* cnt;                // per chunk row: local-pass CTAs finished (zeroed before each chunk)
+    int fuse;                // 1: the last local-pass CTA of a row runs its cross pass
     LimbMap map;
 };
 
@@ -129,8 +130,17 @@ __device__ __forceinline__ void cross_inv_row(const L2Args& a, int i, int p0, in
     }
 }
 
+// Stand-alone cross passes, one launch after the local passes: used for chunks too small to
+// fill the GPU, where the fused form would leave one CTA per row doing all of its cross work.
+template <int LOG_NC, int LOG_C>
+__global__ void __launch_bounds__(256) ntt_cross_inv_kernel(const L2Args a) {
+    cross_inv_row<LOG_NC, LOG_C>(a, blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+// Blocks per SM the register budget is sized for: 64 registers per thread, so twice the
+// CTAs of the single-CTA kernels share an SM (measured 10 % faster at 2^15 and 2^16).
 template <int LOG_T>
-constexpr int kMinB = (1 << (14 - LOG_T)) / 32 > 0 ? (1 << (14 - LOG_T)) / 32 : 1;
+constexpr int kMinB = 2 * ((1 << (14 - LOG_T)) / 32 > 0 ? (1 << (14 - LOG_T)) / 32 : 1);
 
 // ---- quarter pass, inverse: row (stride C, quarter c's bit-reversed share) -> GS stages -> scratch
 template <int LOG_T, int LOG_C>
@@ -201,7 +211,7 @@ __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_quarter_inv_kern
     }
 #pragma unroll
     for (int e = 0; e < 32; ++e) __stcg(&tmp[tid + T * e], v[e]);
-    if (last_of_row(a, i, C)) cross_inv_row<LOG_T + 5, LOG_C>(a, i, tid, T);
+    if (a.fuse && last_of_row(a, i, C)) cross_inv_row<LOG_T + 5, LOG_C>(a, i, tid, T);
 }
 
 // ---- decimation-in-time forward (the two-pass forward): with n = C m + j and
@@ -283,6 +293,11 @@ __device__ __forceinline__ void dit_cross_row(const L2Args& a, int i, int p0, in
     }
 }
 
+template <int LOG_NC, int LOG_C>
+__global__ void __launch_bounds__(256) ntt_dit_cross_kernel(const L2Args a) {
+    dit_cross_row<LOG_NC, LOG_C>(a, blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
 template <int LOG_T, int LOG_C>
 __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_dit_local_kernel(const L2Args a) {
     constexpr int T = 1 << LOG_T, C = 1 << LOG_C, NC = 32 * T, N = NC * C, RB = LOG_T - 5;
@@ -350,7 +365,7 @@ __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_dit_local_kernel
     // natural order: thread tid holds k' = rev5(e) T + tid
 #pragma unroll
     for (int e = 0; e < 32; ++e) __stcg(&tmp[rbits<5>(e) * T + tid], csub(csub(v[e], 2 * q), q));
-    if (last_of_row(a, i, C)) dit_cross_row<LOG_T + 5, LOG_C>(a, i, tid, T);
+    if (a.fuse && last_of_row(a, i, C)) dit_cross_row<LOG_T + 5, LOG_C>(a, i, tid, T);
 }
 
 
@@ -387,12 +402,23 @@ int run_l2(const fhe_ctx* ctx, const NttTables& t, int shape, bool inverse, uint
     if (chunk_rows < 1) return set_error(FHE_EINVAL, "two-pass NTT scratch smaller than one row");
     const int chunk = (int)std::min<size_t>(chunk_rows, (size_t)1 << 30);
     a.cnt = reinterpret_cast<int*>(temp + (size_t)chunk * N);
+    const int gx = (NC / 4 + 255) / 256;
     for (int r0 = 0; r0 < rows; r0 += chunk) {
         a.r0 = r0;
         a.nrows = rows - r0 < chunk ? rows - r0 : chunk;
-        FHE_CUDA_TRY(cudaMemsetAsync(a.cnt, 0, (size_t)a.nrows * sizeof(int), st));
+        // fused cross passes need enough rows for the other CTAs to hide them: at least four
+        // waves of local-pass CTAs
+        a.fuse = (size_t)a.nrows * C >= (size_t)4 * ctx->num_sms * kMinB<LOG_T>;
+        if (a.fuse) FHE_CUDA_TRY(cudaMemsetAsync(a.cnt, 0, (size_t)a.nrows * sizeof(int), st));
         qk<<<dim3(C, a.nrows), T, smem, st>>>(a);
         FHE_CUDA_TRY(cudaGetLastError());
+        if (!a.fuse) {
+            if (inverse)
+                ntt_cross_inv_kernel<LOG_T + 5, LOG_C><<<dim3(gx, a.nrows), 256, 0, st>>>(a);
+            else
+                ntt_dit_cross_kernel<LOG_T + 5, LOG_C><<<dim3(gx, a.nrows), 256, 0, st>>>(a);
+            FHE_CUDA_TRY(cudaGetLastError());
+        }
     }
     return FHE_OK;
 }
