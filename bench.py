@@ -415,7 +415,8 @@ def ours(args):
                         "frac": u32_gbs / peaks["hbm_gbs"], "peak_kind": peak_kind,
                         "kernel": "forward plain NTT call at N=2^16 (%s), %d launch(es) per call"
                                   % (variant_name(vf), u32_launches(vf)),
-                        "traffic": traffic_for("paper_2212_14191_gb300/csrc/ntt_u32_kernels.cuh",
+                        "traffic": traffic_for("paper_2212_14191_gb300/csrc/" +
+                                               ("ntt_u32_l2.cu" if ((vf >> 1) & 3) == 3 else "ntt_u32_kernels.cuh"),
                                                "ntt_fwd_u32_n65536_v%d" % vf)}
             # the plain NTT is bound by integer multiplies, not HBM: 3 IMAD per Shoup modmul,
             # (N/2) log2 N modmuls per limb transform, 64 IMAD lanes per clock per SM
