@@ -12,18 +12,41 @@
 namespace fhe {
 namespace {
 
+// Per-limb moduli with the constants of reduce_red: r32 = 2^32 mod q with its Shoup quotient,
+// m32 = floor(2^32 / q).
 struct ModVec {
     uint32_t q[kMaxLimbs];
-    uint64_t mu[kMaxLimbs];  // floor(2^64 / q) for 64-bit Barrett
+    uint32_t r32[kMaxLimbs], r32s[kMaxLimbs], m32[kMaxLimbs];
 };
 
 ModVec modvec(const fhe_ctx* ctx, const int* mod_idx, int n) {
     ModVec m;
     for (int l = 0; l < n; ++l) {
-        m.q[l] = ctx->mods[mod_idx[l]];
-        m.mu[l] = ~0ull / m.q[l];
+        const uint32_t q = ctx->mods[mod_idx[l]];
+        m.q[l] = q;
+        m.r32[l] = (uint32_t)((1ull << 32) % q);
+        m.r32s[l] = shoup_h(m.r32[l], q);
+        m.m32[l] = (uint32_t)((1ull << 32) / q);
     }
     return m;
+}
+
+struct Red {
+    uint32_t q, r32, r32s, m32;
+};
+__device__ __forceinline__ Red red_of(const ModVec& m, int l) { return Red{m.q[l], m.r32[l], m.r32s[l], m.m32[l]}; }
+
+// x mod q for any x < 2^64 (q < 2^30): the high word times 2^32 mod q by Shoup's method and the
+// low word by a 32-bit Barrett step, each in [0, 2q), summed below 4q and corrected twice.
+__device__ __forceinline__ uint32_t reduce_red(uint64_t x, const Red& r) {
+    const uint32_t xl = (uint32_t)x;
+    const uint32_t t = mul_shoup_lazy((uint32_t)(x >> 32), r.r32, r.r32s, r.q);
+    const uint32_t u = xl - __umulhi(xl, r.m32) * r.q;
+    return csub(csub(t + u, 2 * r.q), r.q);
+}
+// v mod q for v < 2^32 (32-bit Barrett, one correction above [0, 2q)).
+__device__ __forceinline__ uint32_t reduce32(uint32_t v, const Red& r) {
+    return csub(v - __umulhi(v, r.m32) * r.q, r.q);
 }
 
 __device__ __forceinline__ uint4 ld4(const uint32_t* p, size_t i) {
@@ -48,8 +71,7 @@ __global__ void k_tensor(const uint32_t* __restrict__ a, const uint32_t* __restr
                          uint32_t* __restrict__ d2, uint32_t* __restrict__ d2c, size_t L4,
                          size_t comp4, ModVec m) {
     const int l = blockIdx.y;
-    const uint32_t q = m.q[l];
-    const uint64_t mu = m.mu[l];
+    const Red rd = red_of(m, l);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < L4; i += (size_t)gridDim.x * blockDim.x) {
         const size_t idx = (size_t)l * L4 + i;
         uint4 a0 = ld4(a, idx), a1 = ld4(a, comp4 + idx), b0 = ld4(b, idx), b1 = ld4(b, comp4 + idx);
@@ -57,9 +79,9 @@ __global__ void k_tensor(const uint32_t* __restrict__ a, const uint32_t* __restr
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             uint32_t x0 = get(a0, k), x1 = get(a1, k), y0 = get(b0, k), y1 = get(b1, k);
-            set(r0, k, reduce_u64((uint64_t)x0 * y0, mu, q));
-            set(r1, k, reduce_u64((uint64_t)x0 * y1 + (uint64_t)x1 * y0, mu, q));
-            set(r2, k, reduce_u64((uint64_t)x1 * y1, mu, q));
+            set(r0, k, reduce_red((uint64_t)x0 * y0, rd));
+            set(r1, k, reduce_red((uint64_t)x0 * y1 + (uint64_t)x1 * y0, rd));
+            set(r2, k, reduce_red((uint64_t)x1 * y1, rd));
         }
         st4(d0, idx, r0);
         st4(d1, idx, r1);
@@ -115,10 +137,9 @@ __global__ void __launch_bounds__(256) k_conv(const ConvArgs a) {
                 for (int k = 0; k < 4; ++k) acc[k] += (uint64_t)get(y[i], k) * h;
             }
             uint4 r;
-            const uint32_t qt = a.dm.q[t];
-            const uint64_t mu = a.dm.mu[t];
+            const Red rd = red_of(a.dm, t);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) set(r, k, reduce_u64(acc[k], mu, qt));
+            for (int k = 0; k < 4; ++k) set(r, k, reduce_red(acc[k], rd));
             st4(a.dst, t * (a.dst_stride / 4) + n, r);
         }
     }
@@ -153,8 +174,7 @@ struct IpArgs {
 
 __global__ void k_inner_product(const IpArgs a) {
     const int t = blockIdx.y;
-    const uint32_t q = a.m.q[t];
-    const uint64_t mu = a.m.mu[t];
+    const Red rd = red_of(a.m, t);
     const int mod = t < a.nl ? t : a.nq + (t - a.nl);
     const size_t limb = a.L4 * 4;
     uint32_t* k0 = a.ks + (size_t)t * limb;
@@ -167,8 +187,8 @@ __global__ void k_inner_product(const IpArgs a) {
             if (j > 0 && j % 15 == 0) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    r0[k] = reduce_u64(r0[k], mu, q);
-                    r1[k] = reduce_u64(r1[k], mu, q);
+                    r0[k] = reduce_red(r0[k], rd);
+                    r1[k] = reduce_red(r1[k], rd);
                 }
             }
             const int lo = j * a.alpha, hi = min(a.nl, lo + a.alpha);
@@ -184,10 +204,10 @@ __global__ void k_inner_product(const IpArgs a) {
                 r1[k] += (uint64_t)get(x, k) * get(w1, k);
             }
         }
-        st4(k0, i, make_uint4(reduce_u64(r0[0], mu, q), reduce_u64(r0[1], mu, q), reduce_u64(r0[2], mu, q),
-                              reduce_u64(r0[3], mu, q)));
-        st4(k1, i, make_uint4(reduce_u64(r1[0], mu, q), reduce_u64(r1[1], mu, q), reduce_u64(r1[2], mu, q),
-                              reduce_u64(r1[3], mu, q)));
+        st4(k0, i, make_uint4(reduce_red(r0[0], rd), reduce_red(r0[1], rd), reduce_red(r0[2], rd),
+                              reduce_red(r0[3], rd)));
+        st4(k1, i, make_uint4(reduce_red(r1[0], rd), reduce_red(r1[1], rd), reduce_red(r1[2], rd),
+                              reduce_red(r1[3], rd)));
     }
 }
 
@@ -239,7 +259,7 @@ __global__ void k_rescale_broadcast(const uint32_t* __restrict__ last, uint32_t*
         for (int k = 0; k < 4; ++k) {
             uint32_t v = get(x, k);
             // v <= half: v mod q;  v > half: (v - ql) mod q = (v mod q) - (ql mod q) mod q
-            uint32_t vm = v % q;
+            uint32_t vm = reduce32(v, red_of(m, i));
             uint32_t o = v > half ? (vm + q - ql_mod) : vm;
             set(r, k, csub(o, q));
         }
@@ -323,7 +343,7 @@ __global__ void k_rescale_prep(const uint32_t* __restrict__ last, const uint32_t
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const uint32_t v = get(lv, k);
-            const uint32_t vm = v % q;
+            const uint32_t vm = reduce32(v, red_of(m, i));
             const uint32_t x = csub(v > half ? (vm + q - ql_mod) : vm, q);  // (v - ql) mod q above half
             set(r, k, csub(mul_shoup(get(yv, k), pi.x, pi.y, q) + x, q));
         }
@@ -648,16 +668,15 @@ int launch_automorph(const fhe_ctx* ctx, const uint32_t* in, uint32_t* out, uint
 __global__ void k_cmult(const uint32_t* __restrict__ ct, const uint32_t* __restrict__ pt, uint32_t* __restrict__ out,
                         size_t L4, size_t comp4, ModVec m) {
     const int l = blockIdx.y;
-    const uint32_t q = m.q[l];
-    const uint64_t mu = m.mu[l];
+    const Red rd = red_of(m, l);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < L4; i += (size_t)gridDim.x * blockDim.x) {
         const size_t idx = (size_t)l * L4 + i;
         const uint4 p = ld4(pt, idx), c0 = ld4(ct, idx), c1 = ld4(ct, comp4 + idx);
         uint4 r0, r1;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            set(r0, k, reduce_u64((uint64_t)get(c0, k) * get(p, k), mu, q));
-            set(r1, k, reduce_u64((uint64_t)get(c1, k) * get(p, k), mu, q));
+            set(r0, k, reduce_red((uint64_t)get(c0, k) * get(p, k), rd));
+            set(r1, k, reduce_red((uint64_t)get(c1, k) * get(p, k), rd));
         }
         st4(out, idx, r0);
         st4(out, comp4 + idx, r1);
