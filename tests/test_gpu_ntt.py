@@ -214,3 +214,49 @@ def test_batch_zero_and_bad_args(fhe, ctx):
     with pytest.raises(fhe.FheError):
         small.ntt_fwd(torch.zeros((1, 1, 1 << 13), dtype=torch.int32, device="cuda"), 13)
     small.close()
+
+
+@pytest.mark.parametrize("variant", [6, 7])
+@pytest.mark.parametrize("logn", [15, 16])
+def test_two_pass_fused_and_chunked(fhe, ctx, logn, variant):
+    """The two-pass variants with enough rows that every row's cross pass runs in its last
+    local-pass CTA (the fused form; smaller calls elsewhere take the stand-alone cross
+    launch, and RESCALE's small buffer many chunks)."""
+    import torch
+    keep = (fhe.fhe_ntt_get_variant(ctx.handle, logn, 0), fhe.fhe_ntt_get_variant(ctx.handle, logn, 1))
+    fhe.fhe_ntt_set_variant(ctx.handle, logn, variant)
+    n = 1 << logn
+    nl, batch = {15: (8, 80), 16: (5, 64)}[logn]        # 640 / 320 rows: above the fusion threshold
+    mods = MODS[:nl]
+    x = I.uniform_residues(700 + logn + variant, mods, batch, n)
+    d = fhe.to_device(x)
+    ctx.ntt_fwd(d, logn)
+    torch.cuda.synchronize()
+    got = fhe.to_host(d)
+    ps = psis(mods, n)
+    for l in range(nl):
+        for b in (0, batch // 3, batch - 1):
+            assert (got[l, b] == ON.ntt(x[l, b], mods[l], ps[l])).all(), (l, b)
+    ctx.ntt_inv(d, logn)
+    assert torch.equal(d, fhe.to_device(x))
+    fhe.fhe_ntt_set_variant(ctx.handle, logn, keep[0], keep[1])
+
+
+@pytest.mark.parametrize("logn", [15, 16])
+def test_rescale_two_pass_small_chunks(fhe, logn):
+    """RESCALE at N >= 2^15 chunks its NTTs through its own 2-limb buffer (a few rows per
+    chunk): bit-exact against the oracle."""
+    import torch
+    from oracle import ckks as C
+    n, nl, batch = 1 << logn, 4, 3
+    qs, ps = P.default_moduli(nl, 2)
+    prm = C.Params(n, qs, ps, alpha=2)
+    c = fhe.Context(logn, qs, ps, alpha=2)
+    x = I.uniform_residues(800 + logn, qs, 2 * batch, n)
+    ct = x.reshape(nl, 2, batch, n).transpose(1, 0, 2, 3).copy()
+    out = c.rescale(fhe.to_device(ct), logn)
+    torch.cuda.synchronize()
+    got = fhe.to_host(out)
+    for b in (0, batch - 1):
+        assert (got[:, :, b] == C.rescale(prm, ct[:, :, b].astype(np.uint64))).all(), b
+    c.close()
