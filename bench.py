@@ -434,7 +434,7 @@ def ours(args):
             roof_tc = {"bound": "tensor", "achieved": tc_tfs, "peak": peak_tc, "unit": "TFLOP/s",
                        "frac": tc_tfs / peak_tc, "peak_kind": peak_kind + " bf16 dense (sustained)",
                        "kernel": "tensor-core forward NTT call (split + 2 tcgen05 GEMMs per chunk)",
-                       "traffic": None}
+                       "traffic": traffic_for("paper_2212_14191_gb300/csrc/ntt_tc.cu", "tc_fwd_call_n65536")}
         roof = roof_u32 if head == "u32" else roof_tc
         line = {
             "metric": METRIC,

@@ -56,20 +56,6 @@ struct GemmArgs {
     int mod[kMaxChunkLimbs];
 };
 
-template <int NT>
-struct GemmCfg {
-    static constexpr int kABytes = kTileM * 128;
-    static constexpr int kBBytes = 4 * NT * 128;
-    static constexpr int kStageBytes = kABytes + kBBytes;
-    // two CTAs per SM (each with its own TMEM accumulators), so one CTA's epilogue overlaps the
-    // other's loads and MMAs; each gets half of the shared memory for its pipeline
-    static constexpr int kCtasPerSm = 2;
-    static constexpr int kBudget = (226 * 1024) / kCtasPerSm - 2048;
-    static constexpr int kStages = kBudget / kStageBytes > 4 ? 4 : kBudget / kStageBytes;
-    static constexpr int kSmem = kStages * kStageBytes + 1024;
-    static constexpr int kTmemCols = 4 * NT;
-};
-
 __device__ __forceinline__ uint2 split_bf16x4(uint32_t v) {
     int x = (int)v;
     const int d0 = ((x + 128) & 255) - 128;
@@ -114,23 +100,36 @@ __global__ void __launch_bounds__(256) tc_split_kernel(const uint32_t* __restric
     }
 }
 
-// Stages 2-5: one 128 x NT output tile of one limb per CTA; 4 warps.
-// thread 0 drives TMA, thread 32 issues the MMAs, all four warps run the epilogue.
+// Stages 2-5, persistent: one CTA per SM walks the 128 x NT output tiles of all limbs,
+// t = blockIdx.x + k gridDim.x (row tiles fastest, so the CTAs running at one time share their
+// B tiles in L2).
+// Warp 0 issues the TMA loads through a 4-stage ring, warp 1 issues the MMAs, warps 2-5 run
+// the epilogue. The accumulators are double-buffered in TMEM (2 x 4 NT columns), so the MMAs
+// of tile k+1 run while the epilogue drains tile k; acc_full[b] / acc_empty[b] hand each
+// buffer between the MMA warp and the four epilogue warps. Every wait is bounded.
 template <int NT>
-__global__ void __launch_bounds__(128, GemmCfg<NT>::kCtasPerSm)
-tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmArgs a) {
+struct GemmCfg {
+    static constexpr int kABytes = kTileM * 128;
+    static constexpr int kBBytes = 4 * NT * 128;
+    static constexpr int kStageBytes = kABytes + kBBytes;
+    static constexpr int kStages = (200 * 1024) / kStageBytes > 4 ? 4 : (200 * 1024) / kStageBytes;
+    static constexpr int kSmem = kStages * kStageBytes + 1024;
+    static constexpr int kAccCols = 4 * NT;
+    static constexpr int kTmemCols = 2 * kAccCols;  // a power of two: 256 or 512
+};
+
+template <int NT>
+__global__ void __launch_bounds__(192, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                          const GemmArgs a, int tiles_m, int tiles_n, int nl) {
     using Cfg = GemmCfg<NT>;
     constexpr int S = Cfg::kStages;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    __shared__ uint64_t full[S], empty[S], done;
+    __shared__ uint64_t full[S], empty[S], acc_full[2], acc_empty[2], drained;
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int z = blockIdx.z;
-    const int m0 = blockIdx.x * kTileM;
-    const int n0 = blockIdx.y * NT;
-    const int a_row0 = z * a.rows * a.Y + m0;
-    const int b_row0 = a.mod[z] * 4 * a.cols + n0;
+    const int ntiles = tiles_m * tiles_n * nl;
     const int nchunks = a.X4 / kChunk;
 
     if (tid == 0) {
@@ -138,7 +137,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             ptx::mbar_init(&full[s], 1);
             ptx::mbar_init(&empty[s], 1);
         }
-        ptx::mbar_init(&done, 1);
+        for (int b = 0; b < 2; ++b) {
+            ptx::mbar_init(&acc_full[b], 1);
+            ptx::mbar_init(&acc_empty[b], 4);
+        }
+        ptx::mbar_init(&drained, 1);
         ptx::fence_mbar_init();
     }
     if (warp == 0) {
@@ -155,101 +158,127 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         ptx::prefetch_tmap(&tmA);
         ptx::prefetch_tmap(&tmB);
         bool ok = true;
-        int issued = 0;
-        for (int c = 0; c < nchunks && ok; ++c) {
-            const int s = c % S;
-            if (c >= S) ok = ptx::mbar_wait(&empty[s], ((c / S) - 1) & 1, a.status, FHE_ETIMEOUT);
-            if (!ok) break;
-            uint8_t* As = sm + s * Cfg::kStageBytes;
-            uint8_t* Bs = As + Cfg::kABytes;
-            ptx::mbar_arrive_expect_tx(&full[s], Cfg::kStageBytes);
-            ptx::tma_load_2d(As, &tmA, c * kChunk, a_row0, &full[s]);
+        long long issued = 0;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const int mt = t % tiles_m, nt = (t / tiles_m) % tiles_n, z = t / (tiles_m * tiles_n);
+            const int a_row0 = z * a.rows * a.Y + mt * kTileM;
+            const int b_row0 = a.mod[z] * 4 * a.cols + nt * NT;
+            for (int c = 0; c < nchunks; ++c, ++issued) {
+                const int s = (int)(issued % S);
+                if (issued >= S) ok = ptx::mbar_wait(&empty[s], (uint32_t)(((issued / S) - 1) & 1), a.status, FHE_ETIMEOUT);
+                if (!ok) break;
+                uint8_t* As = sm + s * Cfg::kStageBytes;
+                uint8_t* Bs = As + Cfg::kABytes;
+                ptx::mbar_arrive_expect_tx(&full[s], Cfg::kStageBytes);
+                ptx::tma_load_2d(As, &tmA, c * kChunk, a_row0, &full[s]);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) ptx::tma_load_2d(Bs + i * NT * 128, &tmB, c * kChunk, b_row0 + i * a.cols, &full[s]);
-            ++issued;
+                for (int i = 0; i < 4; ++i)
+                    ptx::tma_load_2d(Bs + i * NT * 128, &tmB, c * kChunk, b_row0 + i * a.cols, &full[s]);
+            }
         }
         if (!ok) {
-            // drain the copies already in flight (bounded) before the CTA may exit
-            for (int c = (issued > S ? issued - S : 0); c < issued; ++c)
-                ptx::mbar_wait(&full[c % S], (c / S) & 1, nullptr, 0);
+            // drain the copies that may still be in flight (bounded) before the CTA may exit
+            for (long long c = (issued > S ? issued - S : 0); c < issued; ++c)
+                ptx::mbar_wait(&full[c % S], (uint32_t)((c / S) & 1), nullptr, 0);
         }
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer
         // the four digit planes of the constant matrix are consecutive rows of one B tile, so
-        // a single M=128, N=4*NT MMA per K step fills all four accumulators (TMEM columns
-        // [i*NT, (i+1)*NT) hold acc_i) and reads the A tile once
+        // a single M=128, N=4*NT MMA per K step fills all four accumulators of buffer lt & 1
+        // (its TMEM columns [i*NT, (i+1)*NT) hold acc_i) and reads the A tile once
         constexpr uint32_t idesc = ptx::idesc_bf16(kTileM, 4 * NT);
         bool ok = true;
-        for (int c = 0; c < nchunks; ++c) {
-            const int s = c % S;
-            ok = ptx::mbar_wait(&full[s], (c / S) & 1, a.status, FHE_ETIMEOUT);
+        long long consumed = 0;
+        int lt = 0;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
+            const int buf = lt & 1;
+            if (lt >= 2) ok = ptx::mbar_wait(&acc_empty[buf], (uint32_t)(((lt >> 1) - 1) & 1), a.status, FHE_ETIMEOUT);
             if (!ok) break;
             ptx::tc_fence_after();
-            const uint32_t As = ptx::smem_u32(sm + s * Cfg::kStageBytes);
-            const uint32_t Bs = As + Cfg::kABytes;
+            const uint32_t acc = tmem + buf * Cfg::kAccCols;
+            for (int c = 0; c < nchunks; ++c, ++consumed) {
+                const int s = (int)(consumed % S);
+                ok = ptx::mbar_wait(&full[s], (uint32_t)((consumed / S) & 1), a.status, FHE_ETIMEOUT);
+                if (!ok) break;
+                ptx::tc_fence_after();
+                const uint32_t As = ptx::smem_u32(sm + s * Cfg::kStageBytes);
+                const uint32_t Bs = As + Cfg::kABytes;
 #pragma unroll
-            for (int kk = 0; kk < kChunk / 16; ++kk) {
-                const uint64_t adesc = ptx::sdesc_sw128(As + kk * 32);
-                const uint64_t bdesc = ptx::sdesc_sw128(Bs + kk * 32);
-                ptx::mma_bf16(tmem, adesc, bdesc, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+                for (int kk = 0; kk < kChunk / 16; ++kk) {
+                    const uint64_t adesc = ptx::sdesc_sw128(As + kk * 32);
+                    const uint64_t bdesc = ptx::sdesc_sw128(Bs + kk * 32);
+                    ptx::mma_bf16(acc, adesc, bdesc, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+                }
+                ptx::mma_commit(&empty[s]);
             }
-            ptx::mma_commit(&empty[s]);
+            if (ok) ptx::mma_commit(&acc_full[buf]);
         }
-        ptx::mma_commit(&done);  // arrives once every MMA issued above has completed
-    }
-
-    __syncwarp();  // lanes 0 of warps 0 and 1 rejoin their warps
-
-    // ---- epilogue (all warps): TMEM lane = tile row
-    const bool ok = ptx::mbar_wait(&done, 0, a.status, FHE_ETIMEOUT);
-    __syncwarp();  // tcgen05.ld below is .sync.aligned
-    ptx::tc_fence_after();
-    const int mrow = m0 + warp * 32 + lane;
-    const bool valid = ok && mrow < a.rows * a.Y;
-    const int poly = mrow / a.Y, y = mrow % a.Y;
-    const uint32_t q = a.q[z];
-    const uint64_t mu = a.mu[z], off = a.off[z];
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-    // mode 1: this thread's twiddles for column block cb (16 columns, stride Y), loaded one
-    // block ahead so their L2 latency overlaps the TMEM loads and the previous block's work
-    const uint2* twp = a.tw + ((size_t)a.mod[z] * a.cols + n0) * a.Y + y;
-    uint2 wnext[16];
-    if (a.mode == 1 && valid) {
+        // every MMA issued above has completed before TMEM can be released
+        ptx::mma_commit(&drained);
+        ptx::mbar_wait(&drained, 0, nullptr, 0);
+    } else if (warp >= 2) {
+        // ---- epilogue: warp w reads TMEM lanes [32 (w % 4), 32 (w % 4) + 32) = tile rows
+        const int quarter = warp & 3;
+        int lt = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+            const int buf = lt & 1;
+            // warp-uniform verdict: the tcgen05.ld below is .sync.aligned
+            const bool ok =
+                __all_sync(0xffffffffu, ptx::mbar_wait(&acc_full[buf], (uint32_t)((lt >> 1) & 1), a.status, FHE_ETIMEOUT));
+            if (!ok) break;
+            ptx::tc_fence_after();
+            const int mt = t % tiles_m, nt = (t / tiles_m) % tiles_n, z = t / (tiles_m * tiles_n);
+            const int n0 = nt * NT;
+            const int mrow = mt * kTileM + quarter * 32 + lane;
+            const bool valid = mrow < a.rows * a.Y;
+            const int poly = mrow / a.Y, y = mrow % a.Y;
+            const uint32_t q = a.q[z];
+            const uint64_t mu = a.mu[z], off = a.off[z];
+            const uint32_t lane_base = tmem + buf * Cfg::kAccCols + ((uint32_t)(quarter * 32) << 16);
+            const uint2* twp = a.tw + ((size_t)a.mod[z] * a.cols + n0) * a.Y + y;
+            uint2 wnext[16];
+            if (a.mode == 1 && valid) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) wnext[j] = __ldg(&twp[(size_t)j * a.Y]);
-    }
+                for (int j = 0; j < 16; ++j) wnext[j] = __ldg(&twp[(size_t)j * a.Y]);
+            }
 #pragma unroll 1
-    for (int cb = 0; cb < NT / 16; ++cb) {
-        uint32_t r[4][16];
-        uint2 wcur[16];
+            for (int cb = 0; cb < NT / 16; ++cb) {
+                uint32_t r[4][16];
+                uint2 wcur[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) wcur[j] = wnext[j];
-        if (a.mode == 1 && valid && cb + 1 < NT / 16) {
+                for (int j = 0; j < 16; ++j) wcur[j] = wnext[j];
+                if (a.mode == 1 && valid && cb + 1 < NT / 16) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) wnext[j] = __ldg(&twp[(size_t)((cb + 1) * 16 + j) * a.Y]);
-        }
+                    for (int j = 0; j < 16; ++j) wnext[j] = __ldg(&twp[(size_t)((cb + 1) * 16 + j) * a.Y]);
+                }
 #pragma unroll
-        for (int i = 0; i < 4; ++i) ptx::tmem_ld16(lane_base + i * NT + cb * 16, r[i]);
-        ptx::tmem_wait_ld();
-        if (!valid) continue;
+                for (int i = 0; i < 4; ++i) ptx::tmem_ld16(lane_base + i * NT + cb * 16, r[i]);
+                ptx::tmem_wait_ld();
+                if (!valid) continue;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int col = n0 + cb * 16 + j;
-            const long long a0 = __float2int_rn(__uint_as_float(r[0][j]));
-            const long long a1 = __float2int_rn(__uint_as_float(r[1][j]));
-            const long long a2 = __float2int_rn(__uint_as_float(r[2][j]));
-            const long long a3 = __float2int_rn(__uint_as_float(r[3][j]));
-            const long long yv = a0 + 255 * a1 + 65025 * a2 + 16581375 * a3;
-            uint32_t v = reduce_u64((uint64_t)(yv + (long long)off), mu, q);
-            if (a.mode == 1) {
-                const uint2 w = wcur[j];
-                v = mul_shoup(v, w.x, w.y, q);
-                a.planes[(((size_t)z * a.rows + poly) * a.cols + col) * a.Y + y] = split_bf16x4(v);
-            } else {
-                a.out[z * a.out_limb_stride + (size_t)poly * a.N + (size_t)col * a.Y + y] = v;
+                for (int j = 0; j < 16; ++j) {
+                    const int col = n0 + cb * 16 + j;
+                    const long long a0 = __float2int_rn(__uint_as_float(r[0][j]));
+                    const long long a1 = __float2int_rn(__uint_as_float(r[1][j]));
+                    const long long a2 = __float2int_rn(__uint_as_float(r[2][j]));
+                    const long long a3 = __float2int_rn(__uint_as_float(r[3][j]));
+                    const long long yv = a0 + 255 * a1 + 65025 * a2 + 16581375 * a3;
+                    uint32_t v = reduce_u64((uint64_t)(yv + (long long)off), mu, q);
+                    if (a.mode == 1) {
+                        v = mul_shoup(v, wcur[j].x, wcur[j].y, q);
+                        a.planes[(((size_t)z * a.rows + poly) * a.cols + col) * a.Y + y] = split_bf16x4(v);
+                    } else {
+                        a.out[z * a.out_limb_stride + (size_t)poly * a.N + (size_t)col * a.Y + y] = v;
+                    }
+                }
             }
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&acc_empty[buf]);  // this warp's rows of the buffer are read
         }
     }
+
+    __syncwarp();
     ptx::tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -403,8 +432,10 @@ int launch_gemm(const fhe_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb
     using Cfg = GemmCfg<NT>;
     FHE_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem));
     FHE_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<NT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    dim3 grid((g.rows * g.Y + kTileM - 1) / kTileM, g.cols / NT, nl);
-    tc_gemm_kernel<NT><<<grid, 128, Cfg::kSmem, st>>>(ma, mb, g);
+    const int tiles_m = (g.rows * g.Y + kTileM - 1) / kTileM, tiles_n = g.cols / NT;
+    const int ntiles = tiles_m * tiles_n * nl;
+    const int grid = ntiles < ctx->num_sms ? ntiles : ctx->num_sms;
+    tc_gemm_kernel<NT><<<grid, 192, Cfg::kSmem, st>>>(ma, mb, g, tiles_m, tiles_n, nl);
     FHE_CUDA_TRY(cudaGetLastError());
     return FHE_OK;
 }
