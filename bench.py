@@ -432,8 +432,10 @@ def ours(args):
             tc_tfs = tc_flops / (results["tc"]["fwd_ms"] / 1e3) / 1e12
             peak_tc = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
             roof_tc = {"bound": "tensor", "achieved": tc_tfs, "peak": peak_tc, "unit": "TFLOP/s",
-                       "frac": tc_tfs / peak_tc, "peak_kind": peak_kind + " bf16 dense (sustained)",
-                       "kernel": "tensor-core forward NTT call (split + 2 tcgen05 GEMMs per chunk)",
+                       "frac": tc_tfs / peak_tc,
+                       "peak_kind": peak_kind + " bf16 dense (sustained); fp16 operands, same nominal rate",
+                       "kernel": "tensor-core forward NTT call (2 tcgen05 GEMMs per chunk, Stage 1 fused "
+                                 "into the first)",
                        "traffic": traffic_for("paper_2212_14191_gb300/csrc/ntt_tc.cu", "tc_fwd_call_n65536")}
         roof = roof_u32 if head == "u32" else roof_tc
         line = {

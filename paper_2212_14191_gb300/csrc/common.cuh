@@ -77,11 +77,11 @@ struct NttTables {
 // Tensor-core path tables for one ring degree (device memory); see ntt_tc.cu. Built on the
 // first tensor-core call at that degree.
 struct TcTables {
-    uint16_t* mat[4] = {};     // digit planes (bf16) of W1 fwd, W3 fwd, W3 inv, W1 inv: [nmod][4][cols][4K]
+    uint16_t* mat[4] = {};     // digit planes (fp16) of W1 fwd, W3 fwd, W3 inv, W1 inv: [nmod][4][cols][4K]
     uint2* tw_fwd = nullptr;   // [nmod][N1][N2] (psi^((2k1+1) n2), shoup)
     uint2* tw_inv = nullptr;   // [nmod][N2][N1] (N^-1 psi^(-(2k1+1) n2), shoup)
     CUtensorMap map_b[4];      // TMA maps over mat[kind]
-    CUtensorMap map_a[2][2];   // TMA maps over the two plane buffers, inner extent 4*N1 / 4*N2
+    CUtensorMap map_a[2];      // TMA maps over the plane buffer, inner extent 4*N1 / 4*N2
     int n1 = 0, n2 = 0;
     bool built = false;
 };
@@ -115,7 +115,7 @@ struct fhe_ctx {
     int device = 0;
     int num_sms = 0;
     int* d_status = nullptr;  // device error word written by kernels (FHE_ETIMEOUT, ...)
-    void* tc_planes[2] = {};  // tensor-core path scratch: 8-bit digit planes of two operands
+    void* tc_planes = nullptr;  // tensor-core path scratch: digit planes between the two GEMMs
     uint32_t* ntt_temp = nullptr;  // two-pass plain NTT scratch (kNttTempBytes, stays in L2)
     uint32_t* d_mods = nullptr;  // device copy of `mods`
 };
