@@ -170,10 +170,39 @@ def cpu_oracle_kops(budget_s=10.0, batch_cap=NTT_BATCH):
         assert (z == x).all()
         if dt * 2 > budget_s or b * 2 > batch_cap:
             ops = 2 * NTT_LIMBS * b
+            # the same oracle on one thread, on one polynomial per limb
+            x1 = x[:, :1, :]
+            t1 = time.perf_counter()
+            y1, _ = ON.ntt_batch(x1, qs, psis, threads=1)
+            ON.ntt_batch(y1, qs, psis, inverse=True, threads=1)
+            dt1 = time.perf_counter() - t1
             return {"value": ops / dt / 1e3, "unit": "KOPS", "cores": used, "kind": "oracle",
                     "sample": "%d limbs x %d polys, fwd+inv NTT at N=2^16 (%d limb transforms, %.1f s)"
-                              % (NTT_LIMBS, b, ops, dt)}
+                              % (NTT_LIMBS, b, ops, dt),
+                    "single_thread": {"value": 2 * NTT_LIMBS / dt1 / 1e3, "unit": "KOPS", "cores": 1,
+                                      "sample": "%d limbs x 1 poly, fwd+inv (%.2f s)" % (NTT_LIMBS, dt1)},
+                    "host": host_cpu()}
         b *= 2
+
+
+def host_cpu():
+    """CPU model and logical core count of this host, from /proc/cpuinfo where it says."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read()
+        for key in ("model name", "Model", "CPU part"):
+            for line in info.splitlines():
+                if line.split(":")[0].strip() == key:
+                    model = line.split(":", 1)[1].strip()
+                    break
+            if model:
+                model = ("CPU part " + model) if key == "CPU part" else model
+                break
+    except OSError:
+        pass
+    import platform
+    return "%s, %s, %d logical cores" % (model or "unknown model", platform.machine(), os.cpu_count() or 0)
 
 
 def reference_arm(args):
