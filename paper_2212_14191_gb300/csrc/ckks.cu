@@ -613,15 +613,32 @@ int hmult_fused(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint
     k_last_fix<<<stream_grid(ctx, L4, 2), 256, 0, st>>>(y, last, pinv_l, ql, nl, L4);
     FHE_CUDA_TRY(cudaGetLastError());
     const int nout = nl - 1;
-    ModVec qm = modvec(ctx, qidx, nout);
-    k_rescale_prep<<<stream_grid(ctx, L4, 2 * nout), 256, 0, st>>>(last, y, xb, ctx->p_inv, ql, nl, L4, qm);
-    FHE_CUDA_TRY(cudaGetLastError());
     LimbMap qm2;
     for (int c = 0; c < 2; ++c)
         for (int i = 0; i < nout && i < FHE_MAX_MODULI; ++i) {
             qm2.mod[c * nout + i] = (uint8_t)i;
             qm2.q[c * nout + i] = ctx->mods[i];
         }
+    if (ntt_tail_fusable(ctx, FHE_NTT_DEFAULT, logN)) {
+        // z is built while the forward NTT loads it and the output combined while it stores
+        // z^: the same arithmetic as k_rescale_prep / k_hmult_final without their HBM passes
+        HmultTail tl;
+        tl.y = y;
+        tl.last = last;
+        tl.ks = ks;
+        tl.d = dd;
+        tl.out = out;
+        tl.pinv = ctx->p_inv;
+        tl.qlinv = ctx->ql_inv + (size_t)(nl - 1) * ctx->nq;
+        tl.ql = ql;
+        tl.nl = nl;
+        tl.nout = nout;
+        tl.ext = ext;
+        return ntt_u32_l2_tail(ctx, logN, 2 * nout * batch, batch, qm2, st, ns, tl);
+    }
+    ModVec qm = modvec(ctx, qidx, nout);
+    k_rescale_prep<<<stream_grid(ctx, L4, 2 * nout), 256, 0, st>>>(last, y, xb, ctx->p_inv, ql, nl, L4, qm);
+    FHE_CUDA_TRY(cudaGetLastError());
     if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, false, xb, 2 * nout, batch, qm2, st, ns))) return rc;
     k_hmult_final<<<stream_grid(ctx, L4, 2 * nout), 256, 0, st>>>(dd, ks, xb, out, ctx->p_inv,
                                                                 ctx->ql_inv + (size_t)(nl - 1) * ctx->nq, nl, ext,

@@ -157,6 +157,28 @@ int ntt_u32_rows(const fhe_ctx* ctx, uint32_t logN, bool inverse, const RowRef* 
 int ntt_u32_l2(const fhe_ctx* ctx, uint32_t logN, int shape, bool inverse, uint32_t* d, int rows, int batch,
                const LimbMap& map, const RowRef* rowtab, cudaStream_t st, NttScratch scr);
 
+// The HMULT + RESCALE tail (ckks.cu) fused into the forward two-pass NTT of z. Row r of the
+// transform is limb (c, i) = (r / batch / nout, r / batch % nout) of polynomial p = r % batch.
+// The local pass loads z = y_i P^-1 + [last]_q_i (last taken centred in (-q_l/2, q_l/2]) instead
+// of a stored z, and the cross pass stores out_i = (ks_i P^-1 + d_i - z^_i) q_l^-1 instead of z^:
+// the two HBM passes that would build z and combine z^ disappear.
+struct HmultTail {
+    const uint32_t* y;     // (2, nl, batch, N): ModDown's basis conversion, coefficient domain
+    const uint32_t* last;  // (2, batch, N): the relinearised last limb, coefficient domain, [0, q_l)
+    const uint32_t* ks;    // (2, ext, batch, N): key-switching output, NTT domain
+    const uint32_t* d;     // (2, nl, batch, N): d0, d1 of the tensor product, NTT domain
+    uint32_t* out;         // (2, nout, batch, N)
+    const uint2* pinv;     // [i] P^-1 mod q_i (value, Shoup quotient)
+    const uint2* qlinv;    // [i] q_l^-1 mod q_i
+    uint32_t ql;
+    int nl, nout, ext;
+};
+// True when the forward NTT of this ring degree runs the two-pass plain kernels (the only ones
+// with the fused tail); the tail then runs as one call to ntt_u32_l2_tail.
+bool ntt_tail_fusable(const fhe_ctx* ctx, int path, uint32_t logN);
+int ntt_u32_l2_tail(const fhe_ctx* ctx, uint32_t logN, int rows, int batch, const LimbMap& map, cudaStream_t st,
+                    NttScratch scr, const HmultTail& tail);
+
 // Plain-path batched NTT over `n_limbs` limbs whose moduli are map.mod[l].
 int ntt_u32(const fhe_ctx* ctx, uint32_t logN, bool inverse, uint32_t* d, int n_limbs,
             int batch, const LimbMap& map, cudaStream_t stream, NttScratch scr = NttScratch());

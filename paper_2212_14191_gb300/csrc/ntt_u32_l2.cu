@@ -42,7 +42,17 @@ struct L2Args {
     int* cnt;                // per chunk row: local-pass CTAs finished (zeroed before each chunk)
     int fuse;                // 1: the last local-pass CTA of a row runs its cross pass
     LimbMap map;
+    HmultTail tail;          // TAIL instantiations of the forward kernels only
 };
+
+// Row r of a TAIL transform: component c, output limb i, polynomial p.
+struct TailRow {
+    int c, i, p;
+};
+__device__ __forceinline__ TailRow tail_row(const L2Args& a, int r) {
+    const int limb = r / a.batch;
+    return {limb / a.tail.nout, limb % a.tail.nout, r % a.batch};
+}
 
 // The C local-pass CTAs of a row each count themselves in cnt[i] once their scratch stores
 // are visible (fence, then atomic); the one that completes the count runs the row's cross
@@ -223,12 +233,24 @@ __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_quarter_inv_kern
 // contiguous streams and writing C contiguous streams. Pass 1 reads at stride C (the C CTAs
 // of a row share every sector through L2), where the decimation-in-frequency order would
 // store at stride C.
-template <int LOG_NC, int LOG_C>
+template <int LOG_NC, int LOG_C, bool TAIL>
 __device__ __forceinline__ void dit_cross_row(const L2Args& a, int i, int p0, int pstep) {
     constexpr int NC = 1 << LOG_NC, C = 1 << LOG_C, N = NC * C;
     uint32_t q;
     int mod;
     uint32_t* row = l2_row<N>(a, a.r0 + i, &q, &mod);
+    // TAIL: out = (ks P^-1 + d - z^) q_l^-1 is stored instead of z^
+    const uint32_t* ksr = nullptr;
+    const uint32_t* dr = nullptr;
+    uint2 pinv = make_uint2(0, 0), qlinv = make_uint2(0, 0);
+    if constexpr (TAIL) {
+        const TailRow t = tail_row(a, a.r0 + i);
+        ksr = a.tail.ks + (((size_t)t.c * a.tail.ext + t.i) * a.batch + t.p) * N;
+        dr = a.tail.d + (((size_t)t.c * a.tail.nl + t.i) * a.batch + t.p) * N;
+        row = a.tail.out + (((size_t)t.c * a.tail.nout + t.i) * a.batch + t.p) * N;
+        pinv = __ldg(&a.tail.pinv[t.i]);
+        qlinv = __ldg(&a.tail.qlinv[t.i]);
+    }
     const uint32_t* tmp = a.temp + (size_t)i * N;
     const uint2* twist = a.twist + (size_t)mod * (C - 1) * NC;
     const uint2* om = a.omega + (size_t)mod * (C / 2);
@@ -239,6 +261,17 @@ __device__ __forceinline__ void dit_cross_row(const L2Args& a, int i, int p0, in
         uint4 x[C];
 #pragma unroll
         for (int jj = 0; jj < C; ++jj) x[jj] = __ldcg(reinterpret_cast<const uint4*>(tmp + jj * NC) + p4);
+        // TAIL: ks and d of these outputs, loaded with the scratch so their HBM latency overlaps
+        // (for C <= 4; with C = 8 they would not fit in the registers and load at the store)
+        constexpr bool kHoist = TAIL && C <= 4;
+        uint4 kv[kHoist ? C : 1], dv[kHoist ? C : 1];
+        if constexpr (kHoist) {
+#pragma unroll
+            for (int t = 0; t < C; ++t) {
+                kv[t] = __ldcs(reinterpret_cast<const uint4*>(ksr + t * NC) + p4);
+                dv[t] = __ldcs(reinterpret_cast<const uint4*>(dr + t * NC) + p4);
+            }
+        }
         uint4 tw2[C > 1 ? 2 * (C - 1) : 1];  // four twist pairs of every j >= 1: two uint4 each
 #pragma unroll
         for (int jj = 1; jj < C; ++jj) {
@@ -288,17 +321,41 @@ __device__ __forceinline__ void dit_cross_row(const L2Args& a, int i, int p0, in
                 else o[t].w = val;
             }
         }
+        if constexpr (TAIL) {
 #pragma unroll
-        for (int t = 0; t < C; ++t) reinterpret_cast<uint4*>(row + t * NC)[p4] = o[t];
+            for (int t = 0; t < C; ++t) {
+                uint4 kt, dt;
+                if constexpr (kHoist) {
+                    kt = kv[t];
+                    dt = dv[t];
+                } else {
+                    kt = __ldcs(reinterpret_cast<const uint4*>(ksr + t * NC) + p4);
+                    dt = __ldcs(reinterpret_cast<const uint4*>(dr + t * NC) + p4);
+                }
+                uint4 r;
+                r.x = mul_shoup(csub(mul_shoup(kt.x, pinv.x, pinv.y, q) + dt.x, q) + q - o[t].x, qlinv.x,
+                                qlinv.y, q);
+                r.y = mul_shoup(csub(mul_shoup(kt.y, pinv.x, pinv.y, q) + dt.y, q) + q - o[t].y, qlinv.x,
+                                qlinv.y, q);
+                r.z = mul_shoup(csub(mul_shoup(kt.z, pinv.x, pinv.y, q) + dt.z, q) + q - o[t].z, qlinv.x,
+                                qlinv.y, q);
+                r.w = mul_shoup(csub(mul_shoup(kt.w, pinv.x, pinv.y, q) + dt.w, q) + q - o[t].w, qlinv.x,
+                                qlinv.y, q);
+                __stcs(reinterpret_cast<uint4*>(row + t * NC) + p4, r);
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < C; ++t) reinterpret_cast<uint4*>(row + t * NC)[p4] = o[t];
+        }
     }
 }
 
-template <int LOG_NC, int LOG_C>
+template <int LOG_NC, int LOG_C, bool TAIL>
 __global__ void __launch_bounds__(256) ntt_dit_cross_kernel(const L2Args a) {
-    dit_cross_row<LOG_NC, LOG_C>(a, blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+    dit_cross_row<LOG_NC, LOG_C, TAIL>(a, blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
-template <int LOG_T, int LOG_C>
+template <int LOG_T, int LOG_C, bool TAIL>
 __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_dit_local_kernel(const L2Args a) {
     constexpr int T = 1 << LOG_T, C = 1 << LOG_C, NC = 32 * T, N = NC * C, RB = LOG_T - 5;
     extern __shared__ __align__(128) uint32_t work[];
@@ -311,8 +368,26 @@ __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_dit_local_kernel
     uint32_t* tmp = a.temp + (size_t)i * N + (size_t)j * NC;
     const uint2* tw = a.tw_sub + (size_t)mod * NC;
     uint32_t v[32];
+    if constexpr (TAIL) {
+        // z = y P^-1 + [last]_q (last centred: values above (q_l - 1) / 2 stand for last - q_l)
+        const TailRow t = tail_row(a, a.r0 + i);
+        const uint32_t* yr = a.tail.y + (((size_t)t.c * a.tail.nl + t.i) * a.batch + t.p) * N;
+        const uint32_t* lr = a.tail.last + ((size_t)t.c * a.batch + t.p) * N;
+        const uint2 pinv = __ldg(&a.tail.pinv[t.i]);
+        const uint32_t ql = a.tail.ql, half = (ql - 1) / 2, qlm = ql % q;
+        const bool one_sub = ql <= 2 * (uint64_t)q;  // last < q_l <= 2q: one subtraction reduces it
 #pragma unroll
-    for (int e = 0; e < 32; ++e) v[e] = __ldg(&row[(size_t)(tid + T * e) * C + j]);
+        for (int e = 0; e < 32; ++e) {
+            const size_t idx = (size_t)(tid + T * e) * C + j;
+            const uint32_t lv = __ldcs(&lr[idx]), yv = __ldcs(&yr[idx]);
+            const uint32_t vm = one_sub ? csub(lv, q) : lv % q;
+            const uint32_t x = csub(lv > half ? vm + q - qlm : vm, q);
+            v[e] = csub(mul_shoup(yv, pinv.x, pinv.y, q) + x, q);
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < 32; ++e) v[e] = __ldg(&row[(size_t)(tid + T * e) * C + j]);
+    }
     // round A: stages 0..4 of the NC-point transform
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
@@ -365,18 +440,20 @@ __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_dit_local_kernel
     // natural order: thread tid holds k' = rev5(e) T + tid
 #pragma unroll
     for (int e = 0; e < 32; ++e) __stcg(&tmp[rbits<5>(e) * T + tid], csub(csub(v[e], 2 * q), q));
-    if (a.fuse && last_of_row(a, i, C)) dit_cross_row<LOG_T + 5, LOG_C>(a, i, tid, T);
+    if (a.fuse && last_of_row(a, i, C)) dit_cross_row<LOG_T + 5, LOG_C, TAIL>(a, i, tid, T);
 }
 
 
-template <int LOG_T, int LOG_C>
+template <int LOG_T, int LOG_C, bool TAIL>
 int run_l2(const fhe_ctx* ctx, const NttTables& t, int shape, bool inverse, uint32_t* d, int rows, int batch,
-           const LimbMap& map, const RowRef* rowtab, cudaStream_t st, uint32_t* temp, size_t temp_bytes) {
+           const LimbMap& map, const RowRef* rowtab, cudaStream_t st, uint32_t* temp, size_t temp_bytes,
+           const HmultTail* tail) {
     constexpr int T = 1 << LOG_T, C = 1 << LOG_C, NC = 32 * T, N = NC * C;
     constexpr int smem = PadLayout<LOG_T>::kWords * 4;
     // forward: decimation in time (local NC-point transforms, then twist + C-point DFT);
     // inverse: decimation in frequency (quarter pass, then cross stages with N^-1)
-    auto qk = inverse ? ntt_quarter_inv_kernel<LOG_T, LOG_C> : ntt_dit_local_kernel<LOG_T, LOG_C>;
+    if (TAIL && (inverse || rowtab || !tail)) return set_error(FHE_EINVAL, "fused tail: forward, limb-map rows only");
+    auto qk = inverse ? ntt_quarter_inv_kernel<LOG_T, LOG_C> : ntt_dit_local_kernel<LOG_T, LOG_C, TAIL>;
     FHE_CUDA_TRY(cudaFuncSetAttribute(qk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int carve = (int)((kMinB<LOG_T> * (smem + 1024) * 100 + 228 * 1024 - 1) / (228 * 1024));
     FHE_CUDA_TRY(cudaFuncSetAttribute(qk, cudaFuncAttributePreferredSharedMemoryCarveout, carve > 100 ? 100 : carve));
@@ -397,6 +474,8 @@ int run_l2(const fhe_ctx* ctx, const NttTables& t, int shape, bool inverse, uint
     a.twist = t.dit_twist[shape];
     a.omega = t.dit_omega[shape];
     a.map = map;
+    memset(&a.tail, 0, sizeof(a.tail));
+    if (TAIL) a.tail = *tail;
     // chunk rows: N residues of scratch and one completion counter each
     const size_t chunk_rows = temp_bytes / ((size_t)N * 4 + 4);
     if (chunk_rows < 1) return set_error(FHE_EINVAL, "two-pass NTT scratch smaller than one row");
@@ -416,7 +495,7 @@ int run_l2(const fhe_ctx* ctx, const NttTables& t, int shape, bool inverse, uint
             if (inverse)
                 ntt_cross_inv_kernel<LOG_T + 5, LOG_C><<<dim3(gx, a.nrows), 256, 0, st>>>(a);
             else
-                ntt_dit_cross_kernel<LOG_T + 5, LOG_C><<<dim3(gx, a.nrows), 256, 0, st>>>(a);
+                ntt_dit_cross_kernel<LOG_T + 5, LOG_C, TAIL><<<dim3(gx, a.nrows), 256, 0, st>>>(a);
             FHE_CUDA_TRY(cudaGetLastError());
         }
     }
@@ -425,8 +504,10 @@ int run_l2(const fhe_ctx* ctx, const NttTables& t, int shape, bool inverse, uint
 
 }  // namespace
 
-int ntt_u32_l2(const fhe_ctx* ctx, uint32_t logN, int shape, bool inverse, uint32_t* d, int rows, int batch,
-               const LimbMap& map, const RowRef* rowtab, cudaStream_t st, NttScratch scr) {
+namespace {
+template <bool TAIL>
+int ntt_u32_l2_impl(const fhe_ctx* ctx, uint32_t logN, int shape, bool inverse, uint32_t* d, int rows, int batch,
+                    const LimbMap& map, const RowRef* rowtab, cudaStream_t st, NttScratch scr, const HmultTail* tail) {
     const NttTables& t = ctx->ntt[logN];
     uint32_t* temp = scr.p ? scr.p : ctx->ntt_temp;
     const size_t temp_bytes = scr.p ? scr.bytes : kNttTempBytes;
@@ -435,14 +516,37 @@ int ntt_u32_l2(const fhe_ctx* ctx, uint32_t logN, int shape, bool inverse, uint3
     if (!ntt_variant_shape(logN, shape, &log_t, &log_c) || log_c == 0)
         return set_error(FHE_EINVAL, "two-pass NTT needs N >= 2^15");
     if (log_t == 9 && log_c == 2)
-        return run_l2<9, 2>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes);
+        return run_l2<9, 2, TAIL>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes, tail);
     if (log_t == 9 && log_c == 1)
-        return run_l2<9, 1>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes);
+        return run_l2<9, 1, TAIL>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes, tail);
     if (log_t == 8 && log_c == 3)
-        return run_l2<8, 3>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes);
+        return run_l2<8, 3, TAIL>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes, tail);
     if (log_t == 8 && log_c == 2)
-        return run_l2<8, 2>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes);
+        return run_l2<8, 2, TAIL>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes, tail);
     return set_error(FHE_EINVAL, "no two-pass kernel for this shape");
+}
+}  // namespace
+
+int ntt_u32_l2(const fhe_ctx* ctx, uint32_t logN, int shape, bool inverse, uint32_t* d, int rows, int batch,
+               const LimbMap& map, const RowRef* rowtab, cudaStream_t st, NttScratch scr) {
+    return ntt_u32_l2_impl<false>(ctx, logN, shape, inverse, d, rows, batch, map, rowtab, st, scr, nullptr);
+}
+
+bool ntt_tail_fusable(const fhe_ctx* ctx, int path, uint32_t logN) {
+    if (path == FHE_NTT_DEFAULT) path = ctx->default_path;
+    if (path != FHE_NTT_U32 || logN < 15 || logN > FHE_LOGN_MAX) return false;
+    const int v = ctx->ntt_variant[0][logN];
+    int log_t, log_c;
+    return ntt_variant_exchange(v) == 3 && ntt_variant_shape(logN, v, &log_t, &log_c) && log_c > 0;
+}
+
+int ntt_u32_l2_tail(const fhe_ctx* ctx, uint32_t logN, int rows, int batch, const LimbMap& map, cudaStream_t st,
+                    NttScratch scr, const HmultTail& tail) {
+    if (!ntt_tail_fusable(ctx, FHE_NTT_U32, logN)) return set_error(FHE_EINVAL, "fused tail needs the two-pass NTT");
+    if (rows == 0) return FHE_OK;
+    const int v = ctx->ntt_variant[0][logN];
+    // the data pointer is not read or written by the TAIL kernels (rows come from y / go to out)
+    return ntt_u32_l2_impl<true>(ctx, logN, v & 1, false, tail.out, rows, batch, map, nullptr, st, scr, &tail);
 }
 
 }  // namespace fhe

@@ -231,3 +231,38 @@ def test_concurrent_streams_share_a_context(fhe):
     assert (got[:, :, 0] == C.hmult(prm, nl, a0[:, :, 0].astype(U64), b0[:, :, 0].astype(U64), evk)).all()
     fhe.fhe_device_status(ctx.handle, 1)
     ctx.close()
+
+
+@pytest.mark.parametrize("fwd_variant", [7, 6])
+def test_hmult_fused_rescale_tail(fhe, fwd_variant):
+    """The RESCALE tail fused into the two-pass forward NTT (z built on load, the output combined
+    on store) against the same HMULT with a forward variant that runs the tail as separate
+    passes: identical outputs for every pair, and the oracle on two of them. N = 2^15, 6 + 2
+    limbs, 5 pairs (a batch that is not a multiple of the row chunking)."""
+    import torch
+    logn, nl, K, batch = 15, 6, 2, 5
+    n = 1 << logn
+    qs, ps = P.default_moduli(nl, K)
+    prm = C.Params(n, qs, ps, alpha=2)
+    s, evk = make_key(prm, 600)
+    A, B = batch_cts(prm, nl, batch, 610), batch_cts(prm, nl, batch, 611)
+    za, ca = encrypt_pair(prm, nl, s, 620)
+    zb, cb = encrypt_pair(prm, nl, s, 630)
+    A[:, :, 2], B[:, :, 2] = ca, cb
+    ctx = fhe.Context(logn, qs, ps, alpha=2)
+    da, db, de = fhe.to_device(A), fhe.to_device(B), fhe.to_device(evk.astype(np.uint32))
+    fhe.fhe_ntt_set_variant(ctx.handle, logn, fwd_variant, 7)   # two-pass forward: fused tail
+    fused = ctx.hmult(da, db, de, logn).clone()
+    fhe.fhe_ntt_set_variant(ctx.handle, logn, 0, 7)             # cluster forward: separate passes
+    sep = ctx.hmult(da, db, de, logn).clone()
+    torch.cuda.synchronize()
+    assert torch.equal(fused, sep)
+    got = fhe.to_host(fused)
+    for b in (0, 2):
+        want = C.hmult(prm, nl, A[:, :, b].astype(U64), B[:, :, b].astype(U64), evk)
+        assert (got[:, :, b] == want).all(), b
+    dec = C.decode(np.array(C.decrypt_coeffs(prm, got[:, :, 2].astype(U64), s), dtype=float),
+                   2.0 ** 60 / qs[nl - 1])
+    assert np.abs(dec - za * zb).max() / np.abs(za * zb).max() < 1e-5
+    fhe.fhe_device_status(ctx.handle, 1)
+    ctx.close()
