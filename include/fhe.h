@@ -130,6 +130,23 @@ int fhe_ntt_set_variant(fhe_ctx* ctx, uint32_t logN, int fwd_variant, int inv_va
 int fhe_autotune_ntt(fhe_ctx* ctx, uint32_t logN, uint32_t* d, int n_limbs, int batch, int reps,
                      float* ms_out, void* stream);
 
+/*
+ * Basis conversion (Conv of ModUp and ModDown, Sec. IV-A) kernels; both compute the same exact
+ * residues sum_i [x_i (B/b_i)^-1]_{b_i} [B/b_i]_t mod q_t.
+ *   FHE_CONV_CUDA : 64-bit multiply-adds on the CUDA cores (the default: faster on GB300).
+ *   FHE_CONV_TC   : the same products as an exact fp16 GEMM of 8-bit segments on the tcgen05
+ *                   tensor cores; with at most 15 terms per output the reconstruction costs
+ *                   about as much as the multiply-adds it replaces.
+ * fhe_conv_set_path -- select the kernel used by this context's key switching (HMULT,
+ *   HROTATE, fhe_keyswitch); FHE_EINVAL for another value. Must not race with calls that use
+ *   the context.
+ * fhe_conv_get_path -- the selected kernel, or -1 if ctx is NULL.
+ */
+#define FHE_CONV_CUDA 0
+#define FHE_CONV_TC 1
+int fhe_conv_set_path(fhe_ctx* ctx, int path);
+int fhe_conv_get_path(const fhe_ctx* ctx);
+
 /* Operations for fhe_scratch_bytes. */
 #define FHE_OP_HMULT 1
 #define FHE_OP_KEYSWITCH 2

@@ -159,6 +159,32 @@ int launch_conv(const ConvArgs& ca, dim3 grid, size_t smem, cudaStream_t st) {
     return FHE_OK;
 }
 
+// The context's basis-conversion kernel: tensor cores (conv_tc.cu) or the CUDA-core k_conv.
+int run_conv(const fhe_ctx* ctx, const ConvArgs& ca, const ConvTable& ct, dim3 grid, size_t smem, cudaStream_t st) {
+    if (ctx->conv_path == FHE_CONV_TC && ct.bdig && ca.ndst <= 64) {
+        TcConvArgs t;
+        memset(&t, 0, sizeof(t));
+        t.src = ca.src;
+        t.src_stride = ca.src_stride;
+        t.nsrc = ca.nsrc;
+        for (int i = 0; i < ca.nsrc; ++i) {
+            t.src_q[i] = ca.src_q[i];
+            t.hat_inv[i] = ca.hat_inv[i];
+        }
+        t.bdig = ct.bdig;
+        t.dst = ca.dst;
+        t.dst_stride = ca.dst_stride;
+        t.ndst = ca.ndst;
+        for (int d = 0; d < ca.ndst; ++d) {
+            t.dst_mod[d] = ca.dst_mod[d];
+            t.dst_q[d] = ca.dm.q[d];
+        }
+        t.ncoef = ca.L4 * 4;
+        return launch_conv_tc(ctx, t, st);
+    }
+    return launch_conv(ca, grid, smem, st);
+}
+
 // ---- KS-4: inner product with the evaluation key (Hada-Mult + Ele-Add), all slices at once:
 //   ks_c[t] = sum_j d~_j[t] * evk_{j,c}[t],  d~_j[t] = d2[t] on slice j's own limbs, else the
 //   NTT of slice j's ModUp output. One pass reads every slice and writes ks0, ks1 once.
@@ -447,7 +473,7 @@ int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const u
         size_t smem = (size_t)ca.nsrc * nd * 4;
         dim3 g = stream_grid(ctx, L4, 1);
         g.x = std::min<unsigned>(g.x * 4, (unsigned)((L4 + 255) / 256));
-        if ((rc = launch_conv(ca, g, smem, st))) return rc;
+        if ((rc = run_conv(ctx, ca, ct, g, smem, st))) return rc;
         // KS-3: NTT of the converted limbs
         LimbMap lm;
         for (int t = 0; t < nd; ++t) {
@@ -503,7 +529,7 @@ int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const u
         ca.L4 = L4;
         dim3 g = stream_grid(ctx, L4, 1);
         g.x = std::min<unsigned>(g.x * 4, (unsigned)((L4 + 255) / 256));
-        if ((rc = launch_conv(ca, g, (size_t)K * nl * 4, st))) return rc;
+        if ((rc = run_conv(ctx, ca, ctx->moddown, g, (size_t)K * nl * 4, st))) return rc;
     }
     if (2 * nl > kMaxLimbs) return set_error(FHE_EINVAL, "too many limbs");
     LimbMap qm2;

@@ -87,10 +87,15 @@ struct TcTables {
 };
 
 // Basis-conversion constants (Conv of Sec. IV-A) for one source basis.
+// Reduction length of the tensor-core Conv operand rows: 4 digits x at most 15 source limbs,
+// padded to the 64 fp16 of one 128-byte shared-memory row.
+constexpr int kConvKPad = 64;
+
 struct ConvTable {
     // src: hat_inv[i] = [(B/b_i)^-1]_{b_i} with Shoup quotient; dst: hat_mod[i][t] = [B/b_i]_t
     uint2* hat_inv = nullptr;   // [nsrc]
     uint32_t* hat_mod = nullptr; // [nsrc][nmod]  indexed by destination modulus index
+    uint16_t* bdig = nullptr;   // [nmod][4][kConvKPad] fp16 digits of [hat_mod[i][t] 256^j]_t (tensor-core Conv)
     std::vector<uint2> hat_inv_h; // host copy of hat_inv (passed to kernels by value)
     int nsrc = 0;
 };
@@ -104,6 +109,7 @@ struct fhe_ctx {
     std::vector<uint32_t> mods;  // q_0.., p_0..
     fhe::NttTables ntt[FHE_LOGN_MAX + 1];
     int ntt_variant[2][FHE_LOGN_MAX + 1] = {};  // plain-path variant per direction (0 fwd, 1 inv) and logN
+    int conv_path = FHE_CONV_CUDA;              // basis-conversion kernel (fhe_conv_set_path)
     fhe::TcTables tc[FHE_LOGN_MAX + 1];
     // conv tables: modup[j][e] for slice j ending (exclusive) at limb e; moddown from P
     std::vector<std::vector<fhe::ConvTable>> modup;
@@ -188,6 +194,29 @@ int ntt_tc(const fhe_ctx* ctx, uint32_t logN, bool inverse, uint32_t* d, int n_l
 int build_tc_tables(fhe_ctx* ctx, uint32_t logN);
 int build_ntt_tables(fhe_ctx* ctx, uint32_t logN);
 
+// Basis conversion (Conv of Sec. IV-A) on the tensor cores (conv_tc.cu): for every
+// coefficient n and destination t, dst_t[n] = sum_i [x_i[n] (B/b_i)^-1]_{b_i} [B/b_i]_t mod q_t,
+// as one exact fp16 GEMM per 128 coefficients (K' = 4 nsrc data digits, N = 4 ndst constant
+// digits, fp32 accumulation in TMEM) and a shift-and-add reconstruction.
+struct TcConvArgs {
+    const uint32_t* src;
+    size_t src_stride;         // elements between source limbs
+    int nsrc;                  // 1..15
+    uint32_t src_q[16];
+    uint2 hat_inv[16];         // [(B/b_i)^-1]_{b_i} (value, Shoup quotient)
+    const uint16_t* bdig;      // ConvTable::bdig
+    uint32_t* dst;
+    size_t dst_stride;
+    int ndst;                  // 1..64
+    uint8_t dst_mod[64];       // modulus index of destination t
+    uint32_t dst_q[64];
+    uint2 dst_c16[64];         // [2^16]_{q_t} (value, Shoup quotient)
+    uint2 dst_one[64];         // 1 with its Shoup quotient floor(2^32 / q_t): a reduction mod q_t
+    uint32_t dst_off[64];      // the least multiple of q_t that is >= 2^29
+    size_t ncoef;              // coefficients per limb (batch x N)
+};
+int launch_conv_tc(const fhe_ctx* ctx, const TcConvArgs& a, cudaStream_t st);
+
 // Dispatch on path.
 int ntt_any(const fhe_ctx* ctx, int path, uint32_t logN, bool inverse, uint32_t* d, int n_limbs,
             int batch, const LimbMap& map, cudaStream_t stream, NttScratch scr = NttScratch());
@@ -251,6 +280,30 @@ __device__ __forceinline__ uint32_t csub(uint32_t x, uint32_t m) { return min(x,
 
 __device__ __forceinline__ uint32_t mul_shoup(uint32_t x, uint32_t w, uint32_t wq, uint32_t q) {
     return csub(mul_shoup_lazy(x, w, wq, q), q);
+}
+
+// Four balanced base-256 digits of v < 2^30 as fp16: v = sum_j (b_j - 128) 256^j where b_j are
+// the bytes of v + 0x80808080 (no wrap-around since v < 2^30). The half with bits 0x64bb is
+// exactly 1024 + bb, so one byte permute per pair of digits and one f16x2 subtraction of
+// 1152 give the digits exactly (every integer of magnitude <= 2048 is exact in fp16).
+__device__ __forceinline__ uint2 split_f16x4(uint32_t v) {
+    const uint32_t y = v + 0x80808080u;
+    const uint32_t lo = __byte_perm(y, 0x64u, 0x4140), hi = __byte_perm(y, 0x64u, 0x4342);
+    uint2 r;
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r.x) : "r"(lo), "r"(0x64806480u));
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r.y) : "r"(hi), "r"(0x64806480u));
+    return r;
+}
+
+// fp16 bit pattern of a small integer (exact for |e| <= 2048; host side).
+inline uint16_t f16_bits_of_small_int(int e) {
+    if (e == 0) return 0;
+    const uint16_t sign = e < 0 ? 0x8000 : 0;
+    const uint32_t a = (uint32_t)(e < 0 ? -e : e);
+    int ex = 0;
+    while ((a >> (ex + 1)) != 0) ++ex;  // 2^ex <= a < 2^(ex+1)
+    const uint32_t mant = (a << (10 - ex)) & 0x3FFu;
+    return (uint16_t)(sign | ((ex + 15) << 10) | mant);
 }
 
 // 64-bit Barrett: x mod q for any x < 2^64, with mu = floor(2^64 / q) (q < 2^31).

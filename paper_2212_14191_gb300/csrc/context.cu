@@ -112,11 +112,26 @@ static int build_conv(fhe_ctx* ctx, const std::vector<int>& src, ConvTable* out)
             hat_mod[(size_t)i * nmod + t] = pr;
         }
     }
+    // tensor-core Conv operand: for destination modulus t and digit k, row K' = 4 i + j holds
+    // the k-th balanced base-256 digit of [(B / b_i) 256^j]_t as fp16 (64 entries, zero padded)
+    std::vector<uint16_t> bdig((size_t)nmod * 4 * kConvKPad, 0);
+    for (int t = 0; t < nmod; ++t) {
+        const uint32_t mt = ctx->mods[t];
+        for (int i = 0; i < ns; ++i)
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t w = mulmod_h(hat_mod[(size_t)i * nmod + t], powmod_h(256 % mt, j, mt), mt);
+                const uint32_t y = w + 0x80808080u;  // w < 2^30: bytes of y minus 128 are the digits
+                for (int k = 0; k < 4; ++k)
+                    bdig[((size_t)t * 4 + k) * kConvKPad + 4 * i + j] =
+                        f16_bits_of_small_int((int)((y >> (8 * k)) & 0xFF) - 128);
+            }
+    }
     out->nsrc = ns;
     out->hat_inv_h = hat_inv;
     int rc;
     if ((rc = dev_upload(ctx, &out->hat_inv, hat_inv))) return rc;
     if ((rc = dev_upload(ctx, &out->hat_mod, hat_mod))) return rc;
+    if ((rc = dev_upload(ctx, &out->bdig, bdig))) return rc;
     return FHE_OK;
 }
 
@@ -334,6 +349,15 @@ int fhe_ntt_set_variant(fhe_ctx* ctx, uint32_t logN, int fwd_variant, int inv_va
     ctx->ntt_variant[1][logN] = inv_variant;
     return FHE_OK;
 }
+
+int fhe_conv_set_path(fhe_ctx* ctx, int path) {
+    FHE_CHECK(ctx != nullptr, "ctx is NULL");
+    FHE_CHECK(path == FHE_CONV_CUDA || path == FHE_CONV_TC, "path must be FHE_CONV_CUDA or FHE_CONV_TC");
+    ctx->conv_path = path;
+    return FHE_OK;
+}
+
+int fhe_conv_get_path(const fhe_ctx* ctx) { return ctx ? ctx->conv_path : -1; }
 
 int fhe_autotune_ntt(fhe_ctx* ctx, uint32_t logN, uint32_t* d, int n_limbs, int batch, int reps,
                      float* ms_out, void* stream) {

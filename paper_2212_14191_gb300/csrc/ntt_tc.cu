@@ -57,19 +57,6 @@ struct GemmArgs {
     int mod[kMaxChunkLimbs];
 };
 
-// Four balanced base-256 digits of v < 2^30 as fp16: v = sum_j (b_j - 128) 256^j where b_j are
-// the bytes of v + 0x80808080 (no wrap-around since v < 2^30). The half with bits 0x64bb is
-// exactly 1024 + bb, so one byte permute per pair of digits and one f16x2 subtraction of
-// 1152 give the digits exactly (every integer of magnitude <= 2048 is exact in fp16).
-__device__ __forceinline__ uint2 split_f16x4(uint32_t v) {
-    const uint32_t y = v + 0x80808080u;
-    const uint32_t lo = __byte_perm(y, 0x64u, 0x4140), hi = __byte_perm(y, 0x64u, 0x4342);
-    uint2 r;
-    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r.x) : "r"(lo), "r"(0x64806480u));
-    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r.y) : "r"(hi), "r"(0x64806480u));
-    return r;
-}
-
 // Epilogue of both GEMM kernels, run by one warp over all of the CTA's tiles: the warp reads
 // TMEM lanes [32 quarter, 32 quarter + 32) (= tile rows) of the accumulator buffer lt & 1 once
 // acc_full says its MMAs are complete, rebuilds each value mod q, then either multiplies by the
@@ -527,16 +514,6 @@ int make_src_map(CUtensorMap* m, const uint32_t* base, uint64_t inner, uint64_t 
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(FHE_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
     return FHE_OK;
-}
-
-uint16_t f16_bits_of_small_int(int e) {  // exact for |e| <= 2048
-    if (e == 0) return 0;
-    const uint16_t sign = e < 0 ? 0x8000 : 0;
-    const uint32_t a = (uint32_t)(e < 0 ? -e : e);
-    int ex = 0;
-    while ((a >> (ex + 1)) != 0) ++ex;  // 2^ex <= a < 2^(ex+1)
-    const uint32_t mant = (a << (10 - ex)) & 0x3FFu;
-    return (uint16_t)(sign | ((ex + 15) << 10) | mant);
 }
 
 // Balanced base-255 digits of w < 2^30: w = e0 + 255 e1 + 255^2 e2 + 255^3 e3, |e_i| <= 127.

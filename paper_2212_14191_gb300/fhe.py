@@ -18,6 +18,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "fhe.h")
 
 FHE_OK, FHE_EINVAL, FHE_ENOMEM, FHE_ECUDA, FHE_ETIMEOUT = 0, 1, 2, 3, 4
 FHE_NTT_DEFAULT, FHE_NTT_U32, FHE_NTT_TC = 0, 1, 2
+FHE_CONV_CUDA, FHE_CONV_TC = 0, 1
 FHE_OP_HMULT, FHE_OP_KEYSWITCH, FHE_OP_RESCALE, FHE_OP_HMULT_RELIN, FHE_OP_HROTATE = 1, 2, 3, 4, 5
 FHE_RESCALE_NOALLOC_MAX_BYTES = 32 << 20
 
@@ -63,6 +64,8 @@ _SIGS = {
     "fhe_ntt_variant_count": (_i, [_vp, _u32]),
     "fhe_ntt_get_variant": (_i, [_vp, _u32, _i]),
     "fhe_ntt_set_variant": (_i, [_vp, _u32, _i, _i]),
+    "fhe_conv_set_path": (_i, [_vp, _i]),
+    "fhe_conv_get_path": (_i, [_vp]),
     "fhe_autotune_ntt": (_i, [_vp, _u32, _vp, _i, _i, _i, ctypes.POINTER(ctypes.c_float), _vp]),
     "fhe_last_error": (_i, [ctypes.c_char_p, _sz]),
     "fhe_batch_create": (_i, [_vp, ctypes.POINTER(FheOp), _i, ctypes.POINTER(_vp)]),
@@ -190,6 +193,14 @@ def fhe_ntt_set_variant(ctx, logN, variant, inv_variant=None):
     """Select the forward variant and the inverse one (the same unless given)."""
     inv = variant if inv_variant is None else inv_variant
     return _check(_lib.fhe_ntt_set_variant(ctx, logN, variant, inv))
+
+
+def fhe_conv_set_path(ctx, path):
+    return _check(_lib.fhe_conv_set_path(ctx, path))
+
+
+def fhe_conv_get_path(ctx):
+    return int(_lib.fhe_conv_get_path(ctx))
 
 
 def fhe_autotune_ntt(ctx, logN, d_ptr, n_limbs, batch, reps=3, stream=0):

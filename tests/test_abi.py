@@ -48,10 +48,12 @@ def test_argument_validation_without_gpu(fhe):
     for call in (lambda: fhe.fhe_automorph(None, 12, 1, 5, 16, 32),
                  lambda: fhe.fhe_hrotate(None, 12, 2, 1, 5, 16, 16, 32, 16, 0),
                  lambda: fhe.fhe_cmult(None, 12, 2, 1, 16, 16, 16),
-                 lambda: fhe.fhe_hadd(None, 12, 2, 1, 16, 16, 16)):
+                 lambda: fhe.fhe_hadd(None, 12, 2, 1, 16, 16, 16),
+                 lambda: fhe.fhe_conv_set_path(None, fhe.FHE_CONV_TC)):
         with pytest.raises(fhe.FheError) as e:
             call()
         assert e.value.code == fhe.FHE_EINVAL and "ctx" in str(e.value)
+    assert fhe.fhe_conv_get_path(None) == -1
     # bad moduli are rejected before any device allocation
     composite = ((1 << 30) - 1) // (1 << 17) * (1 << 17) + 1   # above the largest such prime
     assert composite > P.ntt_primes(1)[0]

@@ -266,3 +266,34 @@ def test_hmult_fused_rescale_tail(fhe, fwd_variant):
     assert np.abs(dec - za * zb).max() / np.abs(za * zb).max() < 1e-5
     fhe.fhe_device_status(ctx.handle, 1)
     ctx.close()
+
+
+@pytest.mark.parametrize("logn,nl,K,alpha,batch", [(12, 6, 2, 2, 3), (11, 12, 5, 5, 2), (13, 9, 4, 3, 1)])
+def test_tensor_core_conv_matches_cuda_core(fhe, logn, nl, K, alpha, batch):
+    """Key switching and HMULT with the basis conversion on the tensor cores and on the CUDA
+    cores (the default): identical results (both are the exact sum of Sec. IV-A's Conv), and
+    the oracle on one ciphertext. Source counts 2..5, short last slices, ragged batches."""
+    import torch
+    n = 1 << logn
+    qs, ps = P.default_moduli(nl, K)
+    prm = C.Params(n, qs, ps, alpha=alpha)
+    s, evk = make_key(prm, 700 + logn)
+    A, B = batch_cts(prm, nl, batch, 710), batch_cts(prm, nl, batch, 711)
+    ctx = fhe.Context(logn, qs, ps, alpha=alpha)
+    assert fhe.fhe_conv_get_path(ctx.handle) == fhe.FHE_CONV_CUDA
+    da, db, de = fhe.to_device(A), fhe.to_device(B), fhe.to_device(evk.astype(np.uint32))
+    d2 = fhe.to_device(I.uniform_residues(712, qs[:nl], batch, n))
+    res = {}
+    for path in (fhe.FHE_CONV_TC, fhe.FHE_CONV_CUDA):
+        fhe.fhe_conv_set_path(ctx.handle, path)
+        res[path] = (ctx.hmult(da, db, de, logn).clone(), ctx.keyswitch(d2, de, logn).clone())
+    torch.cuda.synchronize()
+    for x, y in zip(res[fhe.FHE_CONV_TC], res[fhe.FHE_CONV_CUDA]):
+        assert torch.equal(x, y)
+    got = fhe.to_host(res[fhe.FHE_CONV_TC][0])
+    want = C.hmult(prm, nl, A[:, :, 0].astype(U64), B[:, :, 0].astype(U64), evk)
+    assert (got[:, :, 0] == want).all()
+    with pytest.raises(fhe.FheError):
+        fhe.fhe_conv_set_path(ctx.handle, 7)
+    fhe.fhe_device_status(ctx.handle, 1)
+    ctx.close()
