@@ -66,12 +66,15 @@ __device__ __forceinline__ void set(uint4& v, int k, uint32_t x) {
 }
 
 // ---- HM-1: tensor product (Hada-Mult + Ele-Add), d2 written twice (NTT form + copy for INTT)
+// dscale (nullable): limbs l < scale_lt write d0 and d1 multiplied by dscale[l] (Shoup pair).
 __global__ void k_tensor(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b,
                          uint32_t* __restrict__ d0, uint32_t* __restrict__ d1,
                          uint32_t* __restrict__ d2, uint32_t* __restrict__ d2c, size_t L4,
-                         size_t comp4, ModVec m) {
+                         size_t comp4, ModVec m, const uint2* __restrict__ dscale, int scale_lt) {
     const int l = blockIdx.y;
     const Red rd = red_of(m, l);
+    const bool scaled = dscale != nullptr && l < scale_lt;
+    const uint2 sc = scaled ? __ldg(&dscale[l]) : make_uint2(0, 0);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < L4; i += (size_t)gridDim.x * blockDim.x) {
         const size_t idx = (size_t)l * L4 + i;
         uint4 a0 = ld4(a, idx), a1 = ld4(a, comp4 + idx), b0 = ld4(b, idx), b1 = ld4(b, comp4 + idx);
@@ -79,8 +82,13 @@ __global__ void k_tensor(const uint32_t* __restrict__ a, const uint32_t* __restr
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             uint32_t x0 = get(a0, k), x1 = get(a1, k), y0 = get(b0, k), y1 = get(b1, k);
-            set(r0, k, reduce_red((uint64_t)x0 * y0, rd));
-            set(r1, k, reduce_red((uint64_t)x0 * y1 + (uint64_t)x1 * y0, rd));
+            uint32_t v0 = reduce_red((uint64_t)x0 * y0, rd), v1 = reduce_red((uint64_t)x0 * y1 + (uint64_t)x1 * y0, rd);
+            if (scaled) {
+                v0 = mul_shoup(v0, sc.x, sc.y, m.q[l]);
+                v1 = mul_shoup(v1, sc.x, sc.y, m.q[l]);
+            }
+            set(r0, k, v0);
+            set(r1, k, v1);
             set(r2, k, reduce_red((uint64_t)x1 * y1, rd));
         }
         st4(d0, idx, r0);
@@ -106,6 +114,11 @@ struct ConvArgs {
     uint8_t dst_mod[kMaxLimbs];
     ModVec dm;
     size_t L4;  // residues per limb / 4
+    // destinations t < scale_lt come out multiplied by s1[t] s2[t] (Shoup pairs mod q_t, folded
+    // into the constants [B/b_i]_t); 0 leaves every destination unscaled
+    const uint2* s1;
+    const uint2* s2;
+    int scale_lt;
 };
 
 // NS = number of source limbs (a compile-time constant so no issue slot is spent on
@@ -115,7 +128,13 @@ __global__ void __launch_bounds__(256) k_conv(const ConvArgs a) {
     extern __shared__ uint32_t s_hat[];  // [nsrc][ndst]
     for (int k = threadIdx.x; k < NS * a.ndst; k += blockDim.x) {
         int i = k / a.ndst, t = k % a.ndst;
-        s_hat[k] = a.hat_mod[(size_t)i * a.nmod + a.dst_mod[t]];
+        uint32_t h = a.hat_mod[(size_t)i * a.nmod + a.dst_mod[t]];
+        if (t < a.scale_lt) {
+            const uint32_t q = a.dm.q[t];
+            const uint2 u = a.s1[a.dst_mod[t]], v = a.s2[a.dst_mod[t]];
+            h = mul_shoup(mul_shoup(h, u.x, u.y, q), v.x, v.y, q);
+        }
+        s_hat[k] = h;
     }
     __syncthreads();
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < a.L4; n += (size_t)gridDim.x * blockDim.x) {
@@ -161,7 +180,7 @@ int launch_conv(const ConvArgs& ca, dim3 grid, size_t smem, cudaStream_t st) {
 
 // The context's basis-conversion kernel: tensor cores (conv_tc.cu) or the CUDA-core k_conv.
 int run_conv(const fhe_ctx* ctx, const ConvArgs& ca, const ConvTable& ct, dim3 grid, size_t smem, cudaStream_t st) {
-    if (ctx->conv_path == FHE_CONV_TC && ct.bdig && ca.ndst <= 64) {
+    if (ctx->conv_path == FHE_CONV_TC && ct.bdig && ca.ndst <= 64 && ca.scale_lt == 0) {
         TcConvArgs t;
         memset(&t, 0, sizeof(t));
         t.src = ca.src;
@@ -196,6 +215,9 @@ struct IpArgs {
     int nl, alpha, dnum, ext, nq, nmod;
     size_t L4, N4;        // residues per limb / 4, N / 4
     ModVec m;             // per extended limb t < ext
+    const uint2* s1;      // limbs t < scale_lt: outputs multiplied by s1[t] s2[t] (Shoup pairs)
+    const uint2* s2;
+    int scale_lt;
 };
 
 __global__ void k_inner_product(const IpArgs a) {
@@ -230,10 +252,21 @@ __global__ void k_inner_product(const IpArgs a) {
                 r1[k] += (uint64_t)get(x, k) * get(w1, k);
             }
         }
-        st4(k0, i, make_uint4(reduce_red(r0[0], rd), reduce_red(r0[1], rd), reduce_red(r0[2], rd),
-                              reduce_red(r0[3], rd)));
-        st4(k1, i, make_uint4(reduce_red(r1[0], rd), reduce_red(r1[1], rd), reduce_red(r1[2], rd),
-                              reduce_red(r1[3], rd)));
+        uint4 o0 = make_uint4(reduce_red(r0[0], rd), reduce_red(r0[1], rd), reduce_red(r0[2], rd),
+                              reduce_red(r0[3], rd));
+        uint4 o1 = make_uint4(reduce_red(r1[0], rd), reduce_red(r1[1], rd), reduce_red(r1[2], rd),
+                              reduce_red(r1[3], rd));
+        if (t < a.scale_lt) {
+            const uint32_t q = a.m.q[t];
+            const uint2 u = a.s1[t], v = a.s2[t];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                set(o0, k, mul_shoup(mul_shoup(get(o0, k), u.x, u.y, q), v.x, v.y, q));
+                set(o1, k, mul_shoup(mul_shoup(get(o1, k), u.x, u.y, q), v.x, v.y, q));
+            }
+        }
+        st4(k0, i, o0);
+        st4(k1, i, o1);
     }
 }
 
@@ -320,7 +353,10 @@ __global__ void k_rescale_final(const uint32_t* __restrict__ ct, const uint32_t*
 // + d_i the relinearised limb i (NTT domain) and x_i the centred last limb broadcast to q_i,
 // the output is (rel_i - x^_i) q_l^-1 = (ks_i P^-1 + d_i - NTT(y_i P^-1 + x_i)) q_l^-1 by the
 // linearity of the NTT mod q_i, so one forward NTT of z_i = y_i P^-1 + x_i replaces the NTTs
-// of y (ModDown) and of x (RESCALE).
+// of y (ModDown) and of x (RESCALE). The constant factors are applied where they cost no
+// extra pass: for i < l the tensor product writes d'_i = d_i q_l^-1, the inner product
+// ks'_i = ks_i P^-1 q_l^-1 and ModDown's Conv y'_i = y_i P^-1 q_l^-1, so with
+// z'_i = y'_i + x_i q_l^-1 the output is ks'_i + d'_i - NTT(z'_i), additions only.
 //
 // u = ks_l P^-1 + d_l, the last limb of both components without the y term (NTT domain).
 __global__ void k_relin_last(const uint32_t* __restrict__ d, const uint32_t* __restrict__ ks,
@@ -351,14 +387,14 @@ __global__ void k_last_fix(const uint32_t* __restrict__ y, uint32_t* __restrict_
     }
 }
 
-// z_i = y_i P^-1 + [last]_centred mod q_i (coefficient domain), i < l.
+// z'_i = y'_i + [last]_centred q_l^-1 mod q_i (coefficient domain), i < l.
 __global__ void k_rescale_prep(const uint32_t* __restrict__ last, const uint32_t* __restrict__ y,
-                               uint32_t* __restrict__ z, const uint2* __restrict__ pinv, uint32_t ql, int nl,
+                               uint32_t* __restrict__ z, const uint2* __restrict__ qlinv, uint32_t ql, int nl,
                                size_t L4, ModVec m) {
     const int nout = nl - 1;
     const int c = blockIdx.y / nout, i = blockIdx.y % nout;
     const uint32_t q = m.q[i];
-    const uint2 pi = __ldg(&pinv[i]);
+    const uint2 qi = __ldg(&qlinv[i]);
     const uint32_t* lp = last + (size_t)c * L4 * 4;
     const uint32_t* yp = y + ((size_t)c * nl + i) * L4 * 4;
     uint32_t* zp = z + ((size_t)c * nout + i) * L4 * 4;
@@ -371,21 +407,20 @@ __global__ void k_rescale_prep(const uint32_t* __restrict__ last, const uint32_t
             const uint32_t v = get(lv, k);
             const uint32_t vm = reduce32(v, red_of(m, i));
             const uint32_t x = csub(v > half ? (vm + q - ql_mod) : vm, q);  // (v - ql) mod q above half
-            set(r, k, csub(mul_shoup(get(yv, k), pi.x, pi.y, q) + x, q));
+            set(r, k, csub(get(yv, k) + mul_shoup(x, qi.x, qi.y, q), q));
         }
         st4(zp, n, r);
     }
 }
 
-// out_i = (ks_i P^-1 + d_i - z^_i) q_l^-1, i < l.
+// out_i = ks'_i + d'_i - z'^_i, i < l, where ks'_i = ks_i P^-1 q_l^-1 and d'_i = d_i q_l^-1 were
+// scaled when they were written and z'^ is the NTT of z'.
 __global__ void k_hmult_final(const uint32_t* __restrict__ d, const uint32_t* __restrict__ ks,
-                              const uint32_t* __restrict__ zh, uint32_t* __restrict__ out,
-                              const uint2* __restrict__ pinv, const uint2* __restrict__ qlinv, int nl, int ext,
+                              const uint32_t* __restrict__ zh, uint32_t* __restrict__ out, int nl, int ext,
                               size_t L4, ModVec m) {
     const int nout = nl - 1;
     const int c = blockIdx.y / nout, i = blockIdx.y % nout;
     const uint32_t q = m.q[i];
-    const uint2 pi = __ldg(&pinv[i]), qi = __ldg(&qlinv[i]);
     const size_t limb = L4 * 4;
     const uint32_t* dp = d + ((size_t)c * nl + i) * limb;
     const uint32_t* kp = ks + ((size_t)c * ext + i) * limb;
@@ -394,10 +429,7 @@ __global__ void k_hmult_final(const uint32_t* __restrict__ d, const uint32_t* __
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < L4; n += (size_t)gridDim.x * blockDim.x) {
         uint4 dv = ld4(dp, n), kv = ld4(kp, n), zv = ld4(zp, n), r;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint32_t rel = csub(mul_shoup(get(kv, k), pi.x, pi.y, q) + get(dv, k), q);
-            set(r, k, mul_shoup(rel + q - get(zv, k), qi.x, qi.y, q));
-        }
+        for (int k = 0; k < 4; ++k) set(r, k, csub(csub(get(kv, k) + get(dv, k), q) + q - get(zv, k), q));
         st4(op, n, r);
     }
 }
@@ -426,9 +458,11 @@ size_t ks_scratch_limbs(int nl, int K, int alpha) {
 
 // Key switching of d2 (NTT form) into `out` (2, nl, B, N); accumulate != 0 adds to out.
 // d2c (nl limbs of scratch) may already hold a copy of d2 when d2c_ready != 0.
+// scale_lt > 0 (the fused HMULT + RESCALE tail, out == nullptr): q limbs t < scale_lt of ks and
+// of y come out multiplied by P^-1 q_{nl-1}^-1, the factors the tail would otherwise apply.
 int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint32_t* d2,
                    const uint32_t* evk, uint32_t* out, int accumulate, uint32_t* scratch,
-                   bool d2c_ready, cudaStream_t st, NttScratch ns) {
+                   bool d2c_ready, cudaStream_t st, NttScratch ns, int scale_lt = 0) {
     const size_t N = 1ull << logN, limb = N * batch, L4 = limb / 4;
     const int K = ctx->np, ext = nl + K, alpha = ctx->alpha, nq = ctx->nq;
     const int nmod = (int)ctx->mods.size();
@@ -450,6 +484,8 @@ int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const u
         const ConvTable& ct = ctx->modup[j][hi - lo - 1];
         // KS-2: Conv Q_j -> (Q_l \ Q_j) u P
         ConvArgs ca;
+        ca.s1 = ca.s2 = nullptr;
+        ca.scale_lt = 0;
         ca.src = d2c + (size_t)lo * limb;
         ca.src_stride = limb;
         ca.nsrc = hi - lo;
@@ -498,6 +534,9 @@ int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const u
         ia.L4 = L4;
         ia.N4 = N / 4;
         ia.m = ext_m;
+        ia.s1 = ctx->p_inv;
+        ia.s2 = scale_lt > 0 ? ctx->ql_inv + (size_t)(nl - 1) * nq : nullptr;
+        ia.scale_lt = scale_lt;
         k_inner_product<<<stream_grid(ctx, L4, ext), 256, 0, st>>>(ia);
         FHE_CUDA_TRY(cudaGetLastError());
     }
@@ -508,6 +547,9 @@ int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const u
             return rc;
     for (int c = 0; c < 2; ++c) {
         ConvArgs ca;
+        ca.s1 = ctx->p_inv;
+        ca.s2 = scale_lt > 0 ? ctx->ql_inv + (size_t)(nl - 1) * nq : nullptr;
+        ca.scale_lt = scale_lt;
         ca.src = ks + ((size_t)c * ext + nl) * limb;
         ca.src_stride = limb;
         ca.nsrc = K;
@@ -599,7 +641,7 @@ int hmult_relin_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const
     int qidx[kMaxLimbs];
     for (int i = 0; i < nl; ++i) qidx[i] = i;
     k_tensor<<<stream_grid(ctx, L4, nl), 256, 0, st>>>(a, b, out, out + (size_t)nl * limb, d2, ks_scratch, L4,
-                                                     (size_t)nl * L4, modvec(ctx, qidx, nl));
+                                                     (size_t)nl * L4, modvec(ctx, qidx, nl), nullptr, 0);
     FHE_CUDA_TRY(cudaGetLastError());
     return keyswitch_impl(ctx, logN, nl, batch, d2, evk, out, 1, ks_scratch, true, st, ns);
 }
@@ -623,10 +665,14 @@ int hmult_fused(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint
     uint32_t* xb = last + 2 * limb;
     int qidx[kMaxLimbs];
     for (int i = 0; i < nl; ++i) qidx[i] = i;
+    // the limbs i < l of d0, d1, ks and y carry the tail's factors from the start: q_l^-1 on d,
+    // P^-1 q_l^-1 on ks and y (folded into HBM-bound passes and into Conv's constants), so that
+    // the combine below needs no multiplication
+    const uint2* qlinv = ctx->ql_inv + (size_t)(nl - 1) * ctx->nq;
     k_tensor<<<stream_grid(ctx, L4, nl), 256, 0, st>>>(a, b, dd, dd + (size_t)nl * limb, d2, ksx, L4,
-                                                     (size_t)nl * L4, modvec(ctx, qidx, nl));
+                                                     (size_t)nl * L4, modvec(ctx, qidx, nl), qlinv, nl - 1);
     FHE_CUDA_TRY(cudaGetLastError());
-    int rc = keyswitch_impl(ctx, logN, nl, batch, d2, evk, nullptr, 0, ksx, true, st, ns);
+    int rc = keyswitch_impl(ctx, logN, nl, batch, d2, evk, nullptr, 0, ksx, true, st, ns, nl - 1);
     if (rc) return rc;
     const uint32_t ql = ctx->mods[nl - 1];
     const uint2 pinv_l = ctx->p_inv_h[nl - 1];
@@ -654,8 +700,7 @@ int hmult_fused(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint
         tl.ks = ks;
         tl.d = dd;
         tl.out = out;
-        tl.pinv = ctx->p_inv;
-        tl.qlinv = ctx->ql_inv + (size_t)(nl - 1) * ctx->nq;
+        tl.qlinv = qlinv;
         tl.ql = ql;
         tl.nl = nl;
         tl.nout = nout;
@@ -663,12 +708,10 @@ int hmult_fused(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint
         return ntt_u32_l2_tail(ctx, logN, 2 * nout * batch, batch, qm2, st, ns, tl);
     }
     ModVec qm = modvec(ctx, qidx, nout);
-    k_rescale_prep<<<stream_grid(ctx, L4, 2 * nout), 256, 0, st>>>(last, y, xb, ctx->p_inv, ql, nl, L4, qm);
+    k_rescale_prep<<<stream_grid(ctx, L4, 2 * nout), 256, 0, st>>>(last, y, xb, qlinv, ql, nl, L4, qm);
     FHE_CUDA_TRY(cudaGetLastError());
     if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, false, xb, 2 * nout, batch, qm2, st, ns))) return rc;
-    k_hmult_final<<<stream_grid(ctx, L4, 2 * nout), 256, 0, st>>>(dd, ks, xb, out, ctx->p_inv,
-                                                                ctx->ql_inv + (size_t)(nl - 1) * ctx->nq, nl, ext,
-                                                                L4, qm);
+    k_hmult_final<<<stream_grid(ctx, L4, 2 * nout), 256, 0, st>>>(dd, ks, xb, out, nl, ext, L4, qm);
     FHE_CUDA_TRY(cudaGetLastError());
     return FHE_OK;
 }

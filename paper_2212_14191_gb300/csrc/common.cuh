@@ -165,17 +165,18 @@ int ntt_u32_l2(const fhe_ctx* ctx, uint32_t logN, int shape, bool inverse, uint3
 
 // The HMULT + RESCALE tail (ckks.cu) fused into the forward two-pass NTT of z. Row r of the
 // transform is limb (c, i) = (r / batch / nout, r / batch % nout) of polynomial p = r % batch.
-// The local pass loads z = y_i P^-1 + [last]_q_i (last taken centred in (-q_l/2, q_l/2]) instead
-// of a stored z, and the cross pass stores out_i = (ks_i P^-1 + d_i - z^_i) q_l^-1 instead of z^:
-// the two HBM passes that would build z and combine z^ disappear.
+// The local pass loads z'_i = y'_i + [last]_q_i q_l^-1 (last taken centred in (-q_l/2, q_l/2])
+// instead of a stored z', and the cross pass stores out_i = ks'_i + d'_i - z'^_i instead of
+// z'^: the two HBM passes that would build z' and combine z'^ disappear. y', ks', d' are the
+// ModDown conversion, key-switching output and tensor product already multiplied by
+// P^-1 q_l^-1, P^-1 q_l^-1 and q_l^-1 (limbs i < l).
 struct HmultTail {
-    const uint32_t* y;     // (2, nl, batch, N): ModDown's basis conversion, coefficient domain
+    const uint32_t* y;     // (2, nl, batch, N): y', coefficient domain
     const uint32_t* last;  // (2, batch, N): the relinearised last limb, coefficient domain, [0, q_l)
-    const uint32_t* ks;    // (2, ext, batch, N): key-switching output, NTT domain
-    const uint32_t* d;     // (2, nl, batch, N): d0, d1 of the tensor product, NTT domain
+    const uint32_t* ks;    // (2, ext, batch, N): ks', NTT domain
+    const uint32_t* d;     // (2, nl, batch, N): d0', d1', NTT domain
     uint32_t* out;         // (2, nout, batch, N)
-    const uint2* pinv;     // [i] P^-1 mod q_i (value, Shoup quotient)
-    const uint2* qlinv;    // [i] q_l^-1 mod q_i
+    const uint2* qlinv;    // [i] q_l^-1 mod q_i (value, Shoup quotient)
     uint32_t ql;
     int nl, nout, ext;
 };

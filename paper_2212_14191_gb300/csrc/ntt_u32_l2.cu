@@ -239,17 +239,14 @@ __device__ __forceinline__ void dit_cross_row(const L2Args& a, int i, int p0, in
     uint32_t q;
     int mod;
     uint32_t* row = l2_row<N>(a, a.r0 + i, &q, &mod);
-    // TAIL: out = (ks P^-1 + d - z^) q_l^-1 is stored instead of z^
+    // TAIL: out = ks' + d' - z'^ is stored instead of z'^
     const uint32_t* ksr = nullptr;
     const uint32_t* dr = nullptr;
-    uint2 pinv = make_uint2(0, 0), qlinv = make_uint2(0, 0);
     if constexpr (TAIL) {
         const TailRow t = tail_row(a, a.r0 + i);
         ksr = a.tail.ks + (((size_t)t.c * a.tail.ext + t.i) * a.batch + t.p) * N;
         dr = a.tail.d + (((size_t)t.c * a.tail.nl + t.i) * a.batch + t.p) * N;
         row = a.tail.out + (((size_t)t.c * a.tail.nout + t.i) * a.batch + t.p) * N;
-        pinv = __ldg(&a.tail.pinv[t.i]);
-        qlinv = __ldg(&a.tail.qlinv[t.i]);
     }
     const uint32_t* tmp = a.temp + (size_t)i * N;
     const uint2* twist = a.twist + (size_t)mod * (C - 1) * NC;
@@ -333,14 +330,10 @@ __device__ __forceinline__ void dit_cross_row(const L2Args& a, int i, int p0, in
                     dt = __ldcs(reinterpret_cast<const uint4*>(dr + t * NC) + p4);
                 }
                 uint4 r;
-                r.x = mul_shoup(csub(mul_shoup(kt.x, pinv.x, pinv.y, q) + dt.x, q) + q - o[t].x, qlinv.x,
-                                qlinv.y, q);
-                r.y = mul_shoup(csub(mul_shoup(kt.y, pinv.x, pinv.y, q) + dt.y, q) + q - o[t].y, qlinv.x,
-                                qlinv.y, q);
-                r.z = mul_shoup(csub(mul_shoup(kt.z, pinv.x, pinv.y, q) + dt.z, q) + q - o[t].z, qlinv.x,
-                                qlinv.y, q);
-                r.w = mul_shoup(csub(mul_shoup(kt.w, pinv.x, pinv.y, q) + dt.w, q) + q - o[t].w, qlinv.x,
-                                qlinv.y, q);
+                r.x = csub(csub(kt.x + dt.x, q) + q - o[t].x, q);
+                r.y = csub(csub(kt.y + dt.y, q) + q - o[t].y, q);
+                r.z = csub(csub(kt.z + dt.z, q) + q - o[t].z, q);
+                r.w = csub(csub(kt.w + dt.w, q) + q - o[t].w, q);
                 __stcs(reinterpret_cast<uint4*>(row + t * NC) + p4, r);
             }
         } else {
@@ -369,11 +362,11 @@ __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_dit_local_kernel
     const uint2* tw = a.tw_sub + (size_t)mod * NC;
     uint32_t v[32];
     if constexpr (TAIL) {
-        // z = y P^-1 + [last]_q (last centred: values above (q_l - 1) / 2 stand for last - q_l)
+        // z' = y' + [last]_q q_l^-1 (last centred: values above (q_l - 1) / 2 stand for last - q_l)
         const TailRow t = tail_row(a, a.r0 + i);
         const uint32_t* yr = a.tail.y + (((size_t)t.c * a.tail.nl + t.i) * a.batch + t.p) * N;
         const uint32_t* lr = a.tail.last + ((size_t)t.c * a.batch + t.p) * N;
-        const uint2 pinv = __ldg(&a.tail.pinv[t.i]);
+        const uint2 qlinv = __ldg(&a.tail.qlinv[t.i]);
         const uint32_t ql = a.tail.ql, half = (ql - 1) / 2, qlm = ql % q;
         const bool one_sub = ql <= 2 * (uint64_t)q;  // last < q_l <= 2q: one subtraction reduces it
 #pragma unroll
@@ -382,7 +375,7 @@ __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_dit_local_kernel
             const uint32_t lv = __ldcs(&lr[idx]), yv = __ldcs(&yr[idx]);
             const uint32_t vm = one_sub ? csub(lv, q) : lv % q;
             const uint32_t x = csub(lv > half ? vm + q - qlm : vm, q);
-            v[e] = csub(mul_shoup(yv, pinv.x, pinv.y, q) + x, q);
+            v[e] = csub(yv + mul_shoup(x, qlinv.x, qlinv.y, q), q);
         }
     } else {
 #pragma unroll
