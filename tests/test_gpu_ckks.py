@@ -233,6 +233,30 @@ def test_concurrent_streams_share_a_context(fhe):
     ctx.close()
 
 
+def test_hmult_fused_rescale_tail_wide_shapes(fhe):
+    """N = 2^16: the fused tail in the default two-pass shape (512-thread CTAs, C = 4) and in the
+    256-thread shape with C = 8 sub-transforms per row (whose cross pass loads ks and d at the
+    store), both against the tail run as separate passes."""
+    import torch
+    logn, nl, K, batch = 16, 3, 2, 2
+    n = 1 << logn
+    qs, ps = P.default_moduli(nl, K)
+    prm = C.Params(n, qs, ps, alpha=2)
+    s, evk = make_key(prm, 650)
+    A, B = batch_cts(prm, nl, batch, 651), batch_cts(prm, nl, batch, 652)
+    ctx = fhe.Context(logn, qs, ps, alpha=2)
+    da, db, de = fhe.to_device(A), fhe.to_device(B), fhe.to_device(evk.astype(np.uint32))
+    fhe.fhe_ntt_set_variant(ctx.handle, logn, 0, 6)             # cluster forward: separate passes
+    sep = ctx.hmult(da, db, de, logn).clone()
+    for fwd in (6, 7):
+        fhe.fhe_ntt_set_variant(ctx.handle, logn, fwd, 6)
+        fused = ctx.hmult(da, db, de, logn).clone()
+        torch.cuda.synchronize()
+        assert torch.equal(fused, sep), fwd
+    fhe.fhe_device_status(ctx.handle, 1)
+    ctx.close()
+
+
 @pytest.mark.parametrize("fwd_variant", [7, 6])
 def test_hmult_fused_rescale_tail(fhe, fwd_variant):
     """The RESCALE tail fused into the two-pass forward NTT (z built on load, the output combined
