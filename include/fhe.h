@@ -302,6 +302,16 @@ int fhe_rescale_noalloc(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batc
 int fhe_device_status(const fhe_ctx* ctx, int clear);
 
 /*
+ * fhe_selftest_wait_timeout -- checks the failure path of fhe_device_status without faulting
+ * the GPU: launches on `stream` one kernel whose mbarrier wait can never complete (nothing
+ * arrives) and which gives up after limit_cycles SM clock cycles (0 < limit_cycles <= 4e9,
+ * about two seconds at the maximum clock), recording FHE_ETIMEOUT in the context's device
+ * error word exactly as the library's kernels do when one of their bounded waits expires.
+ * The context stays usable; fhe_device_status(ctx, 1) then reports and clears the word.
+ */
+int fhe_selftest_wait_timeout(const fhe_ctx* ctx, long long limit_cycles, void* stream);
+
+/*
  * fhe_last_error -- copy the calling thread's last error message (NUL-terminated, truncated
  * to n bytes) into buf; returns the status code of that failure (FHE_OK if none).
  */

@@ -65,6 +65,7 @@ _SIGS = {
     "fhe_ntt_get_variant": (_i, [_vp, _u32, _i]),
     "fhe_ntt_set_variant": (_i, [_vp, _u32, _i, _i]),
     "fhe_conv_set_path": (_i, [_vp, _i]),
+    "fhe_selftest_wait_timeout": (_i, [_vp, ctypes.c_longlong, _vp]),
     "fhe_conv_get_path": (_i, [_vp]),
     "fhe_autotune_ntt": (_i, [_vp, _u32, _vp, _i, _i, _i, ctypes.POINTER(ctypes.c_float), _vp]),
     "fhe_last_error": (_i, [ctypes.c_char_p, _sz]),
@@ -201,6 +202,10 @@ def fhe_conv_set_path(ctx, path):
 
 def fhe_conv_get_path(ctx):
     return int(_lib.fhe_conv_get_path(ctx))
+
+
+def fhe_selftest_wait_timeout(ctx, limit_cycles, stream=0):
+    return _check(_lib.fhe_selftest_wait_timeout(ctx, limit_cycles, stream))
 
 
 def fhe_autotune_ntt(ctx, logN, d_ptr, n_limbs, batch, reps=3, stream=0):

@@ -49,7 +49,8 @@ def test_argument_validation_without_gpu(fhe):
                  lambda: fhe.fhe_hrotate(None, 12, 2, 1, 5, 16, 16, 32, 16, 0),
                  lambda: fhe.fhe_cmult(None, 12, 2, 1, 16, 16, 16),
                  lambda: fhe.fhe_hadd(None, 12, 2, 1, 16, 16, 16),
-                 lambda: fhe.fhe_conv_set_path(None, fhe.FHE_CONV_TC)):
+                 lambda: fhe.fhe_conv_set_path(None, fhe.FHE_CONV_TC),
+                 lambda: fhe.fhe_selftest_wait_timeout(None, 1000)):
         with pytest.raises(fhe.FheError) as e:
             call()
         assert e.value.code == fhe.FHE_EINVAL and "ctx" in str(e.value)

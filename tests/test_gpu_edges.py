@@ -105,3 +105,30 @@ def test_minimum_limb_counts(fhe):
     assert (fhe.to_host(rot)[:, :, 0] == C.hrotate(prm, 1, ct1[:, :, 0].astype(U64), evk, 5)).all()
     fhe.fhe_device_status(ctx.handle, 1)
     ctx.close()
+
+
+def test_expired_device_wait_is_reported_and_the_context_survives(fhe):
+    """The failure path of the bounded device waits, without a fault: a kernel whose mbarrier
+    wait can never complete gives up after its cycle limit and records FHE_ETIMEOUT; the host
+    reads it through fhe_device_status (which clears it), and the same context then transforms
+    correctly."""
+    import torch
+    qs, ps = P.default_moduli(2, 2)
+    ctx = fhe.Context(12, qs, ps, alpha=1)
+    fhe.fhe_device_status(ctx.handle, 1)
+    fhe.fhe_selftest_wait_timeout(ctx.handle, 20_000_000)     # ~10 ms at the SM clock
+    torch.cuda.synchronize()
+    with pytest.raises(fhe.FheError) as e:
+        fhe.fhe_device_status(ctx.handle, 1)
+    assert e.value.code == fhe.FHE_ETIMEOUT
+    fhe.fhe_device_status(ctx.handle, 0)                       # cleared by the read above
+    with pytest.raises(fhe.FheError):
+        fhe.fhe_selftest_wait_timeout(ctx.handle, 0)
+    x = I.uniform_residues(21, qs, 3, 1 << 12)
+    d = fhe.to_device(x)
+    ctx.ntt_fwd(d, 12)
+    ctx.ntt_inv(d, 12)
+    torch.cuda.synchronize()
+    assert (fhe.to_host(d) == x).all()
+    fhe.fhe_device_status(ctx.handle, 1)
+    ctx.close()
