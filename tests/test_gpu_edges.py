@@ -132,3 +132,30 @@ def test_expired_device_wait_is_reported_and_the_context_survives(fhe):
     assert (fhe.to_host(d) == x).all()
     fhe.fhe_device_status(ctx.handle, 1)
     ctx.close()
+
+
+def test_hmult_at_the_largest_limb_count(fhe):
+    """HMULT with 44 ciphertext limbs and 8 special primes (alpha = 8, dnum = 6): ModUp converts
+    into 44 destination limbs, the largest count, on the CUDA cores and on the tensor cores
+    (whose accumulators then take 176 of 256 TMEM columns); both equal the oracle."""
+    import torch
+    logn, nl, K, batch = 12, 44, 8, 1
+    n = 1 << logn
+    qs, ps = P.default_moduli(nl, K)
+    prm = C.Params(n, qs, ps, alpha=8)
+    s = I.ternary_secret(800, n, hamming_weight=64)
+    arand = I.uniform_residues(801, prm.qs + prm.ps, prm.dnum(nl), n, dtype=np.uint64).transpose(1, 0, 2)
+    evk = C.keygen_evk(prm, s, arand, I.gaussian_error(802, (prm.dnum(nl), n)))
+    x = I.uniform_residues(803, qs, 4 * batch, n)
+    A = x.reshape(nl, 2, 2, batch, n)[:, 0].transpose(1, 0, 2, 3).copy()
+    B = x.reshape(nl, 2, 2, batch, n)[:, 1].transpose(1, 0, 2, 3).copy()
+    want = C.hmult(prm, nl, A[:, :, 0].astype(U64), B[:, :, 0].astype(U64), evk)
+    ctx = fhe.Context(logn, qs, ps, alpha=8)
+    da, db, de = fhe.to_device(A), fhe.to_device(B), fhe.to_device(evk.astype(np.uint32))
+    for path in (fhe.FHE_CONV_CUDA, fhe.FHE_CONV_TC):
+        fhe.fhe_conv_set_path(ctx.handle, path)
+        out = ctx.hmult(da, db, de, logn)
+        torch.cuda.synchronize()
+        assert (fhe.to_host(out)[:, :, 0] == want).all(), path
+    fhe.fhe_device_status(ctx.handle, 1)
+    ctx.close()
