@@ -264,10 +264,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 // the A operand is built on chip from the caller's u32 residues, so their digit planes never
 // reach HBM. Three shared-memory rings, each sized for the latency it has to cover:
 //   B   (4 x 4 NT rows x 128 B): warp 0 loads the constant-matrix planes by TMA;
-//   raw (per converter warp, 3 x 2 KB): each converter warp TMA-loads the 16 reduction indices
+//   raw (per converter warp, 2 x 2 KB): each converter warp TMA-loads the 16 reduction indices
 //       x 32 rows of its quarter of the A tile, and refills a slot as soon as it has read it,
 //       so the raw loads run ahead of the conversion;
-//   A   (3 x 16 KB): the converter warps (6-13, two groups of four taking alternate stages)
+//   A   (4 x 16 KB): the converter warps (6-13, two groups of four taking alternate stages)
 //       split the residues into fp16 digits and store them in the 128-byte swizzled K-major
 //       layout of the MMA descriptors; each stage ends with a proxy fence, whose latency the
 //       other group's stage overlaps.
@@ -276,7 +276,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 template <int NT>
 struct FusedCfg {
     static constexpr int kGroups = 2;                  // converter warp groups (alternate stages)
-    static constexpr int kSA = 3, kSB = 4, kSR = 3;    // kSR: source slots per converter warp
+    static constexpr int kSA = 4, kSB = 4, kSR = 2;    // kSR: source slots per converter warp
     static constexpr int kABytes = kTileM * 128;
     static constexpr int kBBytes = 4 * NT * 128;
     static constexpr int kRawBytes = 32 * (kChunk / 4) * 4;  // one converter warp's 32 rows
