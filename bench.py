@@ -33,7 +33,7 @@ METRIC = "NTT KOPS and HMULT KOPS at N=2^16 (INT8-TC vs plain CUDA), % INT8/HBM 
 LOGN, N = 16, 1 << 16
 NTT_LIMBS, NTT_BATCH = 44, 64
 HM_LIMBS, HM_K, HM_ALPHA, HM_BATCH = 24, 8, 8, 128
-E2E_LIMBS = 4  # limbs per chunk of the pipelined end-to-end step
+E2E_LIMBS = 11  # limbs per chunk of the pipelined end-to-end step
 
 
 def parse():
@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-heax", action="store_true", help="skip the HEAX comparison parameter sets")
     ap.add_argument("--serving-requests", type=int, default=2000)
     ap.add_argument("--batch-ops", type=int, default=1000)
+    ap.add_argument("--e2e-limbs", type=int, default=E2E_LIMBS, help="limbs per chunk of the end-to-end pipeline")
     return ap.parse_args()
 
 
@@ -333,34 +334,43 @@ def ours(args):
     total_head = ops_per_step * args.steps * ws / (results[head]["kops"] * 1e3)
     # end to end through the C ABI with host buffers: every step copies the 44 x 64 batch in
     # from pinned host memory, transforms it forward and back, and copies it out. The batch
-    # moves in chunks of E2E_LIMBS limbs on three streams (H2D, compute, D2H) so that the two
+    # moves in chunks of --e2e-limbs limbs on three streams (H2D, compute, D2H) so that the two
     # copy directions and the kernels overlap; every step still moves all of its bytes.
     pinned_in = torch.from_numpy(x_host.view(np.int32)).pin_memory()
     pinned_out = torch.empty_like(pinned_in).pin_memory()
     e2e_steps = max(2, args.steps // 2)
     s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
-    chunks = [(l0, min(NTT_LIMBS, l0 + E2E_LIMBS)) for l0 in range(0, NTT_LIMBS, E2E_LIMBS)]
+    el = max(1, args.e2e_limbs)
+    chunks = [(l0, min(NTT_LIMBS, l0 + el)) for l0 in range(0, NTT_LIMBS, el)]
+    # two device buffers, alternate steps: a chunk's copy-in waits for the copy-out of the
+    # same chunk two steps back, not the previous step's
+    xbufs = [x, torch.empty_like(x)]
     ev_in = [torch.cuda.Event() for _ in chunks]
     ev_cmp = [torch.cuda.Event() for _ in chunks]
-    ev_out = [torch.cuda.Event() for _ in chunks]
+    ev_out = [[torch.cuda.Event() for _ in chunks] for _ in xbufs]
     barrier()
-    for e in ev_out:
-        e.record(s_out)
+    for evs in ev_out:
+        for e in evs:
+            e.record(s_out)
+    e2e_count = [0]
 
     def e2e_step(path):
+        b = e2e_count[0] & 1
+        e2e_count[0] += 1
+        xb = xbufs[b]
         for c, (l0, l1) in enumerate(chunks):
-            s_in.wait_event(ev_out[c])          # the previous step's copy-out of this chunk is done
+            s_in.wait_event(ev_out[b][c])       # this buffer's copy-out of the chunk is done
             with torch.cuda.stream(s_in):
-                x[l0:l1].copy_(pinned_in[l0:l1], non_blocking=True)
+                xb[l0:l1].copy_(pinned_in[l0:l1], non_blocking=True)
             ev_in[c].record(s_in)
             s_cmp.wait_event(ev_in[c])
-            fhe.fhe_ntt_fwd(ctx.handle, path, LOGN, x[l0:l1].data_ptr(), l0, l1 - l0, NTT_BATCH, s_cmp.cuda_stream)
-            fhe.fhe_ntt_inv(ctx.handle, path, LOGN, x[l0:l1].data_ptr(), l0, l1 - l0, NTT_BATCH, s_cmp.cuda_stream)
+            fhe.fhe_ntt_fwd(ctx.handle, path, LOGN, xb[l0:l1].data_ptr(), l0, l1 - l0, NTT_BATCH, s_cmp.cuda_stream)
+            fhe.fhe_ntt_inv(ctx.handle, path, LOGN, xb[l0:l1].data_ptr(), l0, l1 - l0, NTT_BATCH, s_cmp.cuda_stream)
             ev_cmp[c].record(s_cmp)
             s_out.wait_event(ev_cmp[c])
             with torch.cuda.stream(s_out):
-                pinned_out[l0:l1].copy_(x[l0:l1], non_blocking=True)
-            ev_out[c].record(s_out)
+                pinned_out[l0:l1].copy_(xb[l0:l1], non_blocking=True)
+            ev_out[b][c].record(s_out)
 
     for _ in range(2):
         e2e_step(paths[head])
