@@ -260,3 +260,24 @@ def test_rescale_two_pass_small_chunks(fhe, logn):
     for b in (0, batch - 1):
         assert (got[:, :, b] == C.rescale(prm, ct[:, :, b].astype(np.uint64))).all(), b
     c.close()
+
+
+def test_tensor_core_polynomial_chunks(fhe, ctx):
+    """N = 2^16 on the tensor-core path with more polynomials than one plane buffer holds (512):
+    each limb runs as chunks of 512 and 88 polynomials, whose source rows skip the other chunk's
+    polynomials and whose last row tiles run past the chunk. Rows on both sides of the split
+    against the oracle; the round trip in full."""
+    import torch
+    logn, n, first, nl, batch = 16, 1 << 16, 5, 2, 600
+    mods = MODS[first:first + nl]
+    x = I.uniform_residues(17, mods, batch, n)
+    d = fhe.to_device(x)
+    ctx.ntt_fwd(d, logn, first_limb=first, path=fhe.FHE_NTT_TC)
+    torch.cuda.synchronize()
+    got = fhe.to_host(d)
+    for l in range(nl):
+        for b in (0, 1, 510, 511, 512, 513, 598, 599):
+            assert (got[l, b] == ON.ntt(x[l, b], mods[l], P.psi(mods[l], n))).all(), (l, b)
+    ctx.ntt_inv(d, logn, first_limb=first, path=fhe.FHE_NTT_TC)
+    assert torch.equal(d, fhe.to_device(x))
+    fhe.fhe_device_status(ctx.handle, 1)
