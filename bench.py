@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--serving-requests", type=int, default=2000)
     ap.add_argument("--batch-ops", type=int, default=1000)
     ap.add_argument("--e2e-limbs", type=int, default=E2E_LIMBS, help="limbs per chunk of the end-to-end pipeline")
+    ap.add_argument("--hmult-batch", type=int, default=HM_BATCH,
+                    help="ciphertext pairs per HMULT call (and ciphertexts per HROTATE / CMULT / HADD call)")
     return ap.parse_args()
 
 
@@ -393,15 +395,16 @@ def ours(args):
     # HMULT (N = 2^16, 24 + 8 limbs, dnum = 3, 128 pairs): uniform ciphertexts and key
     hm = ops = None
     if not args.no_hmult:
-        a = fhe.to_device(I.uniform_residues(11, qs[:HM_LIMBS], 2 * HM_BATCH, N))
-        b = fhe.to_device(I.uniform_residues(12, qs[:HM_LIMBS], 2 * HM_BATCH, N))
-        a = a.view(HM_LIMBS, 2, HM_BATCH, N).permute(1, 0, 2, 3).contiguous()
-        b = b.view(HM_LIMBS, 2, HM_BATCH, N).permute(1, 0, 2, 3).contiguous()
+        hb = args.hmult_batch
+        a = fhe.to_device(I.uniform_residues(11, qs[:HM_LIMBS], 2 * hb, N))
+        b = fhe.to_device(I.uniform_residues(12, qs[:HM_LIMBS], 2 * hb, N))
+        a = a.view(HM_LIMBS, 2, hb, N).permute(1, 0, 2, 3).contiguous()
+        b = b.view(HM_LIMBS, 2, hb, N).permute(1, 0, 2, 3).contiguous()
         dnum = -(-HM_LIMBS // HM_ALPHA)
         evk = fhe.to_device(I.uniform_residues(13, qs[:HM_LIMBS] + ps, 2 * dnum, N)).view(
             HM_LIMBS + HM_K, dnum, 2, N).permute(1, 2, 0, 3).contiguous()
-        out = torch.empty((2, HM_LIMBS - 1, HM_BATCH, N), dtype=torch.int32, device="cuda")
-        hm = {"config": "N=2^16, 24 ciphertext limbs + 8 special primes, dnum=3, 128 pairs per call, "
+        out = torch.empty((2, HM_LIMBS - 1, hb, N), dtype=torch.int32, device="cuda")
+        hm = {"config": "N=2^16, 24 ciphertext limbs + 8 special primes, dnum=3, %d pairs per call, " % hb +
                         "HMULT + relinearisation + rescale"}
         for name, path in (("u32", fhe.FHE_NTT_U32), ("tc", fhe.FHE_NTT_TC)):
             hctx = fhe.Context(16, qs[:HM_LIMBS], ps, alpha=HM_ALPHA, default_path=path)
@@ -423,8 +426,8 @@ def ours(args):
             ht = max_over_ranks(h0.elapsed_time(h1) / 1e3)
             # fully fused HBM floor per op: both input ciphertexts, the output, evk / batch
             dnum_h = -(-HM_LIMBS // HM_ALPHA)
-            op_bytes = (16 * HM_LIMBS + 8 * (HM_LIMBS - 1)) * N + dnum_h * 2 * (HM_LIMBS + HM_K) * N * 4 / HM_BATCH
-            kops = HM_BATCH * args.hmult_steps * ws / ht / 1e3
+            op_bytes = (16 * HM_LIMBS + 8 * (HM_LIMBS - 1)) * N + dnum_h * 2 * (HM_LIMBS + HM_K) * N * 4 / hb
+            kops = hb * args.hmult_steps * ws / ht / 1e3
             ceil_kops = measured_peaks()[0]["hbm_gbs"] * 1e9 / op_bytes / 1e3
             hm[name] = {"kops": kops, "ms_per_call": ht / args.hmult_steps * 1e3,
                         "hbm_floor_bytes_per_op": op_bytes, "hbm_ceiling_kops": ceil_kops,
@@ -523,11 +526,12 @@ def other_ops(args, fhe, hctx, a, b, evk, st, barrier, max_over_ranks, ws):
     HBM bandwidth."""
     import torch
     peaks, _ = measured_peaks()
-    res = {"config": "N=2^16, 24 ciphertext limbs (+ 8 special primes for HROTATE), 128 ciphertexts per call"}
+    res = {"config": "N=2^16, 24 ciphertext limbs (+ 8 special primes for HROTATE), %d ciphertexts per call"
+                     % args.hmult_batch}
     galois = 5                                   # 5^1 mod 2N: rotation of the slots by one
     pt = b[0]                                    # any (24, 128, N) residues serve as a plaintext
     out = torch.empty_like(a)
-    limb_bytes = N * HM_BATCH * 4
+    limb_bytes = N * args.hmult_batch * 4
     cases = (("hrotate", lambda: hctx.hrotate(a, evk, LOGN, galois, out=out), None, args.hmult_steps),
              ("cmult", lambda: hctx.cmult(a, pt, LOGN, out=out), 5 * HM_LIMBS * limb_bytes, 10),
              ("hadd", lambda: hctx.hadd(a, b, LOGN, out=out), 6 * HM_LIMBS * limb_bytes, 10))
@@ -543,7 +547,7 @@ def other_ops(args, fhe, hctx, a, b, evk, st, barrier, max_over_ranks, ws):
         torch.cuda.nvtx.range_pop()
         barrier()
         t = max_over_ranks(e0.elapsed_time(e1) / 1e3) / reps
-        res[name] = {"kops": HM_BATCH * ws / t / 1e3, "ms_per_call": t * 1e3}
+        res[name] = {"kops": args.hmult_batch * ws / t / 1e3, "ms_per_call": t * 1e3}
         if nbytes:
             res[name]["hbm_frac"] = nbytes / t / 1e9 / peaks["hbm_gbs"]
     fhe.fhe_device_status(hctx.handle, 1)
