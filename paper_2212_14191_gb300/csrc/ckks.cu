@@ -345,12 +345,11 @@ __global__ void k_rescale_final(const uint32_t* __restrict__ ct, const uint32_t*
     }
 }
 
-// ---- HMULT tail, fused: the relinearised result (d_c + (ks_c - y_c) P^-1) is formed only
-// for the last limb (it feeds the rescale's INTT) and, for the other limbs, directly inside
-// the rescale's final step, so the relinearised ciphertext is never written out.
-// last_c = d_c[l] + (ks_c[l] - y_c[l]) [P^-1]_{q_l}, both components, limb l = nl - 1
-// ---- fused HMULT tail (ModDown combine folded into RESCALE). With rel_i = (ks_i - y^_i) P^-1
-// + d_i the relinearised limb i (NTT domain) and x_i the centred last limb broadcast to q_i,
+// ---- HMULT tail, fused (the ModDown combine folded into RESCALE): the relinearised result
+// d_c + (ks_c - y_c) P^-1 is formed only for the last limb l = nl - 1 (it feeds the rescale's
+// INTT) and, for the other limbs, inside the rescale's final step, so the relinearised
+// ciphertext is never written out. With rel_i = (ks_i - y^_i) P^-1 + d_i the relinearised
+// limb i (NTT domain) and x_i the centred last limb broadcast to q_i,
 // the output is (rel_i - x^_i) q_l^-1 = (ks_i P^-1 + d_i - NTT(y_i P^-1 + x_i)) q_l^-1 by the
 // linearity of the NTT mod q_i, so one forward NTT of z_i = y_i P^-1 + x_i replaces the NTTs
 // of y (ModDown) and of x (RESCALE). The constant factors are applied where they cost no
