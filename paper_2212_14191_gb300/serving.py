@@ -10,7 +10,11 @@ The server
   * keeps one queue per (operation, N, limbs) class and, whenever one of its CUDA streams is
     free, launches up to `max_batch` queued requests of the class with the oldest request as
     one batched library call on that stream;
-  * polls completion events, releases the footprint and records latencies.
+  * polls completion events, releases the footprint and records latencies;
+  * detects failures on the host: if batches are in flight and none completes for `stall_s`
+    seconds the run stops with an error naming them, and after the run every context's
+    device error word is read (fhe_device_status), so an expired bounded wait inside a
+    kernel (whose results are then incomplete) is reported instead of returned.
 Requests that arrive while others run are admitted as memory frees and join the next
 batches (continuous batching); batches on different streams overlap on the GPU.
 All arithmetic runs in libfhe's kernels; batching changes only the batch dimension, so a
@@ -49,13 +53,19 @@ def _op_code(kind):
 
 
 class Server:
-    def __init__(self, contexts, evks, budget_bytes, n_streams=4, max_batch=16):
+    def __init__(self, contexts, evks, budget_bytes, n_streams=4, max_batch=16, stall_s=60.0):
         """contexts: {logN: fhe.Context}; evks: {logN: int32 CUDA tensor (dnum, 2, nq+np, N)}."""
         self.ctx = contexts
         self.evk = evks
         self.budget = budget_bytes
         self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
         self.max_batch = max_batch
+        self.stall_s = stall_s
+
+    def check_device(self):
+        """Raise fhe.FheError if a kernel of any context reported an expired bounded wait."""
+        for ctx in self.ctx.values():
+            fhe.fhe_device_status(ctx.handle, 1)
 
     def footprint(self, r):
         n = 1 << r.logN
@@ -110,8 +120,12 @@ class Server:
         t0 = clock()
         done = 0
         n = len(requests)
+        last_progress = 0.0
         while done < n:
             now = clock() - t0
+            if inflight and now - last_progress > self.stall_s:
+                stuck = sorted({(b["reqs"][0].kind, b["reqs"][0].logN, b["reqs"][0].nl) for b in inflight})
+                raise RuntimeError("serving: no batch completed for %.1f s; in flight: %s" % (now - last_progress, stuck))
             # admission by HBM footprint
             while arrivals and arrivals[0].arrival <= now:
                 r = arrivals[0]
@@ -134,6 +148,8 @@ class Server:
                 reqs = [q.popleft() for _ in range(min(self.max_batch, len(q)))]
                 for r in reqs:
                     r.t_launch = now
+                if not inflight:
+                    last_progress = now
                 inflight.append(self._launch(reqs, free_streams.pop()))
                 batches.append(len(reqs))
             # completions
@@ -146,9 +162,11 @@ class Server:
                         used -= r.footprint
                     done += len(b["reqs"])
                     free_streams.append(b["stream"])
+                    last_progress = t
                 else:
                     still.append(b)
             inflight = still
+        self.check_device()
         t_end = max(r.t_done for r in requests)
         lat = sorted((r.t_done - r.arrival) * 1e3 for r in requests)
 
