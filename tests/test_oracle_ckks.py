@@ -329,3 +329,44 @@ def test_cmult_and_hadd_decrypt_exactly(small):
     assert dec == want
     dec = C.decrypt_coeffs(prm, C.hadd(prm, nl, ct1, ct2), s)
     assert dec == [int(v) for v in (m1 + e1 + m2 + e2)]
+
+
+@pytest.mark.parametrize("nl", [2, 5, 12])
+def test_fused_moddown_rescale_is_exact(small, nl):
+    """Reading 20 on the CPU: the fused tail (one NTT of z_i = y_i P^-1 + [last]_i, output
+    (ks_i P^-1 + d_i - z^_i) q_l^-1) and its scaled form (d'_i = d_i q_l^-1,
+    ks'_i = ks_i P^-1 q_l^-1, y'_i = y_i P^-1 q_l^-1, output ks'_i + d'_i - NTT(y'_i +
+    [last]_i q_l^-1)) both equal relinearisation followed by RESCALE bit for bit."""
+    prm, s, evk = small
+    N = prm.N
+    qm, psi = prm.qs[:nl], prm.psi_q[:nl]
+    ql, l = prm.qs[nl - 1], nl - 1
+    ct_a = I.uniform_residues(70 + nl, qm, 2, N, dtype=np.uint64).transpose(1, 0, 2)
+    ct_b = I.uniform_residues(80 + nl, qm, 2, N, dtype=np.uint64).transpose(1, 0, 2)
+    want = C.hmult(prm, nl, ct_a, ct_b, evk)
+    d0, d1, d2 = C.tensor(ct_a, ct_b, qm)
+    ks = C.inner_product(prm, nl, d2, evk)
+    pinv = np.array([pow(prm.P % q, -1, q) for q in qm], dtype=U64)[:, None]
+    qlinv = np.array([pow(ql, -1, q) if q != ql else 0 for q in qm], dtype=U64)[:, None]
+    mods = np.array(qm, dtype=U64)[:, None]
+    for c, d in enumerate((d0, d1)):
+        k = ks[c]
+        y = C.conv(C.intt(k[nl:], prm.ps, prm.psi_p), prm.ps, qm)            # coefficient domain
+        # the last relinearised limb in the coefficient domain, centred
+        rel_l = (C.sub(k[l:l + 1], C.ntt(y[l:l + 1], [ql], [psi[l]]), [ql]) * pinv[l]) % ql
+        rel_l = (rel_l + d[l:l + 1]) % ql
+        last = C.intt(rel_l, [ql], [psi[l]])[0].astype(np.int64)
+        last = np.where(last > (ql - 1) // 2, last - ql, last)
+        x = C.small_to_residues(last, qm[:l])                                # [last]_i, i < l
+        m = mods[:l]
+        # fused form of reading 20
+        z = ((y[:l] * pinv[:l]) % m + x) % m
+        out = (((k[:l] * pinv[:l]) % m + d[:l]) % m + m - C.ntt(z, qm[:l], psi[:l])) % m
+        out = (out * qlinv[:l]) % m
+        assert (out == want[c]).all(), (nl, c)
+        # scaled form (the GPU's fused tail)
+        sc = (pinv[:l] * qlinv[:l]) % m
+        ks_s, d_s, y_s = (k[:l] * sc) % m, (d[:l] * qlinv[:l]) % m, (y[:l] * sc) % m
+        z_s = (y_s + (x * qlinv[:l]) % m) % m
+        out_s = ((ks_s + d_s) % m + m - C.ntt(z_s, qm[:l], psi[:l])) % m
+        assert (out_s == want[c]).all(), (nl, c)
