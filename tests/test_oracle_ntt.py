@@ -235,3 +235,29 @@ def test_segment_fusion_identities():
     Wj = [(W * (1 << (8 * j))) % q for j in range(4)]
     acc = [sum(planes(Wj[j])[i].dot(Tp[j]) for j in range(4)) for i in range(4)]
     assert (sum(acc[i] << (8 * i) for i in range(4)) % q == exact % q).all()
+
+
+@pytest.mark.parametrize("n,c", [(64, 2), (64, 4), (128, 8), (256, 4)])
+def test_two_pass_dit_identity(n, c):
+    """Reading 21, the plain path's two-pass forward: with N = NC C,
+    B_j = NTT_NC(a[j + C m]) under the root psi^C, and A[k' + NC t] =
+    sum_j w^(t j) psi^((2k'+1) j) B_j[k'] with w = psi^(2 NC) (a C-th root of unity).
+    psi^C is the library's own NC-point root (psi_{N/2} = psi_N^2), so the local pass is the
+    plain NC-point transform with its own tables."""
+    q = Q30[1]
+    psi = P.psi(q, n)
+    nc = n // c
+    psi_c = pow(psi, c, q)
+    assert psi_c == P.psi(q, nc)
+    w = pow(psi, 2 * nc, q)
+    assert pow(w, c, q) == 1 and (c == 1 or pow(w, c // 2, q) == q - 1)
+    a = np.random.default_rng(n + c).integers(0, q, n, dtype=np.uint64).astype(np.uint32)
+    B = [O.ntt_brute(a[j::c].copy(), q, psi_c) for j in range(c)]
+    out = np.zeros(n, dtype=np.uint64)
+    for t in range(c):
+        for k in range(nc):
+            acc = 0
+            for j in range(c):
+                acc += pow(w, t * j, q) * pow(psi, (2 * k + 1) * j, q) * int(B[j][k])
+            out[k + nc * t] = acc % q
+    assert (out.astype(np.uint32) == O.ntt_brute(a, q, psi)).all()
