@@ -1,6 +1,7 @@
 """Host-side checks of the arithmetic the tensor-core NTT relies on (Sec. IV-B, segment fusion
 of Eq. (9)): the balanced 8-bit digits the kernels produce, their exact fp16 encoding, and the
-exactness of the digit GEMM under fp32 accumulation at the largest reduction size.
+exactness of the digit GEMM under fp32 accumulation at the largest reduction size; and of the
+tensor-core form of Conv (Sec. IV-A), its 32-bit reconstruction included.
 
 These run on the CPU and use no GPU code: they pin the identities the kernel arithmetic is
 built on, so that a plausible slip there (a wrong bias, an unbalanced digit, an accumulation
@@ -96,3 +97,63 @@ def test_digit_gemm_exact_under_fp32(K):
         y += (255 ** i) * exact
     np.testing.assert_array_equal(y % q, ref)
     assert 4 * K * 128 * 127 < (1 << 24)
+
+
+def _shoup(x, w, q):
+    """Shoup's product x w mod q for x < 2^32, w < q, in 32-bit words: the quotient estimate
+    floor(x floor(2^32 w / q) / 2^32) is short by at most one, then one conditional subtract."""
+    x = x.astype(np.uint64)
+    wq = np.uint64((int(w) << 32) // int(q))
+    qt = (x * wq) >> np.uint64(32)
+    r = (x * np.uint64(w) - qt * np.uint64(q)) & np.uint64(0xFFFFFFFF)
+    assert (r < 2 * q).all()
+    return np.where(r >= q, r - np.uint64(q), r)
+
+
+@pytest.mark.parametrize("nsrc", [1, 8, 15])
+def test_tensor_core_conv_reconstruction(nsrc):
+    """The tensor-core form of Conv (Sec. IV-A) restated on the CPU: y_i = [x_i (B/b_i)^-1]_{b_i}
+    and the constants [(B/b_i) 256^j]_{q_t} split into balanced base-256 digits, the digit GEMM
+    acc_{t,k} = sum_{i,j} d_{ij} e_{ijk} in fp32, each acc read back exactly by adding 1.5 2^23,
+    then lo = acc_0 + 256 acc_1 and hi = acc_2 + 256 acc_3 made positive by the multiple of q_t
+    at or above 2^29, and out = [lo + [2^16 hi]_q]_q by two Shoup products, all in 32-bit words.
+    It must equal the oracle's Conv for up to 15 sources (the largest the kernel takes)."""
+    from oracle import ckks as OC
+    qs = P.ntt_primes(nsrc + 6)
+    src, dst = qs[:nsrc], qs[nsrc:]
+    B = 1
+    for b in src:
+        B *= b
+    n = 4096
+    rng = np.random.default_rng(100 + nsrc)
+    x = np.stack([rng.integers(0, b, n, dtype=np.int64) for b in src]).astype(np.uint64)
+    # coefficient 0: every y_i has low digits -128 (largest data-digit magnitude)
+    yext = 63 * (1 << 24) - 0x808080
+    for i, b in enumerate(src):
+        x[i, 0] = yext * ((B // b) % b) % b
+    y = np.stack([(x[i] * np.uint64(pow((B // b) % b, -1, b))) % np.uint64(b)
+                  for i, b in enumerate(src)]).astype(np.int64)
+    assert (y[:, 0] == yext).all()
+    d = _digits_from_bias(y.T)                                  # (n, nsrc, 4): digit j of y_i
+    A = d.reshape(n, 4 * nsrc)                                  # K' = 4 i + j
+    ref = OC.conv(x, src, dst)
+    for ti, q in enumerate(dst):
+        w = np.array([[(B // b) % q * pow(256, j, q) % q for j in range(4)] for b in src], dtype=np.int64)
+        e = _digits_from_bias(w)                                # (nsrc, 4 j, 4 k)
+        assert np.abs(e).max() <= 128
+        E = e.reshape(4 * nsrc, 4)                              # row K' = 4 i + j, column k
+        exact = A @ E
+        assert np.abs(exact).max() <= 4 * nsrc * 128 * 128 < (1 << 20)
+        acc32 = A.astype(np.float16).astype(np.float32) @ E.astype(np.float16).astype(np.float32)
+        bits = (acc32 + np.float32(12582912.0)).astype(np.float32).view(np.int32).astype(np.int64)
+        acc = bits - 0x4B400000
+        np.testing.assert_array_equal(acc, exact)
+        off = -(-(1 << 29) // q) * q
+        lo = acc[:, 0] + 256 * acc[:, 1] + off
+        hi = acc[:, 2] + 256 * acc[:, 3] + off
+        assert lo.min() > 0 and hi.min() > 0 and lo.max() < (1 << 31) and hi.max() < (1 << 31)
+        th = _shoup(hi.astype(np.uint64), (1 << 16) % q, q)
+        s = lo.astype(np.uint64) + th
+        assert s.max() < (1 << 32)
+        out = _shoup(s, 1, q)
+        np.testing.assert_array_equal(out, ref[ti])
