@@ -23,7 +23,10 @@ Han and Ki that Sec. II-B and Sec. IV-A name, in this reading:
   the last limb is centred to (-q_l/2, q_l/2] before it is subtracted;
 * HROTATE / conjugation (Sec. II-B's operation table, FrobeniusMap) applies the
   automorphism X -> X^k to both components and key-switches c1(X^k) from
-  s(X^k) back to s; CMULT and HADD are limbwise Hada-Mult and Ele-Add.
+  s(X^k) back to s; CMULT and HADD are limbwise Hada-Mult and Ele-Add;
+* hoisted HROTATE (several rotations of one ciphertext) forms ModUp(c1) once and
+  applies each automorphism to the extended digits (hrotate_hoisted says how
+  that differs from hrotate).
 
 Arrays are numpy uint64 holding canonical residues; products of two residues
 below 2^30 fit in 64 bits, and every step reduces with '%'. The NTTs run in the
@@ -358,6 +361,37 @@ def hrotate(prm, nl, ct, ksk, k):
     c1 = automorph(ct[1], mods, psis, k)
     k0, k1 = keyswitch(prm, nl, c1, ksk)
     return np.stack([add(c0, k0, mods), k1 % _mods_col(mods)])
+
+
+def hrotate_hoisted(prm, nl, ct, ksks, ks):
+    """Several HROTATEs of one ciphertext sharing one ModUp (hoisted rotations): the digits
+    ModUp_j(c1) over q_0..q_{nl-1}, p_0.. are formed once in the NTT domain; for each Galois
+    element k they go through the automorphism, are multiplied by that rotation's key and
+    summed, and ModDown plus c0(X^k) finish as in hrotate. Returns (len(ks), 2, nl, N).
+
+    The automorphism commutes with the NTT and with products, but not exactly with the
+    approximate Conv: where X -> X^k negates a coefficient, the permuted digit holds the
+    negated lift -(sum_i y_i [B_j/b_i]) and ModUp of the permuted c1 the lift
+    sum_i [-y_i]_{b_i} [B_j/b_i]; they differ by B_j times the number of nonzero y_i. Both
+    are lifts of the same residues mod Q_j, so both key switches are valid, but they are
+    different results: this is a parity definition of its own, not hrotate's."""
+    mods, psis = prm.qs[:nl], prm.psi_q[:nl]
+    emods = prm.qs[:nl] + prm.ps
+    epsis = prm.psi_q[:nl] + prm.psi_p
+    c1_coeff = intt(ct[1], mods, psis)
+    digits = [modup(prm, nl, ct[1], c1_coeff, j) for j in range(prm.dnum(nl))]
+    outs = []
+    for ksk, k in zip(ksks, ks):
+        ks0 = np.zeros((nl + prm.K, prm.N), dtype=U64)
+        ks1 = np.zeros_like(ks0)
+        for j, dt in enumerate(digits):
+            dk = automorph(dt, emods, epsis, k)
+            ek = evk_at_level(prm, ksk, j, nl)
+            ks0 = add(ks0, hada(dk, ek[0], emods), emods)
+            ks1 = add(ks1, hada(dk, ek[1], emods), emods)
+        c0 = automorph(ct[0], mods, psis, k)
+        outs.append(np.stack([add(c0, moddown(prm, nl, ks0), mods), moddown(prm, nl, ks1) % _mods_col(mods)]))
+    return np.stack(outs)
 
 
 def cmult(prm, nl, ct, pt_ntt):

@@ -13,7 +13,10 @@ mathematics, not against itself:
   through the brute-force Eq. (4) transform, obeys the group law, permutes
   NTT slots, and rotates / conjugates the canonical-embedding slots;
 * decrypt(HROTATE(enc m)) = m(X^k) within the key-switching bound, and
-  CMULT / HADD decrypt exactly to the schoolbook product / the sum.
+  CMULT / HADD decrypt exactly to the schoolbook product / the sum;
+* hoisted rotations: the permuted ModUp digits differ from ModUp of the permuted
+  c1 by exactly -B_j times the count of nonzero y_i at negated coefficients (big
+  ints), k = 1 reproduces HROTATE, and every rotation decrypts within the bound.
 """
 import math
 
@@ -370,3 +373,89 @@ def test_fused_moddown_rescale_is_exact(small, nl):
         z_s = (y_s + (x * qlinv[:l]) % m) % m
         out_s = ((ks_s + d_s) % m + m - C.ntt(z_s, qm[:l], psi[:l])) % m
         assert (out_s == want[c]).all(), (nl, c)
+
+
+def _rot_key(prm, s, k, seed):
+    L = len(prm.qs)
+    arand = I.uniform_residues(seed, prm.qs + prm.ps, prm.dnum(L), prm.N, dtype=np.uint64).transpose(1, 0, 2)
+    return C.keygen_rot(prm, s, k, arand, I.gaussian_error(seed + 1, (prm.dnum(L), prm.N)))
+
+
+@pytest.mark.parametrize("nl", [5, 12])
+def test_hoisted_digits_differ_by_multiples_of_Qj(small, nl):
+    """Hoisting's one departure from hrotate, exactly: in the coefficient domain the permuted
+    digit automorph(ModUp_j(c1)) and ModUp_j(c1(X^k)) agree on slice j's own limbs, and on every
+    other limb differ by -B_j #{i : y_i != 0} at each coefficient that X -> X^k negates and by 0
+    at the others, with y_i = [c1_i (B_j/b_i)^-1]_{b_i} taken at the source coefficient."""
+    prm, _, _ = small
+    N, k = prm.N, C.galois_rotation(3, prm.N)
+    mods, psis = prm.qs[:nl], prm.psi_q[:nl]
+    emods, epsis = prm.qs[:nl] + prm.ps, prm.psi_q[:nl] + prm.psi_p
+    c1 = I.uniform_residues(90 + nl, mods, 1, N, dtype=np.uint64)[:, 0]
+    c1c = C.intt(c1, mods, psis)
+    c1k = C.automorph(c1, mods, psis, k)
+    c1kc = C.intt(c1k, mods, psis)
+    nonzero_seen = 0
+    for j in range(prm.dnum(nl)):
+        own = prm.slice_limbs(j, nl)
+        Bj = math.prod(prm.qs[i] for i in own)
+        hoisted = C.intt(C.automorph(C.modup(prm, nl, c1, c1c, j), emods, epsis, k), emods, epsis)
+        direct = C.intt(C.modup(prm, nl, c1k, c1kc, j), emods, epsis)
+        cnt = np.zeros(N, dtype=np.int64)
+        for i in own:
+            b = prm.qs[i]
+            y = (c1c[i] * U64(pow((Bj // b) % b, -1, b))) % U64(b)
+            cnt += (y != 0)
+        want = [0] * N
+        for n in range(N):
+            t = (n * k) % (2 * N)
+            if t >= N:
+                want[t - N] = -Bj * int(cnt[n])
+        for r, m in enumerate(emods):
+            diff = (hoisted[r].astype(np.int64) - direct[r].astype(np.int64)) % m
+            expect = np.array([w % m for w in want], dtype=np.int64)
+            np.testing.assert_array_equal(diff, expect, err_msg="slice %d limb %d" % (j, r))
+            nonzero_seen += int((diff != 0).sum())
+    assert nonzero_seen > 0   # the two forms really differ, so the parity definition matters
+
+
+def test_hoisted_identity_rotation_equals_hrotate(small):
+    """With k = 1 the automorphism is the identity and hoisting changes nothing: bit-exact."""
+    prm, s, evk = small
+    nl = 7
+    ct = I.uniform_residues(95, prm.qs[:nl], 2, prm.N, dtype=np.uint64).transpose(1, 0, 2)
+    out = C.hrotate_hoisted(prm, nl, ct, [evk], [1])
+    assert out.shape == (1, 2, nl, prm.N)
+    assert (out[0] == C.hrotate(prm, nl, ct, evk, 1)).all()
+
+
+def test_hoisted_rotations_decrypt_to_rotations(small):
+    """decrypt(hoisted HROTATE_k(enc m)) = m(X^k) within the key-switching bound (the hoisted
+    digits are lifts in (-alpha B_j, alpha B_j) instead of [0, alpha B_j), the same magnitude),
+    for three rotations and the conjugation of one ciphertext, and the slots are rotated /
+    conjugated; each agrees with the unhoisted HROTATE to within twice that bound."""
+    prm, s, _ = small
+    nl, N = 9, prm.N
+    rs = [1, -3, 5]
+    ks = [C.galois_rotation(r, N) for r in rs] + [C.galois_conjugation(N)]
+    keys = [_rot_key(prm, s, k, 300 + 2 * i) for i, k in enumerate(ks)]
+    z = I.uniform_reals(310, N // 2)
+    delta = 2.0 ** 25
+    m = C.encode(z, N, delta)
+    a = I.uniform_residues(311, prm.qs[:nl], 1, N, dtype=np.uint64)[:, 0]
+    ct = C.encrypt(prm, nl, m, s, a, I.gaussian_error(312, N))
+    outs = C.hrotate_hoisted(prm, nl, ct, keys, ks)
+    bound = 19.0
+    for j in range(prm.dnum(nl)):
+        Qj = math.prod(prm.qs[i] for i in prm.slice_limbs(j, nl))
+        bound += N * (prm.alpha + 1) * Qj / prm.P * 19
+    bound += (1 + int(np.abs(s).sum())) * (prm.K + 1)
+    for i, k in enumerate(ks):
+        dec = C.decrypt_coeffs(prm, outs[i], s, n_crt=3)
+        want = _int_automorph(m, k, prm.qs[:3])
+        assert max(abs(x - y) for x, y in zip(dec, want)) <= bound
+        ref = C.decrypt_coeffs(prm, C.hrotate(prm, nl, ct, keys[i], k), s, n_crt=3)
+        assert max(abs(x - y) for x, y in zip(dec, ref)) <= 2 * bound
+        slots = C.decode(np.array(dec, dtype=float), delta)
+        target = np.roll(z, -rs[i]) if i < len(rs) else np.conj(z)
+        assert np.abs(slots - target).max() < 1e-2
