@@ -153,6 +153,7 @@ int fhe_conv_get_path(const fhe_ctx* ctx);
 #define FHE_OP_RESCALE 3
 #define FHE_OP_HMULT_RELIN 4
 #define FHE_OP_HROTATE 5
+#define FHE_OP_HROTATE_HOISTED 6
 
 /*
  * fhe_scratch_bytes -- device scratch (bytes) that fhe_hmult / fhe_keyswitch /
@@ -217,6 +218,16 @@ int fhe_hmult(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const u
  *   k = galois (5^r mod 2N rotates the slots by r, 2N - 1 conjugates them). `ksk` is the
  *   key from s(X^k) to s in the layout of `evk` above. Scratch: fhe_scratch_bytes(
  *   FHE_OP_HROTATE); ct_out must not overlap ct_in. No rescale.
+ * fhe_hrotate_hoisted -- n_rot HROTATEs of one ciphertext batch sharing one ModUp (hoisted
+ *   rotations): ModUp of c1 is formed once in the NTT domain and each rotation applies its
+ *   automorphism to those digits before the inner product and ModDown. The approximate Conv
+ *   does not commute exactly with X -> X^k, so each result is a valid key switch of c1(X^k)
+ *   but not bit-identical to fhe_hrotate's: the automorphism of ModUp(c1) differs from ModUp
+ *   of c1(X^k) by B_j times the number of nonzero Conv terms at every negated coefficient.
+ *   galois: host array of n_rot odd elements < 2N; ksk: host array of n_rot device pointers,
+ *   key r from s(X^galois[r]) to s in the layout of `evk`; ct_out: (n_rot, 2, n_limbs, batch,
+ *   N), which must not overlap ct_in. Scratch: fhe_scratch_bytes(FHE_OP_HROTATE_HOISTED),
+ *   independent of n_rot. n_rot = 0 or batch = 0 does nothing. No rescale.
  * fhe_cmult -- CMULT: both components times the plaintext `pt` ((n_limbs, batch, N), NTT
  *   domain, one plaintext per ciphertext), limbwise mod q_i. No rescale. May run in place.
  * fhe_hadd -- HADD: ct_a + ct_b limbwise mod q_i. May run in place.
@@ -228,6 +239,9 @@ int fhe_automorph(const fhe_ctx* ctx, uint32_t logN, long long rows, uint32_t ga
 int fhe_hrotate(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, uint32_t galois,
                 const uint32_t* ct_in, const uint32_t* ksk, uint32_t* ct_out, void* scratch,
                 size_t scratch_bytes, void* stream);
+int fhe_hrotate_hoisted(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, int n_rot,
+                        const uint32_t* galois, const uint32_t* ct_in, const uint32_t* const* ksk,
+                        uint32_t* ct_out, void* scratch, size_t scratch_bytes, void* stream);
 int fhe_cmult(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const uint32_t* ct,
               const uint32_t* pt, uint32_t* ct_out, void* stream);
 int fhe_hadd(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const uint32_t* ct_a,

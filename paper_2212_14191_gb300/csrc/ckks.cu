@@ -455,31 +455,21 @@ size_t ks_scratch_limbs(int nl, int K, int alpha) {
     return (size_t)nl + dnum * (nl + K) + 2 * (size_t)(nl + K) + 2 * (size_t)nl;
 }
 
-// Key switching of d2 (NTT form) into `out` (2, nl, B, N); accumulate != 0 adds to out.
-// d2c (nl limbs of scratch) may already hold a copy of d2 when d2c_ready != 0.
-// scale_lt > 0 (the fused HMULT + RESCALE tail, out == nullptr): q limbs t < scale_lt of ks and
-// of y come out multiplied by P^-1 q_{nl-1}^-1, the factors the tail would otherwise apply.
-int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint32_t* d2,
-                   const uint32_t* evk, uint32_t* out, int accumulate, uint32_t* scratch,
-                   bool d2c_ready, cudaStream_t st, NttScratch ns, int scale_lt = 0) {
+// KS-1..KS-3: INTT of d2c (nl limbs, in place, NTT form in) and, per slice j, Conv
+// Q_j -> (Q_l \ Q_j) u P and the NTT of the converted limbs into `digits` (dnum, ext, B, N):
+// slice j's converted limbs at j * ext, the q limbs outside the slice first, then P.
+int ks_modup(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, uint32_t* d2c, uint32_t* digits,
+             cudaStream_t st, NttScratch ns) {
     const size_t N = 1ull << logN, limb = N * batch, L4 = limb / 4;
     const int K = ctx->np, ext = nl + K, alpha = ctx->alpha, nq = ctx->nq;
     const int nmod = (int)ctx->mods.size();
     const int dnum = (nl + alpha - 1) / alpha;
-    uint32_t* d2c = scratch;
-    uint32_t* tmp_all = d2c + (size_t)nl * limb;
-    uint32_t* ks = tmp_all + (size_t)dnum * ext * limb;
-    uint32_t* y = ks + 2 * (size_t)ext * limb;
     int rc;
-    if (!d2c_ready) FHE_CUDA_TRY(cudaMemcpyAsync(d2c, d2, (size_t)nl * limb * 4, cudaMemcpyDeviceToDevice, st));
     // KS-1: INTT(d2)
     if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, true, d2c, nl, batch, contiguous_map(ctx, 0, nl), st, ns))) return rc;
-    int ext_mod[kMaxLimbs];
-    for (int t = 0; t < ext; ++t) ext_mod[t] = t < nl ? t : nq + (t - nl);
-    ModVec ext_m = modvec(ctx, ext_mod, ext);
     for (int j = 0; j < dnum; ++j) {
         const int lo = j * alpha, hi = std::min(nl, (j + 1) * alpha);
-        uint32_t* tmp = tmp_all + (size_t)j * ext * limb;
+        uint32_t* tmp = digits + (size_t)j * ext * limb;
         const ConvTable& ct = ctx->modup[j][hi - lo - 1];
         // KS-2: Conv Q_j -> (Q_l \ Q_j) u P
         ConvArgs ca;
@@ -517,11 +507,29 @@ int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const u
         }
         if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, false, tmp, nd, batch, lm, st, ns))) return rc;
     }
+    return FHE_OK;
+}
+
+// KS-4, KS-5: the inner product of the ModUp digits with evk (slice j's own limbs taken from d2,
+// NTT form) and ModDown into `out` (2, nl, B, N); accumulate != 0 adds to out. ks (2 ext limbs)
+// and y (2 nl limbs) are scratch. scale_lt > 0 (the fused HMULT + RESCALE tail, out == nullptr):
+// q limbs t < scale_lt of ks and of y come out multiplied by P^-1 q_{nl-1}^-1.
+int ks_finish(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint32_t* d2, const uint32_t* digits,
+              const uint32_t* evk, uint32_t* out, int accumulate, uint32_t* ks, uint32_t* y, cudaStream_t st,
+              NttScratch ns, int scale_lt) {
+    const size_t N = 1ull << logN, limb = N * batch, L4 = limb / 4;
+    const int K = ctx->np, ext = nl + K, alpha = ctx->alpha, nq = ctx->nq;
+    const int nmod = (int)ctx->mods.size();
+    const int dnum = (nl + alpha - 1) / alpha;
+    int ext_mod[kMaxLimbs];
+    for (int t = 0; t < ext; ++t) ext_mod[t] = t < nl ? t : nq + (t - nl);
+    ModVec ext_m = modvec(ctx, ext_mod, ext);
+    int rc;
     // KS-4: inner product over all slices
     {
         IpArgs ia;
         ia.d2 = d2;
-        ia.tmp = tmp_all;
+        ia.tmp = digits;
         ia.evk = evk;
         ia.ks = ks;
         ia.nl = nl;
@@ -588,6 +596,27 @@ int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const u
                                                                   L4, modvec(ctx, qidx, nl));
     FHE_CUDA_TRY(cudaGetLastError());
     return FHE_OK;
+}
+
+// Key switching of d2 (NTT form) into `out` (2, nl, B, N); accumulate != 0 adds to out.
+// d2c (nl limbs of scratch) may already hold a copy of d2 when d2c_ready != 0.
+// scale_lt > 0 (the fused HMULT + RESCALE tail, out == nullptr): q limbs t < scale_lt of ks and
+// of y come out multiplied by P^-1 q_{nl-1}^-1, the factors the tail would otherwise apply.
+// Scratch: d2c (nl limbs), ModUp digits (dnum (nl + K)), ks (2 (nl + K)), y (2 nl).
+int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint32_t* d2,
+                   const uint32_t* evk, uint32_t* out, int accumulate, uint32_t* scratch,
+                   bool d2c_ready, cudaStream_t st, NttScratch ns, int scale_lt = 0) {
+    const size_t limb = ((size_t)1 << logN) * batch;
+    const int ext = nl + ctx->np;
+    const int dnum = (nl + ctx->alpha - 1) / ctx->alpha;
+    uint32_t* d2c = scratch;
+    uint32_t* tmp_all = d2c + (size_t)nl * limb;
+    uint32_t* ks = tmp_all + (size_t)dnum * ext * limb;
+    uint32_t* y = ks + 2 * (size_t)ext * limb;
+    int rc;
+    if (!d2c_ready) FHE_CUDA_TRY(cudaMemcpyAsync(d2c, d2, (size_t)nl * limb * 4, cudaMemcpyDeviceToDevice, st));
+    if ((rc = ks_modup(ctx, logN, nl, batch, d2c, tmp_all, st, ns))) return rc;
+    return ks_finish(ctx, logN, nl, batch, d2, tmp_all, evk, out, accumulate, ks, y, st, ns, scale_lt);
 }
 
 size_t rescale_scratch_limbs(int nl) { return 2 + 2 * (size_t)(nl - 1); }
@@ -797,6 +826,51 @@ int hrotate_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, uint32_t 
     return keyswitch_impl(ctx, logN, nl, batch, c1k, ksk, out, 1, c1k + (size_t)nl * limb, false, st, ns);
 }
 
+// Hoisted HROTATE: n_rot rotations of one ciphertext share one ModUp. The NTT-domain digits
+// ModUp_j(c1) are formed once; for each Galois element k the automorphism (a permutation of
+// NTT-domain values, the same under every modulus) is applied to c0, to c1 (the digits'
+// own-slice limbs) and to every slice's converted limbs, then the inner product with that
+// rotation's key and ModDown finish as in hrotate_impl. The approximate Conv does not commute
+// exactly with X -> X^k (where a coefficient is negated, its lift changes by a multiple of
+// Q_j), so this is a valid key switch of c1(X^k) that differs from hrotate_impl's result.
+// Scratch: c1 (copy, then coefficients; nl limbs), digits (dnum ext), c1(X^k) (nl), permuted
+// digits (dnum ext), ks (2 ext), y (2 nl); the per-rotation buffers are reused in turn.
+size_t hoisted_scratch_limbs(int nl, int K, int alpha) {
+    const size_t dnum = (size_t)((nl + alpha - 1) / alpha), ext = (size_t)(nl + K);
+    return 2 * (size_t)nl + 2 * dnum * ext + 2 * ext + 2 * (size_t)nl;
+}
+
+int hrotate_hoisted_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, int nrot, const uint32_t* galois,
+                         const uint32_t* ct, const uint32_t* const* ksk, uint32_t* out, uint32_t* scratch,
+                         cudaStream_t st, NttScratch ns) {
+    const size_t limb = ((size_t)1 << logN) * batch, rows = (size_t)nl * batch;
+    const int ext = nl + ctx->np, alpha = ctx->alpha, dnum = (nl + alpha - 1) / alpha;
+    uint32_t* c1c = scratch;
+    uint32_t* digits = c1c + (size_t)nl * limb;
+    uint32_t* c1k = digits + (size_t)dnum * ext * limb;
+    uint32_t* dk = c1k + (size_t)nl * limb;
+    uint32_t* ks = dk + (size_t)dnum * ext * limb;
+    uint32_t* y = ks + 2 * (size_t)ext * limb;
+    int rc;
+    FHE_CUDA_TRY(cudaMemcpyAsync(c1c, ct + (size_t)nl * limb, (size_t)nl * limb * 4, cudaMemcpyDeviceToDevice, st));
+    if ((rc = ks_modup(ctx, logN, nl, batch, c1c, digits, st, ns))) return rc;
+    for (int r = 0; r < nrot; ++r) {
+        const uint32_t k = galois[r];
+        uint32_t* o = out + (size_t)r * 2 * nl * limb;
+        if ((rc = launch_automorph(ctx, ct, o, k, logN, rows, st))) return rc;
+        if ((rc = launch_automorph(ctx, ct + (size_t)nl * limb, c1k, k, logN, rows, st))) return rc;
+        for (int j = 0; j < dnum; ++j) {
+            const int own = std::min(nl, (j + 1) * alpha) - j * alpha;
+            const size_t off = (size_t)j * ext * limb;
+            if ((rc = launch_automorph(ctx, digits + off, dk + off, k, logN, (size_t)(ext - own) * batch, st)))
+                return rc;
+        }
+        FHE_CUDA_TRY(cudaMemsetAsync(o + (size_t)nl * limb, 0, (size_t)nl * limb * 4, st));
+        if ((rc = ks_finish(ctx, logN, nl, batch, c1k, dk, ksk[r], o, 1, ks, y, st, ns, 0))) return rc;
+    }
+    return FHE_OK;
+}
+
 bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 int check_ckks(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, int min_nl) {
@@ -825,6 +899,7 @@ size_t scratch_limbs(const fhe_ctx* ctx, int op, int nl) {
         case FHE_OP_RESCALE: return rescale_scratch_limbs(nl);
         case FHE_OP_HMULT: return 2 * (size_t)nl + (size_t)nl + ks_scratch_limbs(nl, K, ctx->alpha);
         case FHE_OP_HROTATE: return hrotate_scratch_limbs(nl, K, ctx->alpha);
+        case FHE_OP_HROTATE_HOISTED: return hoisted_scratch_limbs(nl, K, ctx->alpha);
         default: return 0;
     }
 }
@@ -925,6 +1000,29 @@ int fhe_hrotate(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, uint3
         return set_error(FHE_ENOMEM, "scratch too small");
     return hrotate_impl(ctx, logN, n_limbs, batch, galois, ct_in, ksk, ct_out, (uint32_t*)scratch,
                         (cudaStream_t)stream, op_ntt_scratch(ctx, FHE_OP_HROTATE, logN, n_limbs, batch, scratch));
+}
+
+int fhe_hrotate_hoisted(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, int n_rot, const uint32_t* galois,
+                        const uint32_t* ct_in, const uint32_t* const* ksk, uint32_t* ct_out, void* scratch,
+                        size_t scratch_bytes, void* stream) {
+    int rc = check_ckks(ctx, logN, n_limbs, batch, 1);
+    if (rc) return rc;
+    FHE_CHECK(n_rot >= 0, "n_rot < 0");
+    if (batch == 0 || n_rot == 0) return FHE_OK;
+    FHE_CHECK(galois != nullptr && ksk != nullptr, "galois or ksk array is NULL");
+    for (int r = 0; r < n_rot; ++r) {
+        FHE_CHECK((galois[r] & 1u) == 1u && galois[r] < (2u << logN), "galois element must be odd and below 2N");
+        if ((rc = check_ptrs({ksk[r]}))) return rc;
+    }
+    if ((rc = check_ptrs({ct_in, ct_out, scratch}))) return rc;
+    const uintptr_t in0 = (uintptr_t)ct_in, out0 = (uintptr_t)ct_out;
+    const size_t ct_bytes = 2 * (size_t)n_limbs * ((size_t)batch << logN) * 4;
+    FHE_CHECK(out0 + (size_t)n_rot * ct_bytes <= in0 || in0 + ct_bytes <= out0, "ct_out overlaps ct_in");
+    if (scratch_bytes < fhe_scratch_bytes(ctx, FHE_OP_HROTATE_HOISTED, logN, n_limbs, batch))
+        return set_error(FHE_ENOMEM, "scratch too small");
+    return hrotate_hoisted_impl(ctx, logN, n_limbs, batch, n_rot, galois, ct_in, ksk, ct_out, (uint32_t*)scratch,
+                                (cudaStream_t)stream,
+                                op_ntt_scratch(ctx, FHE_OP_HROTATE_HOISTED, logN, n_limbs, batch, scratch));
 }
 
 int fhe_cmult(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const uint32_t* ct, const uint32_t* pt,

@@ -20,6 +20,7 @@ FHE_OK, FHE_EINVAL, FHE_ENOMEM, FHE_ECUDA, FHE_ETIMEOUT = 0, 1, 2, 3, 4
 FHE_NTT_DEFAULT, FHE_NTT_U32, FHE_NTT_TC = 0, 1, 2
 FHE_CONV_CUDA, FHE_CONV_TC = 0, 1
 FHE_OP_HMULT, FHE_OP_KEYSWITCH, FHE_OP_RESCALE, FHE_OP_HMULT_RELIN, FHE_OP_HROTATE = 1, 2, 3, 4, 5
+FHE_OP_HROTATE_HOISTED = 6
 FHE_RESCALE_NOALLOC_MAX_BYTES = 32 << 20
 
 if not os.path.exists(LIB_PATH):
@@ -58,6 +59,7 @@ _SIGS = {
     "fhe_rescale_noalloc": (_i, [_vp, _u32, _i, _i, _vp, _vp, _vp]),
     "fhe_automorph": (_i, [_vp, _u32, ctypes.c_longlong, _u32, _vp, _vp, _vp]),
     "fhe_hrotate": (_i, [_vp, _u32, _i, _i, _u32, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "fhe_hrotate_hoisted": (_i, [_vp, _u32, _i, _i, _i, _u32p, _vp, ctypes.POINTER(_vp), _vp, _vp, _sz, _vp]),
     "fhe_cmult": (_i, [_vp, _u32, _i, _i, _vp, _vp, _vp, _vp]),
     "fhe_hadd": (_i, [_vp, _u32, _i, _i, _vp, _vp, _vp, _vp]),
     "fhe_device_status": (_i, [_vp, _i]),
@@ -168,6 +170,17 @@ def fhe_automorph(ctx, logN, rows, galois, d_in, d_out, stream=0):
 def fhe_hrotate(ctx, logN, n_limbs, batch, galois, ct_in, ksk, ct_out, scratch, scratch_bytes, stream=0):
     return _check(_lib.fhe_hrotate(ctx, logN, n_limbs, batch, galois, ct_in, ksk, ct_out, scratch, scratch_bytes,
                                    stream))
+
+
+def fhe_hrotate_hoisted(ctx, logN, n_limbs, batch, galois, ct_in, ksks, ct_out, scratch, scratch_bytes, stream=0):
+    """galois: list of Galois elements; ksks: list of device pointers (one key per element)."""
+    n = len(galois)
+    if len(ksks) != n:
+        raise ValueError("one key per Galois element")
+    g = (ctypes.c_uint32 * max(1, n))(*galois)
+    k = (_vp * max(1, n))(*ksks)
+    return _check(_lib.fhe_hrotate_hoisted(ctx, logN, n_limbs, batch, n, g, ct_in, k, ct_out, scratch,
+                                           scratch_bytes, stream))
 
 
 def fhe_cmult(ctx, logN, n_limbs, batch, ct, pt, ct_out, stream=0):
@@ -353,6 +366,18 @@ class Context:
             out = torch.empty_like(ct)
         s, n = self.scratch(FHE_OP_HROTATE, logN, nl, batch)
         fhe_hrotate(self.handle, logN, nl, batch, galois, _ptr(ct), _ptr(ksk), _ptr(out), _ptr(s), n, _stream())
+        return out
+
+    def hrotate_hoisted(self, ct, ksks, logN, galois, out=None):
+        """Hoisted rotations of ct by every element of `galois` (one key each, same order):
+        returns (len(galois), 2, nl, batch, N)."""
+        import torch
+        nl, batch = ct.shape[1], ct.shape[2]
+        if out is None:
+            out = torch.empty((len(galois),) + tuple(ct.shape), dtype=ct.dtype, device=ct.device)
+        s, n = self.scratch(FHE_OP_HROTATE_HOISTED, logN, nl, batch)
+        fhe_hrotate_hoisted(self.handle, logN, nl, batch, list(galois), _ptr(ct), [_ptr(k) for k in ksks],
+                            _ptr(out), _ptr(s), n, _stream())
         return out
 
     def cmult(self, ct, pt, logN, out=None):

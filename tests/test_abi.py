@@ -45,8 +45,12 @@ def test_argument_validation_without_gpu(fhe):
         fhe.fhe_hmult(None, 12, 2, 1, 16, 16, 16, 16, 16, 0, 0)
     assert fhe.fhe_scratch_bytes(None, fhe.FHE_OP_HMULT, 12, 2, 1) == 0
     assert fhe.fhe_scratch_bytes(None, fhe.FHE_OP_HROTATE, 12, 2, 1) == 0
+    assert fhe.fhe_scratch_bytes(None, fhe.FHE_OP_HROTATE_HOISTED, 12, 2, 1) == 0
+    with pytest.raises(ValueError):
+        fhe.fhe_hrotate_hoisted(None, 12, 2, 1, [5, 25], 16, [16], 32, 16, 0)
     for call in (lambda: fhe.fhe_automorph(None, 12, 1, 5, 16, 32),
                  lambda: fhe.fhe_hrotate(None, 12, 2, 1, 5, 16, 16, 32, 16, 0),
+                 lambda: fhe.fhe_hrotate_hoisted(None, 12, 2, 1, [5, 25], 16, [16, 16], 32, 16, 0),
                  lambda: fhe.fhe_cmult(None, 12, 2, 1, 16, 16, 16),
                  lambda: fhe.fhe_hadd(None, 12, 2, 1, 16, 16, 16),
                  lambda: fhe.fhe_conv_set_path(None, fhe.FHE_CONV_TC),

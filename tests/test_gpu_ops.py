@@ -1,6 +1,7 @@
 """GPU parity of the other ciphertext operations of Sec. II-B's table against the CPU
-oracle: FrobeniusMap (X -> X^k), HROTATE / conjugation, CMULT and HADD, bit-exact on seeded
-inputs, plus CKKS decryption of a GPU rotation. The full-size case uses the HMULT
+oracle: FrobeniusMap (X -> X^k), HROTATE / conjugation, hoisted HROTATE (several rotations
+sharing one ModUp), CMULT and HADD, bit-exact on seeded inputs, plus CKKS decryption of a GPU
+rotation. The full-size case uses the HMULT
 configuration (N = 2^16, 24 + 8 limbs, dnum = 3) with sampled rows."""
 import numpy as np
 import pytest
@@ -77,6 +78,49 @@ def test_hrotate_bitexact(fhe, small, nl):
         for b in range(3):
             want = C.hrotate(prm, nl, ct[:, :, b].astype(U64), ksk, k)
             assert (got[:, :, b] == want).all(), (k, b)
+
+
+@pytest.mark.parametrize("nl", [1, 5, 12])
+def test_hrotate_hoisted_bitexact(fhe, small, nl):
+    """Three rotations and the conjugation of a batch of two ciphertexts sharing one ModUp,
+    against the oracle's hoisted rotation (its own parity definition), bit for bit."""
+    import torch
+    logn, prm, s, ctx = small
+    ks = [C.galois_rotation(3, prm.N), C.galois_conjugation(prm.N), C.galois_rotation(-1, prm.N)]
+    keys = [rot_key(prm, s, k, 130 + 2 * i) for i, k in enumerate(ks)]
+    ct = batch_cts(prm, nl, 2, 140 + nl)
+    out = ctx.hrotate_hoisted(fhe.to_device(ct), [fhe.to_device(k.astype(np.uint32)) for k in keys], logn, ks)
+    torch.cuda.synchronize()
+    got = fhe.to_host(out)
+    assert got.shape == (len(ks), 2, nl, 2, prm.N)
+    for b in range(2):
+        want = C.hrotate_hoisted(prm, nl, ct[:, :, b].astype(U64), keys, ks)
+        for r in range(len(ks)):
+            assert (got[r, :, :, b] == want[r]).all(), (nl, b, r)
+    fhe.fhe_device_status(ctx.handle, 1)
+
+
+def test_hrotate_hoisted_arguments(fhe, small):
+    import torch
+    logn, prm, s, ctx = small
+    x = torch.zeros((2, 2, 1, prm.N), dtype=torch.int32, device="cuda")
+    y = torch.zeros((2, 2, 2, 1, prm.N), dtype=torch.int32, device="cuda")
+    key = torch.zeros(16, dtype=torch.int32, device="cuda")
+    p = x.data_ptr()
+    # no rotations: nothing to do, no scratch needed
+    fhe.fhe_hrotate_hoisted(ctx.handle, logn, 2, 1, [], p, [], y.data_ptr(), 0, 0)
+    for g in ([5, 4], [5, 2 * prm.N + 1]):            # an even or out-of-range element
+        with pytest.raises(fhe.FheError) as e:
+            fhe.fhe_hrotate_hoisted(ctx.handle, logn, 2, 1, g, p, [key.data_ptr()] * 2, y.data_ptr(), p, 16)
+        assert e.value.code == fhe.FHE_EINVAL
+    with pytest.raises(fhe.FheError) as e:            # output overlapping the input
+        fhe.fhe_hrotate_hoisted(ctx.handle, logn, 2, 1, [5, 25], y.data_ptr(), [key.data_ptr()] * 2,
+                                y.data_ptr(), p, 16)
+    assert e.value.code == fhe.FHE_EINVAL
+    with pytest.raises(fhe.FheError) as e:            # scratch too small
+        fhe.fhe_hrotate_hoisted(ctx.handle, logn, 2, 1, [5, 25], p, [key.data_ptr()] * 2, y.data_ptr(), p, 16)
+    assert e.value.code == fhe.FHE_ENOMEM
+    fhe.fhe_device_status(ctx.handle, 1)
 
 
 def test_hrotate_decrypts_to_rotated_slots(fhe, small):
