@@ -521,9 +521,10 @@ def ours(args):
 
 def other_ops(args, fhe, hctx, a, b, evk, st, barrier, max_over_ranks, ws):
     """HROTATE (rotation by one slot; the relinearisation key stands in for the rotation key,
-    which has the same layout), CMULT and HADD on the HMULT workload: 128 ciphertexts of
-    24 limbs at N = 2^16. CMULT and HADD are HBM streams; their fraction is of the measured
-    HBM bandwidth."""
+    which has the same layout), four hoisted rotations of the same ciphertexts (by 1, 2 and 3
+    slots and the conjugation, one ModUp shared; one op = one rotated ciphertext), CMULT and
+    HADD on the HMULT workload: 128 ciphertexts of 24 limbs at N = 2^16. CMULT and HADD are HBM
+    streams; their fraction is of the measured HBM bandwidth."""
     import torch
     peaks, _ = measured_peaks()
     res = {"config": "N=2^16, 24 ciphertext limbs (+ 8 special primes for HROTATE), %d ciphertexts per call"
@@ -531,11 +532,15 @@ def other_ops(args, fhe, hctx, a, b, evk, st, barrier, max_over_ranks, ws):
     galois = 5                                   # 5^1 mod 2N: rotation of the slots by one
     pt = b[0]                                    # any (24, 128, N) residues serve as a plaintext
     out = torch.empty_like(a)
+    rots = (5, 25, 125, 2 * N - 1)
+    hout = torch.empty((len(rots),) + tuple(a.shape), dtype=a.dtype, device=a.device)
     limb_bytes = N * args.hmult_batch * 4
-    cases = (("hrotate", lambda: hctx.hrotate(a, evk, LOGN, galois, out=out), None, args.hmult_steps),
-             ("cmult", lambda: hctx.cmult(a, pt, LOGN, out=out), 5 * HM_LIMBS * limb_bytes, 10),
-             ("hadd", lambda: hctx.hadd(a, b, LOGN, out=out), 6 * HM_LIMBS * limb_bytes, 10))
-    for name, fn, nbytes, reps in cases:
+    cases = (("hrotate", lambda: hctx.hrotate(a, evk, LOGN, galois, out=out), None, args.hmult_steps, 1),
+             ("hrotate_hoisted_x4", lambda: hctx.hrotate_hoisted(a, [evk] * len(rots), LOGN, rots, out=hout), None,
+              args.hmult_steps, len(rots)),
+             ("cmult", lambda: hctx.cmult(a, pt, LOGN, out=out), 5 * HM_LIMBS * limb_bytes, 10, 1),
+             ("hadd", lambda: hctx.hadd(a, b, LOGN, out=out), 6 * HM_LIMBS * limb_bytes, 10, 1))
+    for name, fn, nbytes, reps, nrot in cases:
         fn()
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -547,11 +552,13 @@ def other_ops(args, fhe, hctx, a, b, evk, st, barrier, max_over_ranks, ws):
         torch.cuda.nvtx.range_pop()
         barrier()
         t = max_over_ranks(e0.elapsed_time(e1) / 1e3) / reps
-        res[name] = {"kops": args.hmult_batch * ws / t / 1e3, "ms_per_call": t * 1e3}
+        res[name] = {"kops": nrot * args.hmult_batch * ws / t / 1e3, "ms_per_call": t * 1e3}
+        if nrot > 1:
+            res[name]["ms_per_rotation"] = t * 1e3 / nrot
         if nbytes:
             res[name]["hbm_frac"] = nbytes / t / 1e9 / peaks["hbm_gbs"]
     fhe.fhe_device_status(hctx.handle, 1)
-    del out
+    del out, hout
     return res
 
 

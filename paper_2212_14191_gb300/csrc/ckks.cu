@@ -766,13 +766,17 @@ __global__ void k_automorph(const uint32_t* __restrict__ in, uint32_t* __restric
     }
 }
 
+// One CTA per 1024 outputs of a row (each thread one uint4), the CTAs of a row adjacent in
+// launch order: the rows in flight at once (about 19 at N = 2^16) then hold a few MB, so the
+// stride-k gather of each row is served from L2. With one CTA walking a whole row, some 1200
+// rows of 256 KB would be in flight, far above the 129 MB of L2, and gathered sectors would be
+// fetched from DRAM several times.
 int launch_automorph(const fhe_ctx* ctx, const uint32_t* in, uint32_t* out, uint32_t k, uint32_t logN, size_t rows,
                      cudaStream_t st) {
+    (void)ctx;
     if (rows == 0) return FHE_OK;
     const size_t L4 = ((size_t)1 << logN) / 4;
-    const unsigned gy = (unsigned)std::min<size_t>(rows, 65535);
-    dim3 g = stream_grid(ctx, L4, (int)std::min<size_t>(rows, 1 << 20));
-    g.y = gy;
+    const dim3 g((unsigned)((L4 + 255) / 256), (unsigned)std::min<size_t>(rows, 65535), 1);
     k_automorph<<<g, 256, 0, st>>>(in, out, k, (int)logN, rows);
     FHE_CUDA_TRY(cudaGetLastError());
     return FHE_OK;
