@@ -195,3 +195,27 @@ def test_hrotate_full_size_config(fhe):
         assert (got[:, :, b] == want).all(), b
     fhe.fhe_device_status(ctx.handle, 1)
     ctx.close()
+
+
+def test_hrotate_hoisted_full_size_config(fhe):
+    """N = 2^16, 24 ciphertext limbs + 8 special primes, dnum = 3, 4 ciphertexts, a rotation
+    and the conjugation sharing one ModUp: the first and last ciphertexts of the GPU result
+    against the oracle's hoisted rotation of that ciphertext, bit for bit."""
+    import torch
+    logn, n, nl, K, batch = 16, 1 << 16, 24, 8, 4
+    qs, ps = P.default_moduli(nl, K)
+    prm = C.Params(n, qs, ps, alpha=8)
+    s = I.ternary_secret(160, n, hamming_weight=64)
+    ks = [C.galois_rotation(2, n), C.galois_conjugation(n)]
+    keys = [rot_key(prm, s, k, 170 + 2 * i) for i, k in enumerate(ks)]
+    ct = batch_cts(prm, nl, batch, 180)
+    ctx = fhe.Context(logn, qs, ps, alpha=8)
+    out = ctx.hrotate_hoisted(fhe.to_device(ct), [fhe.to_device(k.astype(np.uint32)) for k in keys], logn, ks)
+    torch.cuda.synchronize()
+    got = fhe.to_host(out)
+    for b in (0, batch - 1):
+        want = C.hrotate_hoisted(prm, nl, ct[:, :, b].astype(U64), keys, ks)
+        for r in range(len(ks)):
+            assert (got[r, :, :, b] == want[r]).all(), (b, r)
+    fhe.fhe_device_status(ctx.handle, 1)
+    ctx.close()
