@@ -188,6 +188,35 @@ def cpu_oracle_kops(budget_s=10.0, batch_cap=NTT_BATCH):
         b *= 2
 
 
+def cpu_oracle_hmult(budget_s=8.0, n=N):
+    """The CKKS oracle (oracle/ckks.py: numpy, with the C oracle's transforms, as it stands) on
+    one ciphertext pair of the HMULT workload (24 + 8 limbs, dnum = 3): HMULT with
+    relinearisation and rescale, repeated until half the budget is spent. Context only: the
+    oracle exists to check parity. Random residues stand in for the key (timing does not
+    depend on the values)."""
+    from oracle import ckks as C
+    from oracle import params as P
+    from paper_2212_14191_gb300 import inputs as I
+    qs, ps = P.default_moduli(HM_LIMBS, HM_K)
+    prm = C.Params(n, qs, ps, alpha=HM_ALPHA)
+    dnum = prm.dnum(HM_LIMBS)
+    ct = [I.uniform_residues(20 + i, qs, 2, n, dtype=np.uint64).transpose(1, 0, 2) for i in range(2)]
+    evk = I.uniform_residues(22, qs + ps, dnum * 2, n, dtype=np.uint64).reshape(
+        HM_LIMBS + HM_K, dnum, 2, n).transpose(1, 2, 0, 3)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        out = C.hmult(prm, HM_LIMBS, ct[0], ct[1], evk)
+        done += 1
+        dt = time.perf_counter() - t0
+        if dt * 2 > budget_s:
+            break
+    assert out.shape == (2, HM_LIMBS - 1, n)
+    return {"value": done / dt / 1e3, "unit": "KOPS (HMULT + relinearisation + rescale)", "kind": "oracle",
+            "cores": "numpy on one thread, transforms on up to %d" % (os.cpu_count() or 1),
+            "sample": "%d ciphertext pair(s), N=%d, %d + %d limbs, dnum=%d (%.1f s)"
+                      % (done, n, HM_LIMBS, HM_K, dnum, dt)}
+
+
 def host_cpu():
     """CPU model and logical core count of this host, from /proc/cpuinfo where it says."""
     model = None
@@ -514,6 +543,8 @@ def ours(args):
         }
         if not args.no_cpu:
             line["cpu_baseline"] = cpu_oracle_kops()
+            if not args.no_hmult:
+                line["cpu_baseline"]["hmult_oracle"] = cpu_oracle_hmult()
         print(json.dumps(line))
     ctx.close()
     R.finish(ws)

@@ -1,7 +1,8 @@
 """Host logic of the benchmark that decides what its JSON line may claim, checked on the CPU:
 the DRAM traffic of a kernel is reported only while the kernel source still matches the
-ncu capture it came from, the peaks fall back (and say so) without the measured file, and
-the variant names and CPU description are well formed."""
+ncu capture it came from, the peaks fall back (and say so) without the measured file, the
+HMULT oracle timing is bounded and labelled, and the variant names and CPU description are
+well formed."""
 import hashlib
 import json
 import os
@@ -62,3 +63,9 @@ def test_variant_names(v):
 def test_host_cpu_description():
     d = bench.host_cpu()
     assert "logical cores" in d and str(os.cpu_count()) in d
+
+
+def test_hmult_oracle_timing_is_bounded_and_labelled():
+    r = bench.cpu_oracle_hmult(budget_s=0.5, n=1 << 11)
+    assert r["kind"] == "oracle" and r["value"] > 0 and "HMULT" in r["unit"]
+    assert "N=2048" in r["sample"] and "24 + 8 limbs" in r["sample"]

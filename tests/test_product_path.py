@@ -50,7 +50,7 @@ def test_package_never_imports_the_oracle():
 
 def test_oracle_is_imported_only_by_the_allowed_legs():
     bench = _oracle_imports(os.path.join(ROOT, "bench.py"))
-    assert bench and {o for o, _ in bench} <= {"cpu_oracle_kops", "reference_arm"}
+    assert bench and {o for o, _ in bench} <= {"cpu_oracle_kops", "cpu_oracle_hmult", "reference_arm"}
     entry = _oracle_imports(os.path.join(ROOT, "__graft_entry__.py"))
     assert entry and {o for o, _ in entry} <= {"build", "smoke"}
 
