@@ -261,3 +261,27 @@ def test_two_pass_dit_identity(n, c):
                 acc += pow(w, t * j, q) * pow(psi, (2 * k + 1) * j, q) * int(B[j][k])
             out[k + nc * t] = acc % q
     assert (out.astype(np.uint32) == O.ntt_brute(a, q, psi)).all()
+
+
+@pytest.mark.parametrize("n1,n2", [(4, 4), (8, 4), (16, 8), (32, 32)])
+def test_inverse_four_step_identity(n1, n2):
+    """The inverse in four-step form (Eq. (2)-(3) with the index maps of Eq. (9)):
+    a[N2 n1 + n2] = N^-1 sum_k1 psi^(-N2 (2k1+1) n1) psi^(-(2k1+1) n2)
+                    sum_k2 psi^(-2 N1 n2 k2) A[k1 + N1 k2],
+    a GEMM over k2, a Hadamard twiddle carrying N^-1, a GEMM over k1, against brute force."""
+    n = n1 * n2
+    q = Q30[2]
+    psi = P.psi(q, n)
+    pinv = pow(psi, -1, q)
+    ninv = pow(n, -1, q)
+    A = np.random.default_rng(n1 * 11 + n2).integers(0, q, n, dtype=np.uint64)
+    Am = A.reshape(n2, n1).T                        # Am[k1][k2] = A[k1 + N1 k2]
+    W3i = np.array([[pow(pinv, 2 * n1 * i * j, q) for j in range(n2)] for i in range(n2)], dtype=object)
+    Bm = _matmul_mod(Am, W3i, q)                    # [k1][n2]
+    T = np.array([[pow(pinv, (2 * k1 + 1) * j, q) * ninv % q for j in range(n2)] for k1 in range(n1)],
+                 dtype=object)
+    Cm = np.array((Bm.astype(object) * T) % q, dtype=np.uint64)
+    W1i = np.array([[pow(pinv, n2 * (2 * k1 + 1) * i, q) for k1 in range(n1)] for i in range(n1)], dtype=object)
+    Dm = _matmul_mod(W1i, Cm, q)                    # [n1][n2]
+    out = Dm.reshape(-1)                            # a[N2 n1 + n2]
+    assert (out.astype(np.uint32) == O.intt_brute(A.astype(np.uint32), q, psi)).all()
