@@ -1,0 +1,108 @@
+"""Host-side checks of the arithmetic the plain 32-bit NTT kernels rely on (Sec. II-A, Eq. (4);
+the comparison path of Sec. IV-B): Harvey's lazy butterflies with Shoup's precomputed-quotient
+products, in 32-bit words. A complete textbook negacyclic transform is run with those
+butterflies at the largest prime the library accepts (q < 2^30, so 4q < 2^32): the forward
+Cooley-Tukey butterflies keep every value in [0, 4q), the inverse Gentleman-Sande ones in
+[0, 2q), no word wraps, and after the final conditional subtractions the result equals the
+oracle's transform. These run on the CPU and use no GPU code."""
+import numpy as np
+import pytest
+
+from oracle import ntt as O
+from oracle import params as P
+
+U64 = np.uint64
+M32 = U64(0xFFFFFFFF)
+
+
+def shoup_quotient(w, q):
+    return (w.astype(object) * (1 << 32) // q).astype(U64) if isinstance(w, np.ndarray) else U64((w << 32) // q)
+
+
+def mul_shoup_lazy(x, w, wq, q):
+    """x w mod q in [0, 2q) for any 32-bit x: x w - floor(x wq / 2^32) q, taken mod 2^32."""
+    qt = (x * wq) >> U64(32)
+    return (x * w - qt * U64(q)) & M32
+
+
+def csub(x, m):
+    """[0, 2m) -> [0, m) as the kernels do it: min(x, x - m) on unsigned 32-bit words."""
+    return np.minimum(x, (x - U64(m)) & M32)
+
+
+def bitrev(k, bits):
+    return int(format(k, "0%db" % bits)[::-1], 2)
+
+
+def forward_lazy(a, q, psi):
+    n = a.size
+    bits = n.bit_length() - 1
+    psi_rev = np.array([pow(psi, bitrev(k, bits), q) for k in range(n)], dtype=U64)
+    psi_rev_q = shoup_quotient(psi_rev, q)
+    a = a.astype(U64).copy()
+    m, t = 1, n
+    while m < n:
+        t //= 2
+        v = a.reshape(m, 2, t)
+        w, wq = psi_rev[m:2 * m, None], psi_rev_q[m:2 * m, None]
+        x2 = csub(v[:, 0, :], 2 * q)
+        tt = mul_shoup_lazy(v[:, 1, :], w, wq, q)
+        assert x2.max() < 2 * q and tt.max() < 2 * q
+        x, y = x2 + tt, x2 - tt + U64(2 * q)
+        assert x.max() < 4 * q and y.max() < 4 * q and y.min() > 0
+        v[:, 0, :], v[:, 1, :] = x, y
+        m *= 2
+    out = csub(csub(a, 2 * q), q)                   # [0, 4q) -> [0, q)
+    return out[[bitrev(k, bits) for k in range(n)]]  # bit-reversed -> natural order
+
+
+def inverse_lazy(A, q, psi):
+    n = A.size
+    bits = n.bit_length() - 1
+    pinv = pow(psi, -1, q)
+    pinv_rev = np.array([pow(pinv, bitrev(k, bits), q) for k in range(n)], dtype=U64)
+    pinv_rev_q = shoup_quotient(pinv_rev, q)
+    a = A.astype(U64)[[bitrev(k, bits) for k in range(n)]].copy()   # natural -> bit-reversed
+    m, t = n, 1
+    while m > 1:
+        h = m // 2
+        v = a.reshape(h, 2, t)
+        w, wq = pinv_rev[h:2 * h, None], pinv_rev_q[h:2 * h, None]
+        x, y = v[:, 0, :], v[:, 1, :]
+        s = csub(x + y, 2 * q)
+        d = x - y + U64(2 * q)
+        assert s.max() < 2 * q and d.max() < 4 * q and d.min() > 0
+        v[:, 0, :], v[:, 1, :] = s, mul_shoup_lazy(d, w, wq, q)
+        assert v[:, 1, :].max() < 2 * q
+        t *= 2
+        m = h
+    ninv = pow(n, -1, q)
+    return csub(mul_shoup_lazy(a, U64(ninv), shoup_quotient(ninv, q), q), q)
+
+
+@pytest.mark.parametrize("logn", [4, 10, 12])
+def test_lazy_butterflies_at_the_largest_prime(logn):
+    n = 1 << logn
+    q = P.ntt_primes(1, logn_max=16)[0]
+    assert q < (1 << 30) and 4 * q < (1 << 32)
+    psi = P.psi(q, n)
+    rng = np.random.default_rng(logn)
+    for a in (rng.integers(0, q, n, dtype=np.int64).astype(U64),
+              np.full(n, q - 1, dtype=U64),                      # every input at its maximum
+              np.zeros(n, dtype=U64)):
+        A = forward_lazy(a, q, psi)
+        np.testing.assert_array_equal(A, O.ntt(a.astype(np.uint32), q, psi).astype(U64))
+        np.testing.assert_array_equal(inverse_lazy(A, q, psi), a)
+
+
+def test_shoup_product_bound_on_extreme_words():
+    """x w - floor(x wq / 2^32) q lies in [0, 2q) for every 32-bit x (the quotient estimate is
+    short by at most one), which is what lets the butterflies feed it values up to 4q."""
+    q = P.ntt_primes(1, logn_max=16)[0]
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.integers(0, 1 << 32, 100000, dtype=np.int64).astype(U64),
+                        np.array([0, 1, q - 1, q, 2 * q - 1, 4 * q - 1, (1 << 32) - 1], dtype=U64)])
+    for w in (0, 1, 2, q // 2, q - 2, q - 1, int(rng.integers(0, q))):
+        r = mul_shoup_lazy(x, U64(w), shoup_quotient(w, q), q)
+        assert r.max() < 2 * q
+        np.testing.assert_array_equal(r % U64(q), (x.astype(object) * w % q).astype(U64))
