@@ -4,7 +4,8 @@ products, in 32-bit words. A complete textbook negacyclic transform is run with 
 butterflies at the largest prime the library accepts (q < 2^30, so 4q < 2^32): the forward
 Cooley-Tukey butterflies keep every value in [0, 4q), the inverse Gentleman-Sande ones in
 [0, 2q), no word wraps, and after the final conditional subtractions the result equals the
-oracle's transform. These run on the CPU and use no GPU code."""
+oracle's transform. Also the 64-bit reduction of the CKKS kernels (Conv, inner product,
+Hada-Mult) and the accumulation bound it relies on. These run on the CPU and use no GPU code."""
 import numpy as np
 import pytest
 
@@ -106,3 +107,31 @@ def test_shoup_product_bound_on_extreme_words():
         r = mul_shoup_lazy(x, U64(w), shoup_quotient(w, q), q)
         assert r.max() < 2 * q
         np.testing.assert_array_equal(r % U64(q), (x.astype(object) * w % q).astype(U64))
+
+
+def reduce_red(x, q):
+    """x mod q for a 64-bit x as the CKKS kernels do it: the high word times [2^32]_q by
+    Shoup's method and the low word by one 32-bit Barrett step with floor(2^32 / q), each in
+    [0, 2q), summed below 4q and corrected twice."""
+    r32 = (1 << 32) % q
+    hi, lo = x >> U64(32), x & M32
+    t = mul_shoup_lazy(hi, U64(r32), shoup_quotient(r32, q), q)
+    u = (lo - (((lo * U64((1 << 32) // q)) >> U64(32)) * U64(q))) & M32
+    assert t.max() < 2 * q and u.max() < 2 * q
+    return csub(csub(t + u, 2 * q), q)
+
+
+def test_64bit_reduction_and_accumulation_bounds():
+    """Conv and the inner product add up to 15 products of residues below 2^30 in 64 bits
+    before one reduction (the inner product reduces after every 15 slices and continues from
+    a value below q): 15 (q - 1)^2 + q < 2^64, and reduce_red is exact on every 64-bit word,
+    including those extremes."""
+    rng = np.random.default_rng(9)
+    for q in (P.ntt_primes(1, logn_max=16)[0], P.ntt_primes(40, logn_max=16)[-1]):
+        assert 15 * (q - 1) ** 2 + q < (1 << 64)
+        x = np.concatenate([
+            rng.integers(0, 1 << 63, 200000, dtype=np.int64).astype(U64) * U64(2) + U64(1),
+            np.array([0, 1, q - 1, q, (1 << 32) - 1, 1 << 32, (1 << 64) - 1,
+                      15 * (q - 1) ** 2, 15 * (q - 1) ** 2 + q - 1], dtype=U64)])
+        got = reduce_red(x, q)
+        np.testing.assert_array_equal(got, np.array([int(v) % q for v in x], dtype=U64))
