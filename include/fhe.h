@@ -157,7 +157,9 @@ int fhe_conv_get_path(const fhe_ctx* ctx);
 
 /*
  * fhe_scratch_bytes -- device scratch (bytes) that fhe_hmult / fhe_keyswitch /
- * fhe_rescale / fhe_hmult_relin need for these sizes; 0 for invalid arguments.
+ * fhe_rescale / fhe_hmult_relin / fhe_hrotate / fhe_hrotate_hoisted need for these sizes
+ * (op = the matching FHE_OP_*; the hoisted size does not depend on the number of
+ * rotations); 0 for invalid arguments.
  */
 size_t fhe_scratch_bytes(const fhe_ctx* ctx, int op, uint32_t logN, int n_limbs, int batch);
 
