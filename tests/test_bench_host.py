@@ -1,8 +1,8 @@
 """Host logic of the benchmark that decides what its JSON line may claim, checked on the CPU:
 the DRAM traffic of a kernel is reported only while the kernel source still matches the
 ncu capture it came from, the peaks fall back (and say so) without the measured file, the
-HMULT oracle timing is bounded and labelled, and the variant names and CPU description are
-well formed."""
+HMULT oracle timing is bounded and labelled, the variant names and CPU description are well
+formed, and the reference arm prints one contract line on rank 0 and nothing elsewhere."""
 import hashlib
 import json
 import os
@@ -69,3 +69,33 @@ def test_hmult_oracle_timing_is_bounded_and_labelled():
     r = bench.cpu_oracle_hmult(budget_s=0.5, n=1 << 11)
     assert r["kind"] == "oracle" and r["value"] > 0 and "HMULT" in r["unit"]
     assert "N=2048" in r["sample"] and "24 + 8 limbs" in r["sample"]
+
+
+def _run_reference(env_extra):
+    import subprocess
+    import sys
+    env = {**os.environ, **env_extra}
+    return subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference",
+                           "--steps", "1", "--warmup", "1"], cwd=bench.ROOT, env=env,
+                          capture_output=True, text=True, timeout=600)
+
+
+def test_reference_arm_prints_one_contract_line():
+    """The reference arm times the oracle on the CPU and prints one JSON line with the CUDA
+    arm's metric, unit and direction, its own cpu_baseline and an e2e with no copies."""
+    r = _run_reference({"RANK": "0", "WORLD_SIZE": "1", "LOCAL_RANK": "0"})
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "KOPS"
+    assert d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 1 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "KOPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert "workload" in d["config"]
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    r = _run_reference({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert not [l for l in r.stdout.splitlines() if l.startswith("{")]
