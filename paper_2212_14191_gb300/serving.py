@@ -11,6 +11,8 @@ The server
     free, launches up to `max_batch` queued requests of the class with the oldest request as
     one batched library call on that stream;
   * polls completion events, releases the footprint and records latencies;
+  * under overload, optionally rejects a request that has waited for admission longer than
+    `admit_timeout_s` while the budget was full (it is marked rejected and never launched);
   * detects failures on the host: if batches are in flight and none completes for `stall_s`
     seconds the run stops with an error naming them, and after the run every context's
     device error word is read (fhe_device_status), so an expired bounded wait inside a
@@ -32,7 +34,7 @@ HMULT, RESCALE, KEYSWITCH = "hmult", "rescale", "keyswitch"
 
 class Request:
     __slots__ = ("rid", "kind", "logN", "nl", "arrival", "inputs", "out", "t_admit", "t_launch", "t_done",
-                 "footprint")
+                 "footprint", "rejected")
 
     def __init__(self, rid, kind, logN, nl, arrival, inputs):
         self.rid, self.kind, self.logN, self.nl, self.arrival = rid, kind, logN, nl, arrival
@@ -40,6 +42,7 @@ class Request:
         self.out = None
         self.t_admit = self.t_launch = self.t_done = None
         self.footprint = 0
+        self.rejected = False
 
 
 def _out_shape(kind, nl, batch, n):
@@ -53,14 +56,18 @@ def _op_code(kind):
 
 
 class Server:
-    def __init__(self, contexts, evks, budget_bytes, n_streams=4, max_batch=16, stall_s=60.0):
-        """contexts: {logN: fhe.Context}; evks: {logN: int32 CUDA tensor (dnum, 2, nq+np, N)}."""
+    def __init__(self, contexts, evks, budget_bytes, n_streams=4, max_batch=16, stall_s=60.0,
+                 admit_timeout_s=None):
+        """contexts: {logN: fhe.Context}; evks: {logN: int32 CUDA tensor (dnum, 2, nq+np, N)}.
+        admit_timeout_s: None waits for memory indefinitely; otherwise a request that cannot be
+        admitted within this many seconds of its arrival is rejected."""
         self.ctx = contexts
         self.evk = evks
         self.budget = budget_bytes
         self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
         self.max_batch = max_batch
         self.stall_s = stall_s
+        self.admit_timeout_s = admit_timeout_s
 
     def check_device(self):
         """Raise fhe.FheError if a kernel of any context reported an expired bounded wait."""
@@ -106,9 +113,10 @@ class Server:
         return {"reqs": reqs, "event": ev, "keep": (ins, out, scratch), "stream": stream}
 
     def run(self, requests, clock=time.perf_counter):
-        """Serve `requests` (sorted by arrival, seconds from start) to completion.
+        """Serve `requests` (sorted by arrival, seconds from start) to completion or rejection.
 
-        Returns a dict of latency percentiles (ms), throughput and batch statistics.
+        Returns a dict of latency percentiles (ms) over the completed requests, throughput,
+        batch statistics and the number rejected.
         """
         pending = collections.OrderedDict()   # class -> deque of admitted requests
         arrivals = collections.deque(requests)
@@ -119,6 +127,7 @@ class Server:
         peak_used = 0
         t0 = clock()
         done = 0
+        rejected = 0
         n = len(requests)
         last_progress = 0.0
         while done < n:
@@ -132,6 +141,12 @@ class Server:
                 if not r.footprint:
                     r.footprint = self.footprint(r)
                 if used + r.footprint > self.budget and (inflight or any(pending.values())):
+                    if self.admit_timeout_s is not None and now - r.arrival > self.admit_timeout_s:
+                        arrivals.popleft()
+                        r.rejected = True
+                        rejected += 1
+                        done += 1
+                        continue
                     break
                 arrivals.popleft()
                 r.t_admit = now
@@ -167,14 +182,16 @@ class Server:
                     still.append(b)
             inflight = still
         self.check_device()
-        t_end = max(r.t_done for r in requests)
-        lat = sorted((r.t_done - r.arrival) * 1e3 for r in requests)
+        served = [r for r in requests if not r.rejected]
+        t_end = max((r.t_done for r in served), default=clock() - t0)
+        lat = sorted((r.t_done - r.arrival) * 1e3 for r in served) or [0.0]
 
         def pct(p):
             return lat[min(len(lat) - 1, int(round(p / 100.0 * (len(lat) - 1))))]
 
-        return {"requests": n, "p50_ms": pct(50), "p99_ms": pct(99), "max_ms": lat[-1],
-                "throughput_kops": n / t_end / 1e3, "wall_s": t_end, "batches": len(batches),
+        return {"requests": n, "completed": len(served), "rejected": rejected,
+                "p50_ms": pct(50), "p99_ms": pct(99), "max_ms": lat[-1],
+                "throughput_kops": len(served) / t_end / 1e3, "wall_s": t_end, "batches": len(batches),
                 "mean_batch": sum(batches) / max(1, len(batches)), "peak_footprint_bytes": peak_used,
                 "budget_bytes": self.budget, "streams": len(self.streams)}
 
