@@ -29,10 +29,13 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2212_14191_gb300 import configs as CFG  # noqa: E402  (after the path insert)
+
 METRIC = "NTT KOPS and HMULT KOPS at N=2^16 (INT8-TC vs plain CUDA), % INT8/HBM roofline"
-LOGN, N = 16, 1 << 16
-NTT_LIMBS, NTT_BATCH = 44, 64
-HM_LIMBS, HM_K, HM_ALPHA, HM_BATCH = 24, 8, 8, 128
+LOGN, N = CFG.NTT_FULL.logN, 1 << CFG.NTT_FULL.logN
+NTT_LIMBS, NTT_BATCH = CFG.NTT_FULL.limbs, CFG.NTT_FULL.batch
+HM_LIMBS, HM_K, HM_ALPHA, HM_BATCH = (CFG.HMULT_FULL.limbs, CFG.HMULT_FULL.special, CFG.HMULT_FULL.alpha,
+                                      CFG.HMULT_FULL.batch)
 E2E_LIMBS = 11  # limbs per chunk of the pipelined end-to-end step
 
 
@@ -595,8 +598,8 @@ def other_ops(args, fhe, hctx, a, b, evk, st, barrier, max_over_ranks, ws):
 
 # Table (HEAX comparison) parameter sets in 30-bit primes: log PQ / 30 rounded up, split
 # into L ciphertext limbs and K special primes with P > Q (one key-switching slice, dnum = 1).
-HEAX_SETS = (("Set_A", 12, 2, 2), ("Set_B", 13, 4, 4), ("Set_C", 14, 7, 8))
-HEAX_BATCH = 1024
+HEAX_SETS = tuple((h.name, h.logN, h.L, h.K) for h in CFG.HEAX_SETS)
+HEAX_BATCH = CFG.HEAX_BATCH
 PAPER_A100 = {"Set_A": (910134, 913267, 88048), "Set_B": (449974, 449084, 27564), "Set_C": (209337, 209178, 3825)}
 
 
@@ -674,8 +677,8 @@ def mixed_batch(args, fhe, ctx, qs, ps, st, barrier, max_over_ranks, ws):
     limb_transforms = 0
     for i in range(n_ops):
         kind = int(g.integers(0, 3))
-        logn = int(g.choice([14, 15, 16]))
-        nl = int(g.integers(3, 45))
+        logn = int(g.choice(list(CFG.MIXED_BATCH.logNs)))
+        nl = int(g.integers(CFG.MIXED_BATCH.limb_range[0], CFG.MIXED_BATCH.limb_range[1] + 1))
         n = 1 << logn
         if kind < 2:
             d = torch.randint(0, 1 << 29, (nl, 1, n), dtype=torch.int32, device="cuda", generator=gen)
@@ -745,7 +748,8 @@ def serving_bench(args, fhe, qs, ps):
     footprint (24 GiB budget), continuous batching over 4 CUDA streams."""
     import torch
     from paper_2212_14191_gb300 import serving as S
-    logns = (15, 16)
+    sv = CFG.SERVING
+    logns = sv.logNs
     ctxs = {lg: fhe.Context(lg, qs[:HM_LIMBS], ps, alpha=HM_ALPHA) for lg in logns}
     dnum = -(-HM_LIMBS // HM_ALPHA)
     gen = torch.Generator(device="cuda")
@@ -762,10 +766,10 @@ def serving_bench(args, fhe, qs, ps):
                      for _ in range(k))
 
     kinds = [S.HMULT, S.RESCALE, S.KEYSWITCH]
-    warm = S.poisson_requests(6, 60, 50000.0, kinds, logns, (3, 24), make_inputs)
-    server = S.Server(ctxs, evks, budget_bytes=24 << 30, n_streams=4, max_batch=32)
+    warm = S.poisson_requests(6, 60, sv.rate_per_s, kinds, logns, sv.limb_range, make_inputs)
+    server = S.Server(ctxs, evks, budget_bytes=sv.budget_bytes, n_streams=sv.streams, max_batch=sv.max_batch)
     server.run(warm)
-    reqs = S.poisson_requests(7, args.serving_requests, 50000.0, kinds, logns, (3, 24), make_inputs)
+    reqs = S.poisson_requests(7, args.serving_requests, sv.rate_per_s, kinds, logns, sv.limb_range, make_inputs)
     torch.cuda.synchronize()
     stats = server.run(reqs)
     torch.cuda.synchronize()
