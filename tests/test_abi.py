@@ -73,3 +73,20 @@ def test_argument_validation_without_gpu(fhe):
     assert "P" in str(e.value)
     code, msg = fhe.last_error()
     assert code == fhe.FHE_EINVAL and msg
+
+
+def test_binding_constants_match_the_header(fhe):
+    """Every numeric #define of include/fhe.h that a caller passes or receives (status codes,
+    paths, operations, batch kinds, sizes) has the same value in the binding."""
+    import re
+    text = open(fhe.HEADER).read()
+    defs = {}
+    for m in re.finditer(r"^#define (FHE_[A-Z0-9_]+) \(?(\d+)u?(?: << (\d+))?\)?", text, re.M):
+        v = int(m.group(2)) << int(m.group(3) or 0)
+        defs[m.group(1)] = v
+    skip = {"FHE_LOGN_MIN", "FHE_LOGN_MAX", "FHE_MAX_MODULI"}   # limits checked by the library itself
+    names = [n for n in defs if n not in skip]
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(fhe, n), n
+        assert getattr(fhe, n) == defs[n], (n, getattr(fhe, n), defs[n])
