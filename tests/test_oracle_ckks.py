@@ -459,3 +459,21 @@ def test_hoisted_rotations_decrypt_to_rotations(small):
         slots = C.decode(np.array(dec, dtype=float), delta)
         target = np.roll(z, -rs[i]) if i < len(rs) else np.conj(z)
         assert np.abs(slots - target).max() < 1e-2
+
+
+def test_conv_hand_worked_example():
+    """The oracle's Conv against the hand-worked example in tests/golden/conv_b5_7_t11_13.txt
+    (Sec. IV-A): x = 1 and x = 23 come back as x + 35, the approximate conversion's u = 1."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "conv_b5_7_t11_13.txt")
+    rows = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            k, *vals = line.split()
+            rows[k] = [int(v) for v in vals]
+    src, dst, x = rows["src"], rows["dst"], np.array(rows["x"], dtype=U64)
+    res = np.stack([x % U64(b) for b in src])
+    out = C.conv(res, src, dst)
+    assert out[0].tolist() == rows["out11"] and out[1].tolist() == rows["out13"]
+    assert [v % 11 for v in rows["lift"]] == rows["out11"]
+    assert all((l - v) % 35 == 0 and 0 <= (l - v) // 35 < len(src) for l, v in zip(rows["lift"], rows["x"]))
