@@ -589,6 +589,8 @@ def other_ops(args, fhe, hctx, a, b, evk, st, barrier, max_over_ranks, ws):
         res[name] = {"kops": nrot * args.hmult_batch * ws / t / 1e3, "ms_per_call": t * 1e3}
         if nrot > 1:
             res[name]["ms_per_rotation"] = t * 1e3 / nrot
+            if "hrotate" in res:                 # single rotations per hoisted rotation time
+                res[name]["speedup_vs_single"] = res["hrotate"]["ms_per_call"] / (t * 1e3 / nrot)
         if nbytes:
             res[name]["hbm_frac"] = nbytes / t / 1e9 / peaks["hbm_gbs"]
     fhe.fhe_device_status(hctx.handle, 1)
