@@ -1,7 +1,8 @@
 """Host-side checks of the arithmetic the tensor-core NTT relies on (Sec. IV-B, segment fusion
 of Eq. (9)): the balanced 8-bit digits the kernels produce, their exact fp16 encoding, and the
-exactness of the digit GEMM under fp32 accumulation at the largest reduction size; and of the
-tensor-core form of Conv (Sec. IV-A), its 32-bit reconstruction included.
+exactness of the digit GEMM under fp32 accumulation at the largest reduction size, the
+epilogues' rebuild mod q from signed accumulators; and of the tensor-core form of Conv
+(Sec. IV-A), its 32-bit reconstruction included.
 
 These run on the CPU and use no GPU code: they pin the identities the kernel arithmetic is
 built on, so that a plausible slip there (a wrong bias, an unbalanced digit, an accumulation
@@ -157,3 +158,30 @@ def test_tensor_core_conv_reconstruction(nsrc):
         assert s.max() < (1 << 32)
         out = _shoup(s, 1, q)
         np.testing.assert_array_equal(out, ref[ti])
+
+
+def test_epilogue_reconstruction_bounds():
+    """The GEMM epilogues' rebuild mod q: y = acc_0 + 255 acc_1 + 255^2 acc_2 + 255^3 acc_3 from
+    accumulators |acc_i| <= 4K x 128 x 127 (K <= 256) stays within 2^49 in magnitude, so adding
+    the least multiple of q at or above 2^49 makes it positive and below 2^51; the 64-bit
+    Barrett step with mu = floor((2^64 - 1) / q) leaves a remainder below 3q, and two
+    conditional subtractions give y mod q. Checked at random and at every sign corner."""
+    amax = 4 * 256 * 128 * 127
+    assert amax < (1 << 24)
+    assert amax * (1 + 255 + 255 ** 2 + 255 ** 3) < (1 << 49)
+    rng = np.random.default_rng(21)
+    corners = [[s0 * amax, s1 * amax, s2 * amax, s3 * amax]
+               for s0 in (-1, 1) for s1 in (-1, 1) for s2 in (-1, 1) for s3 in (-1, 1)]
+    accs = corners + rng.integers(-amax, amax + 1, (20000, 4)).tolist() + [[0, 0, 0, 0]]
+    for q in (P.ntt_primes(1)[0], P.ntt_primes(44)[-1]):
+        mu = ((1 << 64) - 1) // q
+        off = -(-(1 << 49) // q) * q
+        for a in accs:
+            y = a[0] + 255 * a[1] + 65025 * a[2] + 16581375 * a[3]
+            x = y + off
+            assert 0 < x < (1 << 51)
+            r = x - ((x * mu) >> 64) * q
+            assert 0 <= r < 3 * q
+            r = r - 2 * q if r >= 2 * q else r
+            r = r - q if r >= q else r
+            assert r == y % q
