@@ -285,3 +285,26 @@ def test_inverse_four_step_identity(n1, n2):
     Dm = _matmul_mod(W1i, Cm, q)                    # [n1][n2]
     out = Dm.reshape(-1)                            # a[N2 n1 + n2]
     assert (out.astype(np.uint32) == O.intt_brute(A.astype(np.uint32), q, psi)).all()
+
+
+@pytest.mark.parametrize("n,c", [(64, 2), (64, 4), (128, 8), (256, 4)])
+def test_two_pass_dif_inverse_identity(n, c):
+    """The plain path's two-pass inverse splits the inputs by residue class of k mod C (each
+    local pass takes the class r, k = C k' + r, at stride C), then the cross pass combines
+    the C partial results: with N = NC C and n = n' + NC s,
+    a[n] = N^-1 sum_r psi^(-(2r+1) n) G_r[n'],   G_r[n'] = sum_k' A[C k' + r] psi^(-2 C k' n'),
+    G_r being a length-NC transform of the class (psi^(2C) is an NC-th root of unity)."""
+    q = Q30[3]
+    psi = P.psi(q, n)
+    pinv = pow(psi, -1, q)
+    nc = n // c
+    assert pow(psi, 2 * c * nc, q) == 1 and pow(psi, 2 * c * (nc // 2), q) == q - 1
+    A = np.random.default_rng(3 * n + c).integers(0, q, n, dtype=np.uint64).astype(np.uint32)
+    G = [[sum(int(A[c * kk + r]) * pow(pinv, 2 * c * kk * m, q) for kk in range(nc)) % q
+          for m in range(nc)] for r in range(c)]
+    ninv = pow(n, -1, q)
+    out = np.zeros(n, dtype=np.uint64)
+    for nn in range(n):
+        acc = sum(pow(pinv, (2 * r + 1) * nn, q) * G[r][nn % nc] for r in range(c))
+        out[nn] = acc * ninv % q
+    assert (out.astype(np.uint32) == O.intt_brute(A, q, psi)).all()
