@@ -302,6 +302,8 @@ int fhe_batch_destroy(fhe_batch* b);
  *   ...)) exceeds the array is rejected with FHE_ENOMEM.
  *   The first call on a device looks up the array's device address (cudaGetSymbolAddress,
  *   with that device current) and caches it; make that first call before any stream capture.
+ *   The cached address does not survive cudaDeviceReset (neither does any context).
+ *   The current device must be the context's device (FHE_EINVAL otherwise).
  *   All calls share the one array and it keeps the last call's contents: calls whose GPU work
  *   overlaps (other streams, other threads) race on it, so serialise them on one stream.
  * Arguments and layouts as fhe_rescale.

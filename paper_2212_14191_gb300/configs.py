@@ -1,7 +1,7 @@
 """Named parameter sets of the workloads this library is measured and tested on, restating the
 paper's parameter tables (Table V's default N = 2^16 and L = 44; the HMULT key-switching
 configuration with 24 ciphertext limbs, 8 special primes and slices of 8; the default batch of
-Sec. V-F; the HEAX comparison sets of Table VIII with this library's 30-bit primes). The
+Sec. VI-E, the batch-size study; the HEAX comparison sets of Table VIII with this library's 30-bit primes). The
 benchmark reads its sizes from here; a user can take the same sets.
 
 Every modulus set is the library's prime sequence (fhe_gen_primes / oracle.params): 30-bit

@@ -22,11 +22,16 @@ void* g_scratch_ptr[256];
 bool g_scratch_ready[256];
 
 // Looks up the scratch array's device address once per device, with that device current.
-int scratch_address(void** out) {
+// The cached address belongs to the CUDA context in which it was looked up: it does not
+// survive cudaDeviceReset (which also invalidates every fhe_ctx on that device).
+int scratch_address(const fhe_ctx* ctx, void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fhe::cuda_error(e, "cudaGetDevice");
     if (dev < 0 || dev >= 256) return fhe::set_error(FHE_EINVAL, "device ordinal out of range");
+    // the array is per device: the context's tables and the scratch must be on the same GPU
+    if (dev != ctx->device)
+        return fhe::set_error(FHE_EINVAL, "fhe_rescale_noalloc: the current device is not the context's device");
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_scratch_ready[dev]) {
         void* p = nullptr;
@@ -54,7 +59,7 @@ extern "C" int fhe_rescale_noalloc(const fhe_ctx* ctx, uint32_t logN, int n_limb
                                   std::to_string((size_t)FHE_RESCALE_NOALLOC_MAX_BYTES) +
                                   "; use fhe_rescale with caller-provided scratch");
     void* scratch = nullptr;
-    int rc = scratch_address(&scratch);
+    int rc = scratch_address(ctx, &scratch);
     if (rc) return rc;
     // The rescale overwrites every scratch word it reads, so nothing needs clearing first.
     return fhe_rescale(ctx, logN, n_limbs, batch, ct_in, ct_out, scratch, need, stream);

@@ -4,6 +4,9 @@ invokes the kernels, with intermediate results kept in device memory).
 
 Each request names an operation, a ring degree N = 2^logN and a limb count, and its
 ciphertext operands already live in HBM; evaluation keys are resident per ring degree.
+Operands may still be in production on the stream that is current when `run` is called:
+every launch stream first waits for an event recorded on that stream at the start of the
+run, so no batch reads an operand before it is written.
 The server
   * admits a request only while the HBM footprint of everything admitted and in flight
     (operands, result and the batch's scratch share) stays under `budget_bytes`;
@@ -68,6 +71,7 @@ class Server:
         self.max_batch = max_batch
         self.stall_s = stall_s
         self.admit_timeout_s = admit_timeout_s
+        self._ready = None   # event on the caller's stream at the start of run()
 
     def check_device(self):
         """Raise fhe.FheError if a kernel of any context reported an expired bounded wait."""
@@ -75,19 +79,31 @@ class Server:
             fhe.fhe_device_status(ctx.handle, 1)
 
     def footprint(self, r):
+        """Bytes a request holds while admitted: its operands, the gathered copy of them that
+        its batch makes, its result and its share of the batch's scratch. The result stays
+        allocated after completion (it belongs to the caller) and is no longer counted then."""
         n = 1 << r.logN
-        ins = sum(t.numel() * 4 for t in r.inputs)
+        ins = 2 * sum(t.numel() * 4 for t in r.inputs)   # the operands and their gathered copy
         out = 4 * n
         for d in _out_shape(r.kind, r.nl, 1, n)[:-1]:
             out *= d
         scratch = fhe.fhe_scratch_bytes(self.ctx[r.logN].handle, _op_code(r.kind), r.logN, r.nl, 1)
         return ins + out + scratch
 
+    def _producer_event(self):
+        """An event on the caller's current stream: everything queued there so far (the
+        operands' producers included) completes before any batch of this run starts."""
+        ev = torch.cuda.Event()
+        ev.record(torch.cuda.current_stream())
+        return ev
+
     def _launch(self, reqs, stream):
         r0 = reqs[0]
         kind, logN, nl, n = r0.kind, r0.logN, r0.nl, 1 << r0.logN
         ctx = self.ctx[logN]
         bsz = len(reqs)
+        if self._ready is not None:
+            stream.wait_event(self._ready)   # operands written on the producer stream come first
         with torch.cuda.stream(stream):
             if kind == KEYSWITCH:
                 ins = [torch.cat([r.inputs[0] for r in reqs], dim=1)]
@@ -118,6 +134,7 @@ class Server:
         Returns a dict of latency percentiles (ms) over the completed requests, throughput,
         batch statistics and the number rejected.
         """
+        self._ready = self._producer_event()
         pending = collections.OrderedDict()   # class -> deque of admitted requests
         arrivals = collections.deque(requests)
         inflight = []

@@ -165,3 +165,74 @@ def test_batch_rejects_bad_ops(fhe):
             fhe.fhe_batch_create(ctx.handle, [op])
         assert e.value.code == fhe.FHE_EINVAL
     ctx.close()
+
+
+def test_batch_full_size_ring_degrees(fhe):
+    """A plan at the uneven-batch workload's sizes: NTT and INTT rows at N = 2^15 and 2^16 with
+    24 to 44 limbs (the two-pass row-table kernels) and HMULT groups at 2^15 and 2^16 with 24,
+    36 and 44 limbs (3, 5 and 6 key-switching slices; one group gathers two operations). Every
+    operation equals its single call, eagerly and after graph capture; sampled NTT rows and
+    one 44-limb HMULT are compared with the oracle."""
+    import torch
+    qs, ps = P.default_moduli(44, 8)
+    mods = qs + ps
+    ctx = fhe.Context(16, qs, ps, alpha=8)
+    prm = {lg: C.Params(1 << lg, qs, ps, alpha=8) for lg in (15, 16)}
+    evk_h, evks = {}, {}
+    for lg in (15, 16):
+        n = 1 << lg
+        dn = prm[lg].dnum(len(qs))
+        evk_h[lg] = I.uniform_residues(900 + lg, mods, 2 * dn, n).reshape(len(mods), dn, 2, n).transpose(1, 2, 0, 3).copy()
+        evks[lg] = fhe.to_device(evk_h[lg])
+    ops, keep = [], []
+    ntt_specs = [(16, fhe.FHE_OPK_NTT_FWD, 0, 24, 2), (15, fhe.FHE_OPK_NTT_INV, 0, 44, 1),
+                 (15, fhe.FHE_OPK_NTT_FWD, 8, 30, 2), (16, fhe.FHE_OPK_NTT_INV, 4, 40, 1),
+                 (16, fhe.FHE_OPK_NTT_FWD, 44, 8, 1)]
+    for i, (lg, kind, first, nl, batch) in enumerate(ntt_specs):
+        x = I.uniform_residues(950 + i, mods[first:first + nl], batch, 1 << lg)
+        d = fhe.to_device(x)
+        ops.append(fhe.FheOp(kind=kind, logN=lg, first_limb=first, n_limbs=nl, batch=batch, data=d.data_ptr()))
+        keep.append(("ntt", lg, first, nl, batch, d, x, kind))
+    hm_specs = [(16, 44, 1), (15, 36, 1), (15, 36, 2), (16, 24, 1)]
+    for i, (lg, nl, batch) in enumerate(hm_specs):
+        n = 1 << lg
+        a = fhe.to_device(I.uniform_residues(970 + i, qs[:nl], 2 * batch, n).reshape(nl, 2, batch, n).transpose(1, 0, 2, 3).copy())
+        b = fhe.to_device(I.uniform_residues(980 + i, qs[:nl], 2 * batch, n).reshape(nl, 2, batch, n).transpose(1, 0, 2, 3).copy())
+        out = torch.empty((2, nl - 1, batch, n), dtype=torch.int32, device="cuda")
+        ops.append(fhe.FheOp(kind=fhe.FHE_OPK_HMULT, logN=lg, n_limbs=nl, batch=batch, a=a.data_ptr(),
+                             b=b.data_ptr(), evk=evks[lg].data_ptr(), out=out.data_ptr()))
+        keep.append(("hmult", lg, nl, batch, a, b, evks[lg], out))
+    want = reference_results(fhe, ctx, keep)
+    plan = fhe.fhe_batch_create(ctx.handle, ops)
+    nbytes = fhe.fhe_batch_scratch_bytes(plan)
+    scratch = torch.empty(max(4, nbytes // 4 + 4), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    fhe.fhe_batch_run(plan, scratch.data_ptr(), nbytes, stream)
+    torch.cuda.synchronize()
+    got = batch_results(fhe, keep)
+    for i, (w, g) in enumerate(zip(want, got)):
+        assert (w == g).all(), i
+    # oracle: the first and last limb of every NTT op (first polynomial), and the 44-limb HMULT
+    for k, g in zip(keep, got):
+        if k[0] == "ntt":
+            _, lg, first, nl, batch, d, x, kind = k
+            for l in (0, nl - 1):
+                m = mods[first + l]
+                ref, _ = ON.ntt_batch(x[l:l + 1, :1], [m], [P.psi(m, 1 << lg)], inverse=kind == fhe.FHE_OPK_NTT_INV)
+                assert (g[l:l + 1, :1] == ref).all(), (lg, first, l)
+    _, lg, nl, batch, a, b, evk, out = keep[len(ntt_specs)]
+    ha, hb = fhe.to_host(a), fhe.to_host(b)
+    oracle = C.hmult(prm[lg], nl, ha[:, :, 0].astype(np.uint64), hb[:, :, 0].astype(np.uint64),
+                     evk_h[lg].astype(np.uint64))
+    assert (got[len(ntt_specs)][:, :, 0] == oracle).all()
+    # graph capture and a replay
+    reset_inputs(fhe, keep)
+    fhe.fhe_batch_capture(plan, scratch.data_ptr(), nbytes)
+    reset_inputs(fhe, keep)
+    fhe.fhe_batch_launch(plan, stream)
+    torch.cuda.synchronize()
+    for i, (w, g) in enumerate(zip(want, batch_results(fhe, keep))):
+        assert (w == g).all(), i
+    fhe.fhe_device_status(ctx.handle, 1)
+    fhe.fhe_batch_destroy(plan)
+    ctx.close()

@@ -112,38 +112,77 @@ def test_hmult_decrypts(fhe, small):
     assert np.abs(dec - ref).max() / np.abs(ref).max() < 1e-5
 
 
-def test_hmult_full_size_config(fhe):
-    """N = 2^16, 24 ciphertext limbs + 8 special primes, dnum = 3 (alpha = 8), 128 pairs.
-
-    Two pairs (b = 0 and b = 127) are genuine encryptions under a sparse ternary secret
-    (h = 64); the rest are uniform. The whole batch goes through one fhe_hmult call; the two
-    genuine pairs are compared with the oracle bit-exactly and decrypted (error <= 1e-5).
-    """
+def _full_size_hmult(fhe, path, genuine, secret_weight=64, seed=1000):
+    """N = 2^16, 24 ciphertext limbs + 8 special primes, dnum = 3 (alpha = 8), 128 pairs
+    through one fhe_hmult call on a context whose default NTT path is `path`. The pairs at
+    `genuine` are encryptions of uniform reals in [-1, 1] at Delta = 2^30 under a ternary
+    secret of Hamming weight `secret_weight` (None: dense); the rest are uniform residues.
+    Returns (secret, key, inputs A and B, GPU output, slot products of the genuine pairs)."""
     import torch
     logn, N, nl, batch = 16, 1 << 16, 24, 128
     qs, ps = P.default_moduli(24, 8)
     prm = C.Params(N, qs, ps, alpha=8)
-    s, evk = make_key(prm, 1000)
+    s, evk = make_key(prm, seed, h=secret_weight)
     A = batch_cts(prm, nl, batch, 11)
     B = batch_cts(prm, nl, batch, 12)
-    zs = []
-    for k, b in enumerate((0, batch - 1)):
+    zs = {}
+    for k, b in enumerate(genuine):
         za, ca = encrypt_pair(prm, nl, s, 400 + 10 * k)
         zb, cb = encrypt_pair(prm, nl, s, 500 + 10 * k)
         A[:, :, b] = ca
         B[:, :, b] = cb
-        zs.append(za * zb)
-    ctx = fhe.Context(16, qs, ps, alpha=8)
+        zs[b] = za * zb
+    ctx = fhe.Context(16, qs, ps, alpha=8, default_path=path)
     out = ctx.hmult(fhe.to_device(A), fhe.to_device(B), fhe.to_device(evk.astype(np.uint32)), logn)
     torch.cuda.synchronize()
+    fhe.fhe_device_status(ctx.handle, 1)
     got = fhe.to_host(out)
     ctx.close()
-    scale = 2.0 ** 60 / qs[nl - 1]
-    for k, b in enumerate((0, batch - 1)):
+    return prm, s, evk, A, B, got, zs
+
+
+def _decode_error(prm, nl, ct, s, z):
+    """max_j |dec_j - z_j| / max_j |z_j| of the rescaled product (scale Delta^2 / q_(nl-1))."""
+    scale = 2.0 ** 60 / prm.qs[nl - 1]
+    dec = C.decode(np.array(C.decrypt_coeffs(prm, ct.astype(U64), s), dtype=float), scale)
+    return np.abs(dec - z).max() / np.abs(z).max()
+
+
+@pytest.mark.parametrize("path", ["u32", "tc"])
+def test_hmult_full_size_config(fhe, path):
+    """The benchmarked HMULT configuration on both NTT paths: N = 2^16, 24 + 8 limbs, dnum = 3,
+    128 pairs in one call. Pairs b = 0, 63 and 127 (first, middle and last of the batch, so
+    the 128 x 72 extended limbs' chunking through the tensor-core plane buffer is crossed)
+    are compared with the oracle bit for bit; the genuine pairs b = 0 and 127 (sparse ternary
+    secret, h = 64) decrypt to the slot products within 1e-5."""
+    nl = 24
+    p = fhe.FHE_NTT_U32 if path == "u32" else fhe.FHE_NTT_TC
+    prm, s, evk, A, B, got, zs = _full_size_hmult(fhe, p, genuine=(0, 127))
+    for b in (0, 63, 127):
         want = C.hmult(prm, nl, A[:, :, b].astype(U64), B[:, :, b].astype(U64), evk)
         assert (got[:, :, b] == want).all(), b
-        dec = C.decode(np.array(C.decrypt_coeffs(prm, got[:, :, b].astype(U64), s), dtype=float), scale)
-        assert np.abs(dec - zs[k]).max() / np.abs(zs[k]).max() < 1e-5
+    for b, z in zs.items():
+        assert _decode_error(prm, nl, got[:, :, b], s, z) < 1e-5, b
+
+
+def test_hmult_dense_ternary_error(fhe):
+    """Precision with a dense ternary secret (each coefficient uniform in {-1, 0, 1}) at the
+    benchmarked shape (N = 2^16, 24 + 8 limbs, dnum = 3, 128 pairs; four genuine pairs). The
+    1e-5 target is stated for the sparse secret (h = 64): with a dense one the rescale's
+    rounding error r0 + r1 s grows with the secret's weight (about 2N/3 nonzero coefficients), so
+    1e-5 is not claimed here. The test checks bit-exactness on one pair, prints the measured
+    maximum relative error per genuine pair and bounds it loosely by 5e-4 (the oracle's own
+    HMULT of the same pairs gives about 1e-4)."""
+    nl = 24
+    genuine = (0, 42, 85, 127)
+    prm, s, evk, A, B, got, zs = _full_size_hmult(fhe, fhe.FHE_NTT_U32, genuine=genuine, secret_weight=None,
+                                                  seed=1500)
+    assert np.count_nonzero(s) > prm.N // 2          # dense: about 2N/3 nonzero coefficients
+    want = C.hmult(prm, nl, A[:, :, 0].astype(U64), B[:, :, 0].astype(U64), evk)
+    assert (got[:, :, 0] == want).all()
+    errs = [_decode_error(prm, nl, got[:, :, b], s, zs[b]) for b in genuine]
+    print("dense ternary HMULT max relative error per pair:", ["%.3e" % e for e in errs])
+    assert max(errs) < 5e-4
 
 
 def test_hmult_tensor_core_path(fhe):

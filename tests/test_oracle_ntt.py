@@ -4,7 +4,7 @@ Every check here ties the oracle to something other than itself: a worked
 example computed by hand from Eq. (4), polynomial evaluation at the roots of
 X^N + 1 (Horner), closed forms for monomials, the schoolbook product in
 Z_q[X]/(X^N+1) (convolution theorem, Sec. II-A Eq. (3)), INTT(NTT(x)) = x (the
-correctness check of Sec. V-A), linearity, and library primality.
+correctness check of Sec. VI-A), linearity, and library primality.
 """
 import math
 

@@ -50,6 +50,9 @@ class FakeServer(S.Server):
     def check_device(self):
         self.checked = True
 
+    def _producer_event(self):
+        return None
+
 
 def requests(n, gap=0.0005, kinds=(S.HMULT, S.RESCALE)):
     return [S.Request(i, kinds[i % len(kinds)], 15, 4, i * gap, ()) for i in range(n)]

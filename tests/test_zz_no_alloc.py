@@ -1,8 +1,11 @@
 """fhe_rescale_noalloc: the rescale entry point for callers that cannot allocate device
 memory (it takes its scratch from a fixed array inside the library instead of from the
-caller or from cudaMalloc). Its output must equal fhe_rescale's, bit for bit, on two calls
-in a row (the shared array keeps the previous call's contents, which must not leak into
-the next result). Collected last on purpose."""
+caller or from cudaMalloc). Its output must equal fhe_rescale's, bit for bit, call after
+call: the shared array keeps the previous call's contents, which must not leak into the next
+result. The calls alternate between a large and a small shape, so each call runs over
+leftovers of a different layout, and the reference runs use scratch filled with all-ones
+words, so a read of a scratch word that the rescale did not write first would differ from
+the reference. Collected last on purpose."""
 import numpy as np
 import pytest
 
@@ -21,17 +24,16 @@ def fhe():
     return f
 
 
-@pytest.mark.parametrize("logn,nl,batch", [(12, 5, 3), (16, 24, 2)])
-def test_noalloc_rescale_matches_rescale(fhe, logn, nl, batch):
+def test_noalloc_rescale_matches_rescale(fhe):
     import torch
-    n = 1 << logn
     qs, ps = P.default_moduli(24, 8)
-    ctx = fhe.Context(logn, qs, ps, alpha=8)
-    need = fhe.fhe_scratch_bytes(ctx.handle, fhe.FHE_OP_RESCALE, logn, nl, batch)
-    assert 0 < need <= fhe.FHE_RESCALE_NOALLOC_MAX_BYTES
-    scratch = torch.empty(need // 4, dtype=torch.int32, device="cuda")
+    ctx = fhe.Context(16, qs, ps, alpha=8)
     stream = torch.cuda.current_stream().cuda_stream
-    for call in range(2):
+    for call, (logn, nl, batch) in enumerate([(16, 24, 2), (12, 5, 3), (16, 24, 2), (14, 9, 1)]):
+        n = 1 << logn
+        need = fhe.fhe_scratch_bytes(ctx.handle, fhe.FHE_OP_RESCALE, logn, nl, batch)
+        assert 0 < need <= fhe.FHE_RESCALE_NOALLOC_MAX_BYTES
+        scratch = torch.full((need // 4,), -1, dtype=torch.int32, device="cuda")
         x = I.uniform_residues(300 + call, qs[:nl], 2 * batch, n)
         ct = fhe.to_device(x.reshape(nl, 2, batch, n).transpose(1, 0, 2, 3).copy())
         want = torch.empty((2, nl - 1, batch, n), dtype=torch.int32, device="cuda")
@@ -40,7 +42,7 @@ def test_noalloc_rescale_matches_rescale(fhe, logn, nl, batch):
                         need, stream)
         fhe.fhe_rescale_noalloc(ctx.handle, logn, nl, batch, ct.data_ptr(), got.data_ptr(), stream)
         torch.cuda.synchronize()
-        assert torch.equal(got, want), call
+        assert torch.equal(got, want), (call, logn, nl, batch)
     ctx.close()
 
 
