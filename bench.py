@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-heax", action="store_true", help="skip the HEAX comparison parameter sets")
-    ap.add_argument("--serving-requests", type=int, default=2000)
+    ap.add_argument("--serving-seconds", type=float, default=2.0, help="seconds of arrivals per serving run")
     ap.add_argument("--batch-ops", type=int, default=1000)
     ap.add_argument("--e2e-limbs", type=int, default=E2E_LIMBS, help="limbs per chunk of the end-to-end pipeline")
     ap.add_argument("--hmult-batch", type=int, default=HM_BATCH,
@@ -665,7 +665,9 @@ def heax_sets(args, fhe, st, barrier, max_over_ranks, ws):
 def mixed_batch(args, fhe, ctx, qs, ps, st, barrier, max_over_ranks, ws):
     """Uneven batch: `--batch-ops` operations, kind uniform over {NTT, INTT, HMULT}, N uniform
     over {2^14, 2^15, 2^16}, level count (ciphertext limbs) uniform in 3..44, batch 1 each.
-    One CUDA-graph replay of the batched plan vs. one library call per operation."""
+    One CUDA-graph replay of the persistent plan (one persistent launch popping every
+    operation's stage tiles from a device queue) vs. the grouped plan (group after group) vs.
+    one library call per operation."""
     import torch
     g = np.random.default_rng(4)
     gen = torch.Generator(device="cuda")
@@ -700,10 +702,12 @@ def mixed_batch(args, fhe, ctx, qs, ps, st, barrier, max_over_ranks, ws):
                                  b=b.data_ptr(), evk=evk[logn].data_ptr(), out=out.data_ptr()))
             tensors += [a, b, out]
             desc.append((fhe.FHE_OPK_HMULT, logn, nl, (a, b, out)))
-    plan = fhe.fhe_batch_create(ctx.handle, ops)
-    nbytes = fhe.fhe_batch_scratch_bytes(plan)
+    plan = fhe.fhe_batch_create_ex(ctx.handle, ops, fhe.FHE_BATCH_PERSISTENT, 0)
+    gplan = fhe.fhe_batch_create_ex(ctx.handle, ops, fhe.FHE_BATCH_GROUPED, 0)
+    nbytes = max(fhe.fhe_batch_scratch_bytes(plan), fhe.fhe_batch_scratch_bytes(gplan))
     scratch = torch.empty(nbytes // 4 + 4, dtype=torch.int32, device="cuda")
     fhe.fhe_batch_capture(plan, scratch.data_ptr(), nbytes)
+    fhe.fhe_batch_capture(gplan, scratch.data_ptr(), nbytes)
     per_op_bytes = max(fhe.fhe_scratch_bytes(ctx.handle, fhe.FHE_OP_HMULT, lg, 44, 1) for lg in (14, 15, 16))
     op_scratch = torch.empty(per_op_bytes // 4 + 4, dtype=torch.int32, device="cuda")
 
@@ -730,24 +734,33 @@ def mixed_batch(args, fhe, ctx, qs, ps, st, barrier, max_over_ranks, ws):
         return max_over_ranks(e0.elapsed_time(e1) / 1e3 / reps)
 
     t_graph = timed(lambda: fhe.fhe_batch_launch(plan, sh), 3)
+    t_grouped = timed(lambda: fhe.fhe_batch_launch(gplan, sh), 3)
     t_ops = timed(per_op, 2)
     n_hm = sum(1 for d in desc if d[0] == fhe.FHE_OPK_HMULT)
     res = {"ops": n_ops, "hmult_ops": n_hm, "ntt_ops": n_ops - n_hm, "ntt_limb_transforms": limb_transforms,
-           "graph_ms": t_graph * 1e3, "per_op_ms": t_ops * 1e3,
-           "graph_kops": n_ops * ws / t_graph / 1e3, "per_op_kops": n_ops * ws / t_ops / 1e3,
-           "config": "N in {2^14,2^15,2^16}, 3..44 limbs, batch 1 per op, one graph launch vs one call per op",
+           "graph_ms": t_graph * 1e3, "grouped_graph_ms": t_grouped * 1e3, "per_op_ms": t_ops * 1e3,
+           "graph_kops": n_ops * ws / t_graph / 1e3, "grouped_graph_kops": n_ops * ws / t_grouped / 1e3,
+           "per_op_kops": n_ops * ws / t_ops / 1e3, "scratch_bytes": nbytes,
+           "config": "N in {2^14,2^15,2^16}, 3..44 limbs, batch 1 per op; graph replay of the persistent plan "
+                     "(one launch, device work queue) vs the grouped plan vs one call per op",
            "ntt_variant_16": [fhe.fhe_ntt_get_variant(ctx.handle, 16, 0), fhe.fhe_ntt_get_variant(ctx.handle, 16, 1)]}
     fhe.fhe_device_status(ctx.handle, 1)
     fhe.fhe_batch_destroy(plan)
+    fhe.fhe_batch_destroy(gplan)
     del tensors, scratch, op_scratch, evk
     torch.cuda.empty_cache()
     return res
 
 
 def serving_bench(args, fhe, qs, ps):
-    """Poisson stream (mean 50k requests/s) of HMULT / RESCALE / KEYSWITCH requests, N in
-    {2^15, 2^16}, 3..24 limbs, operands and evaluation keys resident in HBM, admitted by HBM
-    footprint (24 GiB budget), continuous batching over 4 CUDA streams."""
+    """Poisson streams of HMULT / RESCALE / KEYSWITCH requests, N in {2^15, 2^16}, 3..24 limbs,
+    operands and evaluation keys resident in HBM, admitted by HBM footprint (24 GiB budget),
+    continuous batching over 4 CUDA streams. Two steady-state runs of `--serving-seconds` of
+    arrivals each: the configured mean rate (50k requests/s, above capacity; a request not
+    admitted within 50 ms of its arrival is rejected), whose completion rate is the sustainable
+    capacity, then 0.8x that capacity (nothing rejected). Operands come from a pool of two
+    operand sets per (operation, N, limbs), since requests only read them; results are dropped
+    as batches complete."""
     import torch
     from paper_2212_14191_gb300 import serving as S
     sv = CFG.SERVING
@@ -758,31 +771,48 @@ def serving_bench(args, fhe, qs, ps):
     gen.manual_seed(5)
     evks = {lg: torch.randint(0, 1 << 29, (dnum, 2, HM_LIMBS + HM_K, 1 << lg), dtype=torch.int32, device="cuda",
                               generator=gen) for lg in logns}
+    pool = {}
 
     def make_inputs(kind, logN, nl, rid):
-        n = 1 << logN
-        if kind == S.KEYSWITCH:
-            return (torch.randint(0, 1 << 29, (nl, 1, n), dtype=torch.int32, device="cuda", generator=gen),)
-        k = 2 if kind == S.HMULT else 1
-        return tuple(torch.randint(0, 1 << 29, (2, nl, 1, n), dtype=torch.int32, device="cuda", generator=gen)
-                     for _ in range(k))
+        key = (kind, logN, nl, rid % 2)
+        if key not in pool:
+            n = 1 << logN
+            if kind == S.KEYSWITCH:
+                pool[key] = (torch.randint(0, 1 << 29, (nl, 1, n), dtype=torch.int32, device="cuda", generator=gen),)
+            else:
+                k = 2 if kind == S.HMULT else 1
+                pool[key] = tuple(torch.randint(0, 1 << 29, (2, nl, 1, n), dtype=torch.int32, device="cuda",
+                                                generator=gen) for _ in range(k))
+        return pool[key]
 
     kinds = [S.HMULT, S.RESCALE, S.KEYSWITCH]
-    warm = S.poisson_requests(6, 60, sv.rate_per_s, kinds, logns, sv.limb_range, make_inputs)
-    server = S.Server(ctxs, evks, budget_bytes=sv.budget_bytes, n_streams=sv.streams, max_batch=sv.max_batch)
-    server.run(warm)
-    reqs = S.poisson_requests(7, args.serving_requests, sv.rate_per_s, kinds, logns, sv.limb_range, make_inputs)
-    torch.cuda.synchronize()
-    stats = server.run(reqs)
-    torch.cuda.synchronize()
-    stats["config"] = ("Poisson 50k req/s, HMULT/RESCALE/KEYSWITCH, N in {2^15,2^16}, 3..24 limbs, "
-                       "24 GiB admission budget, 4 streams, batches of <= 32")
+
+    def run(rate, seconds, seed, admit_timeout_s):
+        n = max(1, int(rate * seconds))
+        reqs = S.poisson_requests(seed, n, rate, kinds, logns, sv.limb_range, make_inputs)
+        server = S.Server(ctxs, evks, budget_bytes=sv.budget_bytes, n_streams=sv.streams, max_batch=sv.max_batch,
+                          admit_timeout_s=admit_timeout_s, keep_results=False)
+        torch.cuda.synchronize()
+        st = server.run(reqs)
+        torch.cuda.synchronize()
+        st["offered_req_s"] = rate
+        st["arrival_s"] = reqs[-1].arrival
+        st["completed_req_s"] = st["completed"] / st["wall_s"]
+        return st
+
+    run(sv.rate_per_s, 0.05, 6, 0.05)                      # warm-up (pool, allocator, kernels)
+    over = run(sv.rate_per_s, args.serving_seconds, 7, 0.05)
+    capacity = over["completed_req_s"]
+    steady = run(0.8 * capacity, args.serving_seconds, 8, None)
     for c in ctxs.values():
         fhe.fhe_device_status(c.handle, 1)
         c.close()
-    del reqs, warm, evks
+    del pool, evks
     torch.cuda.empty_cache()
-    return stats
+    return {"overload": over, "steady_0p8": steady, "capacity_req_s": capacity,
+            "config": ("Poisson arrivals for %.1f s each: %d req/s (rejection after 50 ms without admission) and "
+                       "0.8 x the measured capacity; HMULT/RESCALE/KEYSWITCH, N in {2^15,2^16}, 3..24 limbs, "
+                       "24 GiB admission budget, 4 streams, batches of <= 32" % (args.serving_seconds, sv.rate_per_s))}
 
 
 def main():

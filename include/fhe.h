@@ -69,8 +69,15 @@ int fhe_gen_primes(uint32_t logN_max, int bits, int count, uint32_t* out);
  *              slice may be short. Requires prod(p) > every slice product (checked).
  *   default_path : FHE_NTT_U32 or FHE_NTT_TC, used by FHE_NTT_DEFAULT and by the HMULT pipeline.
  * Every prime must be distinct, prime, < 2^30 and = 1 mod 2^(logN_max+1); nq + np <= 64;
- * 1 <= alpha <= 15; np <= 15. The context owns its device tables and is immutable after
- * creation, so concurrent calls on different streams may share it.
+ * 1 <= alpha <= 15; np <= 15. The context owns its device tables.
+ * Concurrency: the CKKS operations (fhe_keyswitch .. fhe_hadd) take every NTT buffer they
+ * use, the tensor-core path's digit planes included, from the caller's scratch, so calls on
+ * one context may run at the same time on different streams with separate scratch buffers.
+ * fhe_ntt_fwd / fhe_ntt_inv with a two-pass plain variant or the tensor-core path use buffers
+ * owned by the context and must not overlap one another in time on one context. Calls that
+ * change the context (fhe_ntt_set_variant, fhe_autotune_ntt, fhe_conv_set_path) must not
+ * race with any call using it; the tensor-core tables of a ring degree are built on its first
+ * tensor-core call, under a lock.
  * Allocates device memory (cudaMalloc) on the current device: the tables, and for
  * logN_max >= 15 a 1 GiB scratch for the two-pass plain NTT; *out = NULL on failure.
  */
@@ -95,8 +102,7 @@ int fhe_ntt_fwd(const fhe_ctx* ctx, int path, uint32_t logN, uint32_t* d, int fi
 /*
  * Plain-path variants that run in two passes (and the tensor-core path) use buffers owned
  * by the context: fhe_ntt_fwd / fhe_ntt_inv calls on one context must not overlap in time on
- * different streams. The CKKS calls below take the two-pass buffer from the caller's
- * scratch and may overlap freely on the plain path.
+ * different streams (see fhe_ctx_create; the CKKS calls below may overlap).
  *
  * fhe_ntt_inv -- in-place inverse of fhe_ntt_fwd (Sec. II-A, Eq. (2) with the psi^-n
  * post-twist of Eq. (3); Sec. IV-C Stage 5 names the N^-1 factor):
@@ -257,12 +263,28 @@ int fhe_hadd(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const ui
  *     FHE_OPK_HMULT computes out = fhe_hmult(a, b, evk) at n_limbs ciphertext limbs
  *     (first_limb ignored). All device pointers 16-byte aligned; operations must not
  *     overlap in memory; their results equal those of the single-operation calls.
- *   fhe_batch_create -- validates and plans the list: every limb transform of one (N,
- *     direction) becomes a row of one NTT launch; HMULTs sharing (N, n_limbs, evk) are
- *     gathered into one batch. Allocates the plan's device tables (cudaMalloc). The op list
- *     may be freed afterwards; the buffers it names must outlive the plan's runs.
+ *   fhe_batch_create -- validates and plans the list (mode FHE_BATCH_PERSISTENT, default slot
+ *     budget). Allocates the plan's device tables (cudaMalloc). The op list may be freed
+ *     afterwards; the buffers it names must outlive the plan's runs.
+ *   fhe_batch_create_ex -- the same with a mode:
+ *     FHE_BATCH_PERSISTENT: every operation at N >= 2^14 runs inside ONE persistent kernel
+ *       launch whose CTAs (a grid sized from the SM count and the kernel's occupancy) pop
+ *       tiles of the operations' stages from a device queue: NTT/INTT local passes of one row
+ *       part, and chunks of 16384 residues of the HMULT's tensor product, basis conversions,
+ *       inner product and last-limb steps. A tile starts once the stages it reads have
+ *       completed (device counters, bounded waits: an expired wait records FHE_ETIMEOUT in the
+ *       context's status word, the remaining tiles are skipped, the kernel ends; see
+ *       fhe_device_status). HMULTs run in scratch slots of at most `slot_bytes` in total
+ *       (0: 8 GiB; at least one slot); an HMULT waits for the previous one of its slot.
+ *       Operations at N < 2^14 run in the grouped form below, before the persistent launch.
+ *     FHE_BATCH_GROUPED: every limb transform of one (N, direction) becomes a row of one NTT
+ *       launch; HMULTs sharing (N, n_limbs, evk) are gathered into one batched fhe_hmult;
+ *       the groups run one after another.
  *   fhe_batch_scratch_bytes -- device scratch needed by fhe_batch_run / _capture.
- *   fhe_batch_run -- enqueues the plan on `stream` (capturable in a CUDA graph).
+ *   fhe_batch_run -- enqueues the plan on `stream` (capturable in a CUDA graph). A persistent
+ *     plan's first run on a scratch buffer (and the first after a change of buffer) uploads
+ *     its tables, which hold absolute addresses inside that buffer, synchronously: it fails
+ *     with FHE_EINVAL during stream capture, and earlier runs on other buffers must be done.
  *   fhe_batch_capture -- runs the plan once, then captures it into a graph owned by the plan
  *     (bound to this scratch buffer); fhe_batch_launch replays that graph on `stream`.
  *   fhe_batch_destroy -- frees the plan and its graph (no work may be pending).
@@ -283,7 +305,11 @@ typedef struct fhe_op {
     uint32_t* out;
 } fhe_op;
 typedef struct fhe_batch fhe_batch;
+#define FHE_BATCH_PERSISTENT 0
+#define FHE_BATCH_GROUPED 1
 int fhe_batch_create(const fhe_ctx* ctx, const fhe_op* ops, int n, fhe_batch** out);
+int fhe_batch_create_ex(const fhe_ctx* ctx, const fhe_op* ops, int n, int mode, size_t slot_bytes,
+                        fhe_batch** out);
 size_t fhe_batch_scratch_bytes(const fhe_batch* b);
 int fhe_batch_run(const fhe_batch* b, void* scratch, size_t scratch_bytes, void* stream);
 int fhe_batch_capture(fhe_batch* b, void* scratch, size_t scratch_bytes);
@@ -328,6 +354,16 @@ int fhe_device_status(const fhe_ctx* ctx, int clear);
  * The context stays usable; fhe_device_status(ctx, 1) then reports and clears the word.
  */
 int fhe_selftest_wait_timeout(const fhe_ctx* ctx, long long limit_cycles, void* stream);
+
+/*
+ * fhe_selftest_queue_timeout -- the same check for the persistent batch kernel's dependency
+ * waits (fhe_batch_create_ex, FHE_BATCH_PERSISTENT): runs that kernel on `stream` over a queue
+ * of one tile whose dependency counter nothing increments, with the wait limited to
+ * limit_cycles (0 < limit_cycles <= 4e9). The wait expires, FHE_ETIMEOUT is recorded in the
+ * context's device error word and the kernel returns. Allocates a few bytes of device memory
+ * and waits for the stream before returning.
+ */
+int fhe_selftest_queue_timeout(const fhe_ctx* ctx, long long limit_cycles, void* stream);
 
 /*
  * fhe_last_error -- copy the calling thread's last error message (NUL-terminated, truncated

@@ -1,16 +1,19 @@
 // Operation-level batching (Sec. IV-D) of many independent NTT / INTT / HMULT operations of
 // uneven ring degree and level, submitted as one plan and replayed as one CUDA graph launch.
 //
-// Planning groups the operations: every limb transform of one ring degree and direction
-// becomes one row of a single row-table NTT launch (rows may live in any buffer); HMULTs of
-// the same (N, limbs, key) are gathered into one (2, L, B, N) batch, run through the batched
-// HMULT pipeline and scattered back. Gathers and scatters are one copy kernel each, driven by
-// a device table of segments.
+// Operations at N >= 2^14 go through the persistent engine of persist.cu: one launch whose CTAs
+// pop the tiles of every operation's stages from a device queue. The grouped form below is used
+// for smaller ring degrees (and for every operation when a plan asks for it): every limb
+// transform of one ring degree and direction becomes one row of a single row-table NTT launch
+// (rows may live in any buffer); HMULTs of the same (N, limbs, key) are gathered into one
+// (2, L, B, N) batch, run through the batched HMULT pipeline and scattered back. Gathers and
+// scatters are one copy kernel each, driven by a device table of segments.
 #include <algorithm>
 #include <map>
 #include <tuple>
 
 #include "common.cuh"
+#include "persist.h"
 
 namespace fhe {
 namespace {
@@ -60,6 +63,7 @@ struct fhe_batch {
     std::vector<void*> allocs;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
+    fhe::PersistPlan* persist = nullptr;  // operations at N >= 2^14 (persistent mode)
     int n_ops = 0;
     int n_launch = 0;  // kernels launched per run (excluding those inside library calls' counts)
 };
@@ -107,6 +111,8 @@ int run_batch(const fhe_batch* b, void* scratch, cudaStream_t st) {
         k_segcopy<<<dim3(gx, g.nout), 256, 0, st>>>(g.d_out, base);
         FHE_CUDA_TRY(cudaGetLastError());
     }
+    // the persistent engine runs after the grouped operations and reuses the same scratch
+    if (b->persist) return persist_run(b->persist, scratch, st);
     return FHE_OK;
 }
 
@@ -115,10 +121,16 @@ int run_batch(const fhe_batch* b, void* scratch, cudaStream_t st) {
 extern "C" {
 
 int fhe_batch_create(const fhe_ctx* ctx, const fhe_op* ops, int n, fhe_batch** out) {
+    return fhe_batch_create_ex(ctx, ops, n, FHE_BATCH_PERSISTENT, 0, out);
+}
+
+int fhe_batch_create_ex(const fhe_ctx* ctx, const fhe_op* ops, int n, int mode, size_t slot_bytes, fhe_batch** out) {
     FHE_CHECK(out != nullptr, "out is NULL");
     *out = nullptr;
     FHE_CHECK(ctx != nullptr, "ctx is NULL");
     FHE_CHECK(n >= 0 && (n == 0 || ops != nullptr), "bad op list");
+    FHE_CHECK(mode == FHE_BATCH_PERSISTENT || mode == FHE_BATCH_GROUPED, "unknown batch mode");
+    std::vector<int> persistent;  // operations for the persistent engine
     const int nmod = (int)ctx->mods.size();
     std::map<std::pair<uint32_t, int>, std::vector<RowRef>> rows;  // (logN, inverse) -> rows
     std::map<std::tuple<uint32_t, int, const uint32_t*>, std::vector<int>> hm;  // (logN, nl, evk) -> ops
@@ -127,9 +139,14 @@ int fhe_batch_create(const fhe_ctx* ctx, const fhe_op* ops, int n, fhe_batch** o
         FHE_CHECK(o.logN >= FHE_LOGN_MIN && o.logN <= ctx->logN_max, "op: logN out of range");
         FHE_CHECK(o.batch >= 0, "op: batch < 0");
         const size_t N = (size_t)1 << o.logN;
+        const bool pers = mode == FHE_BATCH_PERSISTENT && o.logN >= 14;
         if (o.kind == FHE_OPK_NTT_FWD || o.kind == FHE_OPK_NTT_INV) {
             FHE_CHECK(o.n_limbs >= 1 && o.first_limb >= 0 && o.first_limb + o.n_limbs <= nmod, "op: limb range");
             FHE_CHECK(o.batch == 0 || (o.data && al16(o.data)), "op: data NULL or misaligned");
+            if (pers) {
+                persistent.push_back(i);
+                continue;
+            }
             auto& v = rows[{o.logN, o.kind == FHE_OPK_NTT_INV ? 1 : 0}];
             for (int l = 0; l < o.n_limbs; ++l)
                 for (int bb = 0; bb < o.batch; ++bb)
@@ -139,7 +156,10 @@ int fhe_batch_create(const fhe_ctx* ctx, const fhe_op* ops, int n, fhe_batch** o
             FHE_CHECK(o.n_limbs >= 2 && o.n_limbs <= ctx->nq, "op: HMULT n_limbs out of [2, nq]");
             FHE_CHECK(o.batch == 0 || (o.a && o.b && o.evk && o.out && al16(o.a) && al16(o.b) && al16(o.out)),
                       "op: HMULT pointer NULL or misaligned");
-            if (o.batch > 0) hm[std::make_tuple(o.logN, o.n_limbs, o.evk)].push_back(i);
+            if (pers)
+                persistent.push_back(i);
+            else if (o.batch > 0)
+                hm[std::make_tuple(o.logN, o.n_limbs, o.evk)].push_back(i);
         } else {
             return set_error(FHE_EINVAL, "op: unknown kind");
         }
@@ -205,6 +225,14 @@ int fhe_batch_create(const fhe_ctx* ctx, const fhe_op* ops, int n, fhe_batch** o
         if ((rc = upload(b, &g.d_out, outs))) break;
         b->hm.push_back(g);
     }
+    if (rc == FHE_OK && !persistent.empty()) {
+        const size_t budget = slot_bytes ? slot_bytes : ((size_t)8 << 30);
+        rc = persist_create(ctx, ops, n, persistent, budget, &b->persist);
+        if (rc == FHE_OK) {
+            b->scratch_bytes = std::max(b->scratch_bytes, persist_scratch_bytes(b->persist));
+            b->n_launch += 2;
+        }
+    }
     if (rc != FHE_OK) {
         fhe_batch_destroy(b);
         return rc;
@@ -269,8 +297,15 @@ int fhe_batch_destroy(fhe_batch* b) {
     if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     for (void* v : b->allocs) cudaFree(v);
+    persist_destroy(b->persist);
     delete b;
     return FHE_OK;
+}
+
+int fhe_selftest_queue_timeout(const fhe_ctx* ctx, long long limit_cycles, void* stream) {
+    FHE_CHECK(ctx != nullptr, "ctx is NULL");
+    FHE_CHECK(limit_cycles > 0 && limit_cycles <= 4000000000LL, "limit_cycles out of (0, 4e9]");
+    return persist_selftest_timeout(ctx, limit_cycles, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -7,161 +7,23 @@
 // and grid.x strides over the B*N residues of that limb.
 #include <algorithm>
 
-#include "common.cuh"
+#include "ckks_kernels.cuh"
 
 namespace fhe {
 namespace {
 
-// Per-limb moduli with the constants of reduce_red: r32 = 2^32 mod q with its Shoup quotient,
-// m32 = floor(2^32 / q).
-struct ModVec {
-    uint32_t q[kMaxLimbs];
-    uint32_t r32[kMaxLimbs], r32s[kMaxLimbs], m32[kMaxLimbs];
-};
-
-ModVec modvec(const fhe_ctx* ctx, const int* mod_idx, int n) {
-    ModVec m;
-    for (int l = 0; l < n; ++l) {
-        const uint32_t q = ctx->mods[mod_idx[l]];
-        m.q[l] = q;
-        m.r32[l] = (uint32_t)((1ull << 32) % q);
-        m.r32s[l] = shoup_h(m.r32[l], q);
-        m.m32[l] = (uint32_t)((1ull << 32) / q);
-    }
-    return m;
+// ---- HM-1: tensor product (tensor_range in ckks_kernels.cuh), one limb per grid row
+__global__ void k_tensor(const TensorArgs t) {
+    tensor_range(t, blockIdx.y, blockIdx.x * (size_t)blockDim.x + threadIdx.x, t.L4, (size_t)gridDim.x * blockDim.x);
 }
 
-struct Red {
-    uint32_t q, r32, r32s, m32;
-};
-__device__ __forceinline__ Red red_of(const ModVec& m, int l) { return Red{m.q[l], m.r32[l], m.r32s[l], m.m32[l]}; }
-
-// x mod q for any x < 2^64 (q < 2^30): the high word times 2^32 mod q by Shoup's method and the
-// low word by a 32-bit Barrett step, each in [0, 2q), summed below 4q and corrected twice.
-__device__ __forceinline__ uint32_t reduce_red(uint64_t x, const Red& r) {
-    const uint32_t xl = (uint32_t)x;
-    const uint32_t t = mul_shoup_lazy((uint32_t)(x >> 32), r.r32, r.r32s, r.q);
-    const uint32_t u = xl - __umulhi(xl, r.m32) * r.q;
-    return csub(csub(t + u, 2 * r.q), r.q);
-}
-// v mod q for v < 2^32 (32-bit Barrett, one correction above [0, 2q)).
-__device__ __forceinline__ uint32_t reduce32(uint32_t v, const Red& r) {
-    return csub(v - __umulhi(v, r.m32) * r.q, r.q);
-}
-
-__device__ __forceinline__ uint4 ld4(const uint32_t* p, size_t i) {
-    return __ldg(reinterpret_cast<const uint4*>(p) + i);
-}
-__device__ __forceinline__ void st4(uint32_t* p, size_t i, uint4 v) {
-    reinterpret_cast<uint4*>(p)[i] = v;
-}
-__device__ __forceinline__ uint32_t get(const uint4& v, int k) {
-    return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
-}
-__device__ __forceinline__ void set(uint4& v, int k, uint32_t x) {
-    if (k == 0) v.x = x;
-    else if (k == 1) v.y = x;
-    else if (k == 2) v.z = x;
-    else v.w = x;
-}
-
-// ---- HM-1: tensor product (Hada-Mult + Ele-Add), d2 written twice (NTT form + copy for INTT)
-// dscale (nullable): limbs l < scale_lt write d0 and d1 multiplied by dscale[l] (Shoup pair).
-__global__ void k_tensor(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b,
-                         uint32_t* __restrict__ d0, uint32_t* __restrict__ d1,
-                         uint32_t* __restrict__ d2, uint32_t* __restrict__ d2c, size_t L4,
-                         size_t comp4, ModVec m, const uint2* __restrict__ dscale, int scale_lt) {
-    const int l = blockIdx.y;
-    const Red rd = red_of(m, l);
-    const bool scaled = dscale != nullptr && l < scale_lt;
-    const uint2 sc = scaled ? __ldg(&dscale[l]) : make_uint2(0, 0);
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < L4; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t idx = (size_t)l * L4 + i;
-        uint4 a0 = ld4(a, idx), a1 = ld4(a, comp4 + idx), b0 = ld4(b, idx), b1 = ld4(b, comp4 + idx);
-        uint4 r0, r1, r2;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            uint32_t x0 = get(a0, k), x1 = get(a1, k), y0 = get(b0, k), y1 = get(b1, k);
-            uint32_t v0 = reduce_red((uint64_t)x0 * y0, rd), v1 = reduce_red((uint64_t)x0 * y1 + (uint64_t)x1 * y0, rd);
-            if (scaled) {
-                v0 = mul_shoup(v0, sc.x, sc.y, m.q[l]);
-                v1 = mul_shoup(v1, sc.x, sc.y, m.q[l]);
-            }
-            set(r0, k, v0);
-            set(r1, k, v1);
-            set(r2, k, reduce_red((uint64_t)x1 * y1, rd));
-        }
-        st4(d0, idx, r0);
-        st4(d1, idx, r1);
-        st4(d2, idx, r2);
-        st4(d2c, idx, r2);
-    }
-}
-
-// ---- KS-2 / KS-5: Conv (fast basis conversion, Sec. IV-A)
-//   y_i = [x_i * (B/b_i)^-1]_{b_i};  out_t = sum_i y_i * [B/b_i]_t  mod t
-struct ConvArgs {
-    const uint32_t* src;
-    size_t src_stride;  // elements between source limbs
-    int nsrc;
-    uint32_t src_q[16];
-    uint2 hat_inv[16];
-    const uint32_t* hat_mod;  // [nsrc][nmod]
-    int nmod;
-    uint32_t* dst;
-    size_t dst_stride;
-    int ndst;
-    uint8_t dst_mod[kMaxLimbs];
-    ModVec dm;
-    size_t L4;  // residues per limb / 4
-    // destinations t < scale_lt come out multiplied by s1[t] s2[t] (Shoup pairs mod q_t, folded
-    // into the constants [B/b_i]_t); 0 leaves every destination unscaled
-    const uint2* s1;
-    const uint2* s2;
-    int scale_lt;
-};
-
-// NS = number of source limbs (a compile-time constant so no issue slot is spent on
-// predicated-off source terms).
+// ---- KS-2 / KS-5: Conv (conv_range in ckks_kernels.cuh)
 template <int NS>
 __global__ void __launch_bounds__(256) k_conv(const ConvArgs a) {
     extern __shared__ uint32_t s_hat[];  // [nsrc][ndst]
-    for (int k = threadIdx.x; k < NS * a.ndst; k += blockDim.x) {
-        int i = k / a.ndst, t = k % a.ndst;
-        uint32_t h = a.hat_mod[(size_t)i * a.nmod + a.dst_mod[t]];
-        if (t < a.scale_lt) {
-            const uint32_t q = a.dm.q[t];
-            const uint2 u = a.s1[a.dst_mod[t]], v = a.s2[a.dst_mod[t]];
-            h = mul_shoup(mul_shoup(h, u.x, u.y, q), v.x, v.y, q);
-        }
-        s_hat[k] = h;
-    }
+    conv_load_hat(a, NS, s_hat);
     __syncthreads();
-    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < a.L4; n += (size_t)gridDim.x * blockDim.x) {
-        uint4 y[NS];
-#pragma unroll
-        for (int i = 0; i < NS; ++i) {
-            uint4 x = ld4(a.src, i * (a.src_stride / 4) + n);
-            const uint32_t b = a.src_q[i];
-            const uint2 h = a.hat_inv[i];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) set(y[i], k, mul_shoup(get(x, k), h.x, h.y, b));
-        }
-        for (int t = 0; t < a.ndst; ++t) {
-            uint64_t acc[4] = {0, 0, 0, 0};
-#pragma unroll
-            for (int i = 0; i < NS; ++i) {
-                const uint64_t h = s_hat[i * a.ndst + t];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) acc[k] += (uint64_t)get(y[i], k) * h;
-            }
-            uint4 r;
-            const Red rd = red_of(a.dm, t);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) set(r, k, reduce_red(acc[k], rd));
-            st4(a.dst, t * (a.dst_stride / 4) + n, r);
-        }
-    }
+    conv_range<NS, false>(a, s_hat, blockIdx.x * (size_t)blockDim.x + threadIdx.x, a.L4, (size_t)gridDim.x * blockDim.x);
 }
 
 int launch_conv(const ConvArgs& ca, dim3 grid, size_t smem, cudaStream_t st) {
@@ -204,70 +66,9 @@ int run_conv(const fhe_ctx* ctx, const ConvArgs& ca, const ConvTable& ct, dim3 g
     return launch_conv(ca, grid, smem, st);
 }
 
-// ---- KS-4: inner product with the evaluation key (Hada-Mult + Ele-Add), all slices at once:
-//   ks_c[t] = sum_j d~_j[t] * evk_{j,c}[t],  d~_j[t] = d2[t] on slice j's own limbs, else the
-//   NTT of slice j's ModUp output. One pass reads every slice and writes ks0, ks1 once.
-struct IpArgs {
-    const uint32_t* d2;   // (nl, B, N) NTT domain
-    const uint32_t* tmp;  // (dnum, ext, B, N): slice j's converted limbs at j*ext (q limbs outside the slice, then P)
-    const uint32_t* evk;  // (dnum_ctx, 2, nmod, N)
-    uint32_t* ks;         // (2, ext, B, N)
-    int nl, alpha, dnum, ext, nq, nmod;
-    size_t L4, N4;        // residues per limb / 4, N / 4
-    ModVec m;             // per extended limb t < ext
-    const uint2* s1;      // limbs t < scale_lt: outputs multiplied by s1[t] s2[t] (Shoup pairs)
-    const uint2* s2;
-    int scale_lt;
-};
-
+// ---- KS-4: inner product with the evaluation key (ip_range in ckks_kernels.cuh)
 __global__ void k_inner_product(const IpArgs a) {
-    const int t = blockIdx.y;
-    const Red rd = red_of(a.m, t);
-    const int mod = t < a.nl ? t : a.nq + (t - a.nl);
-    const size_t limb = a.L4 * 4;
-    uint32_t* k0 = a.ks + (size_t)t * limb;
-    uint32_t* k1 = a.ks + (size_t)(a.ext + t) * limb;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < a.L4; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t n4 = i % a.N4;
-        // products < 2^60: up to 15 of them accumulate exactly in 64 bits, then one reduction
-        uint64_t r0[4] = {0, 0, 0, 0}, r1[4] = {0, 0, 0, 0};
-        for (int j = 0; j < a.dnum; ++j) {
-            if (j > 0 && j % 15 == 0) {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    r0[k] = reduce_red(r0[k], rd);
-                    r1[k] = reduce_red(r1[k], rd);
-                }
-            }
-            const int lo = j * a.alpha, hi = min(a.nl, lo + a.alpha);
-            const uint32_t* src = (t >= lo && t < hi)
-                                      ? a.d2 + (size_t)t * limb
-                                      : a.tmp + ((size_t)j * a.ext + (t < lo ? t : t - (hi - lo))) * limb;
-            const uint4 x = ld4(src, i);
-            const uint4 w0 = ld4(a.evk + ((size_t)(j * 2 + 0) * a.nmod + mod) * a.N4 * 4, n4);
-            const uint4 w1 = ld4(a.evk + ((size_t)(j * 2 + 1) * a.nmod + mod) * a.N4 * 4, n4);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                r0[k] += (uint64_t)get(x, k) * get(w0, k);
-                r1[k] += (uint64_t)get(x, k) * get(w1, k);
-            }
-        }
-        uint4 o0 = make_uint4(reduce_red(r0[0], rd), reduce_red(r0[1], rd), reduce_red(r0[2], rd),
-                              reduce_red(r0[3], rd));
-        uint4 o1 = make_uint4(reduce_red(r1[0], rd), reduce_red(r1[1], rd), reduce_red(r1[2], rd),
-                              reduce_red(r1[3], rd));
-        if (t < a.scale_lt) {
-            const uint32_t q = a.m.q[t];
-            const uint2 u = a.s1[t], v = a.s2[t];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                set(o0, k, mul_shoup(mul_shoup(get(o0, k), u.x, u.y, q), v.x, v.y, q));
-                set(o1, k, mul_shoup(mul_shoup(get(o1, k), u.x, u.y, q), v.x, v.y, q));
-            }
-        }
-        st4(k0, i, o0);
-        st4(k1, i, o1);
-    }
+    ip_range<false>(a, blockIdx.y, blockIdx.x * (size_t)blockDim.x + threadIdx.x, a.L4, (size_t)gridDim.x * blockDim.x);
 }
 
 // ---- KS-5 tail + HM-2: out_c[i] (+)= (ks_c[i] - y_c[i]) * [P^-1]_{q_i}
@@ -357,33 +158,17 @@ __global__ void k_rescale_final(const uint32_t* __restrict__ ct, const uint32_t*
 // ks'_i = ks_i P^-1 q_l^-1 and ModDown's Conv y'_i = y_i P^-1 q_l^-1, so with
 // z'_i = y'_i + x_i q_l^-1 the output is ks'_i + d'_i - NTT(z'_i), additions only.
 //
-// u = ks_l P^-1 + d_l, the last limb of both components without the y term (NTT domain).
-__global__ void k_relin_last(const uint32_t* __restrict__ d, const uint32_t* __restrict__ ks,
-                             uint32_t* __restrict__ last, uint2 pinv, uint32_t q, int nl, int ext, size_t L4) {
-    const int c = blockIdx.y, l = nl - 1;
-    const uint32_t* dp = d + ((size_t)c * nl + l) * L4 * 4;
-    const uint32_t* kp = ks + ((size_t)c * ext + l) * L4 * 4;
-    uint32_t* op = last + (size_t)c * L4 * 4;
-    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < L4; n += (size_t)gridDim.x * blockDim.x) {
-        uint4 dv = ld4(dp, n), kv = ld4(kp, n), r;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) set(r, k, csub(mul_shoup(get(kv, k), pinv.x, pinv.y, q) + get(dv, k), q));
-        st4(op, n, r);
-    }
+// u = ks_l P^-1 + d_l, the last limb of both components without the y term (NTT domain), and
+// last = INTT(u) - y_l P^-1 mod q_l: the last relinearised limb in the coefficient domain
+// (relin_last_range / last_fix_range in ckks_kernels.cuh).
+__global__ void k_relin_last(const LastArgs a) {
+    relin_last_range<false>(a, blockIdx.y, blockIdx.x * (size_t)blockDim.x + threadIdx.x, a.L4,
+                            (size_t)gridDim.x * blockDim.x);
 }
 
-// last = INTT(u) - y_l P^-1 mod q_l: the last relinearised limb in the coefficient domain.
-__global__ void k_last_fix(const uint32_t* __restrict__ y, uint32_t* __restrict__ last, uint2 pinv, uint32_t q,
-                           int nl, size_t L4) {
-    const int c = blockIdx.y, l = nl - 1;
-    const uint32_t* yp = y + ((size_t)c * nl + l) * L4 * 4;
-    uint32_t* op = last + (size_t)c * L4 * 4;
-    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < L4; n += (size_t)gridDim.x * blockDim.x) {
-        uint4 yv = ld4(yp, n), lv = ld4(op, n), r;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) set(r, k, csub(get(lv, k) + q - mul_shoup(get(yv, k), pinv.x, pinv.y, q), q));
-        st4(op, n, r);
-    }
+__global__ void k_last_fix(const LastArgs a) {
+    last_fix_range<false>(a, blockIdx.y, blockIdx.x * (size_t)blockDim.x + threadIdx.x, a.L4,
+                          (size_t)gridDim.x * blockDim.x);
 }
 
 // z'_i = y'_i + [last]_centred q_l^-1 mod q_i (coefficient domain), i < l.
@@ -668,8 +453,8 @@ int hmult_relin_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const
     uint32_t* ks_scratch = d2 + (size_t)nl * limb;  // begins with d2c
     int qidx[kMaxLimbs];
     for (int i = 0; i < nl; ++i) qidx[i] = i;
-    k_tensor<<<stream_grid(ctx, L4, nl), 256, 0, st>>>(a, b, out, out + (size_t)nl * limb, d2, ks_scratch, L4,
-                                                     (size_t)nl * L4, modvec(ctx, qidx, nl), nullptr, 0);
+    k_tensor<<<stream_grid(ctx, L4, nl), 256, 0, st>>>(TensorArgs{a, b, out, out + (size_t)nl * limb, d2, ks_scratch,
+                                                                L4, (size_t)nl * L4, modvec(ctx, qidx, nl), nullptr, 0});
     FHE_CUDA_TRY(cudaGetLastError());
     return keyswitch_impl(ctx, logN, nl, batch, d2, evk, out, 1, ks_scratch, true, st, ns);
 }
@@ -697,20 +482,21 @@ int hmult_fused(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint
     // P^-1 q_l^-1 on ks and y (folded into HBM-bound passes and into Conv's constants), so that
     // the combine below needs no multiplication
     const uint2* qlinv = ctx->ql_inv + (size_t)(nl - 1) * ctx->nq;
-    k_tensor<<<stream_grid(ctx, L4, nl), 256, 0, st>>>(a, b, dd, dd + (size_t)nl * limb, d2, ksx, L4,
-                                                     (size_t)nl * L4, modvec(ctx, qidx, nl), qlinv, nl - 1);
+    k_tensor<<<stream_grid(ctx, L4, nl), 256, 0, st>>>(TensorArgs{a, b, dd, dd + (size_t)nl * limb, d2, ksx, L4,
+                                                                (size_t)nl * L4, modvec(ctx, qidx, nl), qlinv, nl - 1});
     FHE_CUDA_TRY(cudaGetLastError());
     int rc = keyswitch_impl(ctx, logN, nl, batch, d2, evk, nullptr, 0, ksx, true, st, ns, nl - 1);
     if (rc) return rc;
     const uint32_t ql = ctx->mods[nl - 1];
     const uint2 pinv_l = ctx->p_inv_h[nl - 1];
-    k_relin_last<<<stream_grid(ctx, L4, 2), 256, 0, st>>>(dd, ks, last, pinv_l, ql, nl, ext, L4);
+    const LastArgs la{dd, ks, y, last, pinv_l, ql, nl, ext, L4};
+    k_relin_last<<<stream_grid(ctx, L4, 2), 256, 0, st>>>(la);
     FHE_CUDA_TRY(cudaGetLastError());
     LimbMap lm;
     lm.mod[0] = lm.mod[1] = (uint8_t)(nl - 1);
     lm.q[0] = lm.q[1] = ql;
     if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, true, last, 2, batch, lm, st, ns))) return rc;
-    k_last_fix<<<stream_grid(ctx, L4, 2), 256, 0, st>>>(y, last, pinv_l, ql, nl, L4);
+    k_last_fix<<<stream_grid(ctx, L4, 2), 256, 0, st>>>(la);
     FHE_CUDA_TRY(cudaGetLastError());
     const int nout = nl - 1;
     LimbMap qm2;
@@ -911,7 +697,7 @@ size_t scratch_limbs(const fhe_ctx* ctx, int op, int nl) {
 // The two-pass NTT region of an operation's caller scratch (after the operation's limbs).
 NttScratch op_ntt_scratch(const fhe_ctx* ctx, int op, uint32_t logN, int nl, int batch, void* scratch) {
     NttScratch s;
-    s.bytes = ntt_region_bytes(logN, ntt_rows(ctx, op, nl) * batch);
+    s.bytes = op_region_bytes(ctx, logN, ntt_rows(ctx, op, nl) * batch);
     if (s.bytes) s.p = (uint32_t*)((uint8_t*)scratch + scratch_limbs(ctx, op, nl) * ((size_t)batch << logN) * 4);
     return s;
 }
@@ -931,7 +717,7 @@ size_t fhe_scratch_bytes(const fhe_ctx* ctx, int op, uint32_t logN, int n_limbs,
     const size_t limbs = scratch_limbs(ctx, op, n_limbs);
     if (limbs == 0) return 0;
     // the operation's limbs, then the two-pass NTT region of its NTT calls
-    return limbs * ((size_t)batch << logN) * 4 + ntt_region_bytes(logN, ntt_rows(ctx, op, n_limbs) * batch);
+    return limbs * ((size_t)batch << logN) * 4 + op_region_bytes(ctx, logN, ntt_rows(ctx, op, n_limbs) * batch);
 }
 
 int fhe_keyswitch(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const uint32_t* d2,

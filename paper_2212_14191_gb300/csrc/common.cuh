@@ -121,7 +121,7 @@ struct fhe_ctx {
     int device = 0;
     int num_sms = 0;
     int* d_status = nullptr;  // device error word written by kernels (FHE_ETIMEOUT, ...)
-    void* tc_planes = nullptr;  // tensor-core path scratch: digit planes between the two GEMMs
+    void* tc_planes = nullptr;  // tensor-core digit planes of fhe_ntt_fwd / fhe_ntt_inv (kTcPlaneBytes)
     uint32_t* ntt_temp = nullptr;  // two-pass plain NTT scratch (kNttTempBytes, stays in L2)
     uint32_t* d_mods = nullptr;  // device copy of `mods`
 };
@@ -153,6 +153,17 @@ struct NttScratch {
 };
 // Bytes of that region for NTT calls of up to `rows` rows at 2^logN (0 below 2^15).
 size_t ntt_region_bytes(uint32_t logN, size_t rows);
+// Digit-plane buffer of the tensor-core NTT between its two GEMMs: the context's own buffer
+// (fhe_ntt_fwd / fhe_ntt_inv), and the most an operation's scratch region provides for it.
+// 64 MiB holds the planes of 2 limbs x 64 polynomials at N = 2^16, so that a chunk's planes
+// can stay in the 129 MB L2 between the two GEMMs.
+#ifndef FHE_TC_PLANE_MIB
+#define FHE_TC_PLANE_MIB 64
+#endif
+constexpr size_t kTcPlaneBytes = (size_t)FHE_TC_PLANE_MIB << 20;
+// The NTT region of a CKKS operation's scratch for NTT calls of up to `rows` rows on this
+// context: the two-pass region, and on a tensor-core context room for its digit planes.
+size_t op_region_bytes(const fhe_ctx* ctx, uint32_t logN, size_t rows);
 
 // Plain-path NTT over rows listed in a device table (operation-level batching of rows
 // that live in different buffers).
@@ -189,9 +200,10 @@ int ntt_u32_l2_tail(const fhe_ctx* ctx, uint32_t logN, int rows, int batch, cons
 // Plain-path batched NTT over `n_limbs` limbs whose moduli are map.mod[l].
 int ntt_u32(const fhe_ctx* ctx, uint32_t logN, bool inverse, uint32_t* d, int n_limbs,
             int batch, const LimbMap& map, cudaStream_t stream, NttScratch scr = NttScratch());
-// Tensor-core path.
+// Tensor-core path; its digit planes go to scr (at least 8 N bytes) when given, else to the
+// context's own buffer.
 int ntt_tc(const fhe_ctx* ctx, uint32_t logN, bool inverse, uint32_t* d, int n_limbs,
-           int batch, const LimbMap& map, cudaStream_t stream);
+           int batch, const LimbMap& map, cudaStream_t stream, NttScratch scr = NttScratch());
 int build_tc_tables(fhe_ctx* ctx, uint32_t logN);
 int build_ntt_tables(fhe_ctx* ctx, uint32_t logN);
 

@@ -82,7 +82,7 @@ LimbMap contiguous_map(const fhe_ctx* ctx, int first, int n) {
 int ntt_any(const fhe_ctx* ctx, int path, uint32_t logN, bool inverse, uint32_t* d, int n_limbs,
             int batch, const LimbMap& map, cudaStream_t stream, NttScratch scr) {
     if (path == FHE_NTT_DEFAULT) path = ctx->default_path;
-    if (path == FHE_NTT_TC) return ntt_tc(ctx, logN, inverse, d, n_limbs, batch, map, stream);
+    if (path == FHE_NTT_TC) return ntt_tc(ctx, logN, inverse, d, n_limbs, batch, map, stream, scr);
     return ntt_u32(ctx, logN, inverse, d, n_limbs, batch, map, stream, scr);
 }
 
@@ -90,6 +90,16 @@ size_t ntt_region_bytes(uint32_t logN, size_t rows) {
     if (logN < 15 || rows == 0) return 0;
     const size_t b = rows * (((size_t)4 << logN) + 4);  // residues and a completion counter per row
     return b < kNttTempBytes ? b : kNttTempBytes;
+}
+
+size_t op_region_bytes(const fhe_ctx* ctx, uint32_t logN, size_t rows) {
+    size_t b = ntt_region_bytes(logN, rows);
+    if (ctx->default_path == FHE_NTT_TC && rows > 0) {
+        // the tensor-core path's digit planes: 8 bytes per residue of a chunk of rows
+        const size_t tc = std::min(rows * ((size_t)8 << logN), kTcPlaneBytes);
+        b = std::max(b, tc);
+    }
+    return b;
 }
 
 static int build_conv(fhe_ctx* ctx, const std::vector<int>& src, ConvTable* out) {

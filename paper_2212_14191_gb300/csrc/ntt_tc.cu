@@ -24,6 +24,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -35,7 +36,6 @@ namespace {
 constexpr int kTileM = 128;
 constexpr int kChunk = 64;             // K' elements (fp16) per pipeline stage = 128 bytes
 constexpr int kMaxChunkLimbs = 64;
-constexpr size_t kPlaneBytes = 256ull << 20;  // digit planes between the two GEMMs
 
 struct GemmArgs {
     int rows;     // polynomials per limb in this launch
@@ -549,7 +549,7 @@ int build_tc_tables(fhe_ctx* ctx, uint32_t logN) {
     t.n2 = n2;
     int rc;
     if (!ctx->tc_planes) {
-        if ((rc = dev_alloc(ctx, (uint8_t**)&ctx->tc_planes, kPlaneBytes))) return rc;
+        if ((rc = dev_alloc(ctx, (uint8_t**)&ctx->tc_planes, kTcPlaneBytes))) return rc;
     }
     for (int kind = 0; kind < 4; ++kind) {
         const int cols = (kind == 0 || kind == 3) ? n1 : n2;
@@ -607,7 +607,7 @@ int build_tc_tables(fhe_ctx* ctx, uint32_t logN) {
     if ((rc = dev_upload(ctx, &t.tw_fwd, twf))) return rc;
     if ((rc = dev_upload(ctx, &t.tw_inv, twi))) return rc;
     // second-GEMM operand maps over the plane buffer: [rows][4X] for X = n1 and X = n2
-    const uint64_t cap_n1 = kPlaneBytes / 2 / (4ull * n1), cap_n2 = kPlaneBytes / 2 / (4ull * n2);
+    const uint64_t cap_n1 = kTcPlaneBytes / 2 / (4ull * n1), cap_n2 = kTcPlaneBytes / 2 / (4ull * n2);
     if ((rc = make_map(&t.map_a[0], ctx->tc_planes, 4ull * n1, cap_n1, kTileM))) return rc;
     if ((rc = make_map(&t.map_a[1], ctx->tc_planes, 4ull * n2, cap_n2, kTileM))) return rc;
     t.built = true;
@@ -645,7 +645,7 @@ int launch_gemm_fused(const fhe_ctx* ctx, const CUtensorMap& ms, const CUtensorM
 }
 
 int ntt_tc(const fhe_ctx* cctx, uint32_t logN, bool inverse, uint32_t* d, int n_limbs, int batch,
-           const LimbMap& map, cudaStream_t st) {
+           const LimbMap& map, cudaStream_t st, NttScratch scr) {
     fhe_ctx* ctx = const_cast<fhe_ctx*>(cctx);
     {
         std::lock_guard<std::mutex> lock(g_tc_mu);
@@ -659,7 +659,22 @@ int ntt_tc(const fhe_ctx* cctx, uint32_t logN, bool inverse, uint32_t* d, int n_
     const int X1 = inverse ? n2 : n1, Y1 = inverse ? n1 : n2;
     const int cols1 = inverse ? n2 : n1, cols2 = inverse ? n1 : n2;
     const int kind1 = inverse ? 2 : 0, kind2 = inverse ? 3 : 1;
-    const size_t cap_polys = kPlaneBytes / (N * 8);  // fp16 x 4 digits per residue
+    // the digit planes: the caller's region when given (calls may then overlap on other
+    // streams), else the context's buffer, with the second GEMM's operand map over it
+    uint2* planes = (uint2*)ctx->tc_planes;
+    size_t plane_bytes = kTcPlaneBytes;
+    CUtensorMap own_a;
+    const CUtensorMap* a2 = &t.map_a[inverse ? 0 : 1];
+    if (scr.p) {
+        plane_bytes = std::min(scr.bytes, kTcPlaneBytes);
+        if (plane_bytes < N * 8) return set_error(FHE_EINVAL, "tensor-core NTT: scratch region below 8 N bytes");
+        planes = (uint2*)scr.p;
+        const uint64_t inner = 4ull * (inverse ? n1 : n2);
+        int rc0 = make_map(&own_a, planes, inner, plane_bytes / 2 / inner, kTileM);
+        if (rc0) return rc0;
+        a2 = &own_a;
+    }
+    const size_t cap_polys = plane_bytes / (N * 8);  // fp16 x 4 digits per residue
     int nb = batch, nlc = (int)(cap_polys / batch);
     if (nlc < 1) {
         nlc = 1;
@@ -697,7 +712,7 @@ int ntt_tc(const fhe_ctx* cctx, uint32_t logN, bool inverse, uint32_t* d, int n_
             g.cols = cols1;
             g.mode = 1;
             g.tw = inverse ? t.tw_inv : t.tw_fwd;
-            g.planes = (uint2*)ctx->tc_planes;
+            g.planes = planes;
             rc = cols1 >= 64 ? launch_gemm_fused<64>(ctx, src, t.map_b[kind1], g, nl, st)
                              : launch_gemm_fused<32>(ctx, src, t.map_b[kind1], g, nl, st);
             if (rc) return rc;
@@ -708,9 +723,8 @@ int ntt_tc(const fhe_ctx* cctx, uint32_t logN, bool inverse, uint32_t* d, int n_
             g.mode = 2;
             g.out = base;
             g.out_limb_stride = (size_t)batch * N;
-            const CUtensorMap& a2 = t.map_a[inverse ? 0 : 1];
-            rc = cols2 >= 64 ? launch_gemm<64>(ctx, a2, t.map_b[kind2], g, nl, st)
-                             : launch_gemm<32>(ctx, a2, t.map_b[kind2], g, nl, st);
+            rc = cols2 >= 64 ? launch_gemm<64>(ctx, *a2, t.map_b[kind2], g, nl, st)
+                             : launch_gemm<32>(ctx, *a2, t.map_b[kind2], g, nl, st);
             if (rc) return rc;
         }
     }

@@ -35,6 +35,7 @@ _i = ctypes.c_int
 _sz = ctypes.c_size_t
 
 FHE_OPK_NTT_FWD, FHE_OPK_NTT_INV, FHE_OPK_HMULT = 1, 2, 3
+FHE_BATCH_PERSISTENT, FHE_BATCH_GROUPED = 0, 1
 
 
 class FheOp(ctypes.Structure):
@@ -72,6 +73,8 @@ _SIGS = {
     "fhe_autotune_ntt": (_i, [_vp, _u32, _vp, _i, _i, _i, ctypes.POINTER(ctypes.c_float), _vp]),
     "fhe_last_error": (_i, [ctypes.c_char_p, _sz]),
     "fhe_batch_create": (_i, [_vp, ctypes.POINTER(FheOp), _i, ctypes.POINTER(_vp)]),
+    "fhe_batch_create_ex": (_i, [_vp, ctypes.POINTER(FheOp), _i, _i, _sz, ctypes.POINTER(_vp)]),
+    "fhe_selftest_queue_timeout": (_i, [_vp, ctypes.c_longlong, _vp]),
     "fhe_batch_scratch_bytes": (_sz, [_vp]),
     "fhe_batch_run": (_i, [_vp, _vp, _sz, _vp]),
     "fhe_batch_capture": (_i, [_vp, _vp, _sz]),
@@ -235,6 +238,17 @@ def fhe_batch_create(ctx, ops):
     h = _vp()
     _check(_lib.fhe_batch_create(ctx, arr, len(ops), ctypes.byref(h)))
     return h.value
+
+
+def fhe_batch_create_ex(ctx, ops, mode=FHE_BATCH_PERSISTENT, slot_bytes=0):
+    arr = (FheOp * max(1, len(ops)))(*ops)
+    h = _vp()
+    _check(_lib.fhe_batch_create_ex(ctx, arr, len(ops), mode, slot_bytes, ctypes.byref(h)))
+    return h.value
+
+
+def fhe_selftest_queue_timeout(ctx, limit_cycles, stream=0):
+    return _check(_lib.fhe_selftest_queue_timeout(ctx, limit_cycles, stream))
 
 
 def fhe_batch_scratch_bytes(batch):

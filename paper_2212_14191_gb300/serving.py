@@ -60,10 +60,12 @@ def _op_code(kind):
 
 class Server:
     def __init__(self, contexts, evks, budget_bytes, n_streams=4, max_batch=16, stall_s=60.0,
-                 admit_timeout_s=None):
+                 admit_timeout_s=None, keep_results=True):
         """contexts: {logN: fhe.Context}; evks: {logN: int32 CUDA tensor (dnum, 2, nq+np, N)}.
         admit_timeout_s: None waits for memory indefinitely; otherwise a request that cannot be
-        admitted within this many seconds of its arrival is rejected."""
+        admitted within this many seconds of its arrival is rejected.
+        keep_results: False drops each batch's output once it completes (r.out stays None), for
+        long load measurements whose results are not read."""
         self.ctx = contexts
         self.evk = evks
         self.budget = budget_bytes
@@ -71,6 +73,7 @@ class Server:
         self.max_batch = max_batch
         self.stall_s = stall_s
         self.admit_timeout_s = admit_timeout_s
+        self.keep_results = keep_results
         self._ready = None   # event on the caller's stream at the start of run()
 
     def check_device(self):
@@ -124,8 +127,9 @@ class Server:
                                   out.data_ptr(), scratch.data_ptr(), nbytes, sh)
             ev = torch.cuda.Event()
             ev.record(stream)
-        for j, r in enumerate(reqs):
-            r.out = out[:, :, j:j + 1]
+        if self.keep_results:
+            for j, r in enumerate(reqs):
+                r.out = out[:, :, j:j + 1]
         return {"reqs": reqs, "event": ev, "keep": (ins, out, scratch), "stream": stream}
 
     def run(self, requests, clock=time.perf_counter):

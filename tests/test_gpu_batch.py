@@ -1,6 +1,8 @@
 """Operation-level batching: a plan of mixed NTT / INTT / HMULT operations of uneven ring
 degree and level gives exactly the results of the single-operation calls, eagerly and when
-replayed as one CUDA graph."""
+replayed as one CUDA graph, in both plan modes (the persistent launch with its device work
+queue, and the grouped launches); the persistent kernel's bounded dependency wait reports an
+expired wait without hanging."""
 import numpy as np
 import pytest
 
@@ -88,13 +90,24 @@ def reset_inputs(fhe, keep):
             k[5].copy_(fhe.to_device(k[6]))
 
 
-def test_batch_equals_single_calls(fhe):
+MODES = ["persistent", "grouped"]
+
+
+def create(fhe, ctx, ops, mode, slot_bytes=0):
+    m = fhe.FHE_BATCH_PERSISTENT if mode == "persistent" else fhe.FHE_BATCH_GROUPED
+    return fhe.fhe_batch_create_ex(ctx.handle, ops, m, slot_bytes)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_batch_equals_single_calls(fhe, mode):
+    """N = 2^12..2^14: in persistent mode the 2^14 transforms run in the persistent launch and
+    the smaller operations in grouped launches before it, in one plan."""
     import torch
     qs, ps = P.default_moduli(8, 4)
     ctx = fhe.Context(14, qs, ps, alpha=4)
     ops, keep = make_ops(fhe, qs, ps, 7)
     want = reference_results(fhe, ctx, keep)
-    plan = fhe.fhe_batch_create(ctx.handle, ops)
+    plan = create(fhe, ctx, ops, mode)
     nbytes = fhe.fhe_batch_scratch_bytes(plan)
     scratch = torch.empty(max(4, nbytes // 4 + 4), dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
@@ -167,7 +180,8 @@ def test_batch_rejects_bad_ops(fhe):
     ctx.close()
 
 
-def test_batch_full_size_ring_degrees(fhe):
+@pytest.mark.parametrize("mode", MODES)
+def test_batch_full_size_ring_degrees(fhe, mode):
     """A plan at the uneven-batch workload's sizes: NTT and INTT rows at N = 2^15 and 2^16 with
     24 to 44 limbs (the two-pass row-table kernels) and HMULT groups at 2^15 and 2^16 with 24,
     36 and 44 limbs (3, 5 and 6 key-switching slices; one group gathers two operations). Every
@@ -203,7 +217,7 @@ def test_batch_full_size_ring_degrees(fhe):
                              b=b.data_ptr(), evk=evks[lg].data_ptr(), out=out.data_ptr()))
         keep.append(("hmult", lg, nl, batch, a, b, evks[lg], out))
     want = reference_results(fhe, ctx, keep)
-    plan = fhe.fhe_batch_create(ctx.handle, ops)
+    plan = create(fhe, ctx, ops, mode)
     nbytes = fhe.fhe_batch_scratch_bytes(plan)
     scratch = torch.empty(max(4, nbytes // 4 + 4), dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
@@ -234,5 +248,107 @@ def test_batch_full_size_ring_degrees(fhe):
     for i, (w, g) in enumerate(zip(want, batch_results(fhe, keep))):
         assert (w == g).all(), i
     fhe.fhe_device_status(ctx.handle, 1)
+    fhe.fhe_batch_destroy(plan)
+    ctx.close()
+
+
+@pytest.mark.parametrize("slot_bytes", [1, 0])
+def test_persistent_hmult_slots(fhe, slot_bytes):
+    """Persistent mode with HMULTs at N = 2^14, 2^15 and 2^16 (3 to 24 limbs, batches of one and
+    two ciphertexts) between NTT and INTT operations. slot_bytes = 1 leaves one scratch slot, so
+    every HMULT waits for the one before it (the chained dependency); 0 gives each HMULT its own
+    slot. Every result equals the single call, on the eager run and on two graph replays with
+    the inputs restored in between; one HMULT per ring degree is compared with the oracle."""
+    import torch
+    qs, ps = P.default_moduli(24, 8)
+    mods = qs + ps
+    ctx = fhe.Context(16, qs, ps, alpha=8)
+    evk_h, evks, prm = {}, {}, {}
+    for lg in (14, 15, 16):
+        n = 1 << lg
+        prm[lg] = C.Params(n, qs, ps, alpha=8)
+        dn = prm[lg].dnum(len(qs))
+        evk_h[lg] = I.uniform_residues(1200 + lg, mods, 2 * dn, n).reshape(len(mods), dn, 2, n).transpose(1, 2, 0, 3).copy()
+        evks[lg] = fhe.to_device(evk_h[lg])
+    ops, keep = [], []
+    specs = [("hmult", 16, 24, 1), ("ntt", 15, 0, 12, 2, fhe.FHE_OPK_NTT_FWD), ("hmult", 14, 3, 2),
+             ("hmult", 15, 17, 1), ("ntt", 14, 3, 20, 1, fhe.FHE_OPK_NTT_INV), ("hmult", 16, 9, 2),
+             ("hmult", 14, 24, 1), ("ntt", 16, 30, 2, 1, fhe.FHE_OPK_NTT_INV)]
+    for i, sp in enumerate(specs):
+        if sp[0] == "hmult":
+            _, lg, nl, batch = sp
+            n = 1 << lg
+            a = fhe.to_device(I.uniform_residues(1300 + i, qs[:nl], 2 * batch, n).reshape(nl, 2, batch, n).transpose(1, 0, 2, 3).copy())
+            b = fhe.to_device(I.uniform_residues(1400 + i, qs[:nl], 2 * batch, n).reshape(nl, 2, batch, n).transpose(1, 0, 2, 3).copy())
+            out = torch.full((2, nl - 1, batch, n), -1, dtype=torch.int32, device="cuda")
+            ops.append(fhe.FheOp(kind=fhe.FHE_OPK_HMULT, logN=lg, n_limbs=nl, batch=batch, a=a.data_ptr(),
+                                 b=b.data_ptr(), evk=evks[lg].data_ptr(), out=out.data_ptr()))
+            keep.append(("hmult", lg, nl, batch, a, b, evks[lg], out))
+        else:
+            _, lg, first, nl, batch, kind = sp
+            x = I.uniform_residues(1500 + i, mods[first:first + nl], batch, 1 << lg)
+            d = fhe.to_device(x)
+            ops.append(fhe.FheOp(kind=kind, logN=lg, first_limb=first, n_limbs=nl, batch=batch, data=d.data_ptr()))
+            keep.append(("ntt", lg, first, nl, batch, d, x, kind))
+    want = reference_results(fhe, ctx, keep)
+    plan = create(fhe, ctx, ops, "persistent", slot_bytes)
+    nbytes = fhe.fhe_batch_scratch_bytes(plan)
+    scratch = torch.full((nbytes // 4 + 4,), -1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    fhe.fhe_batch_run(plan, scratch.data_ptr(), nbytes, stream)
+    torch.cuda.synchronize()
+    fhe.fhe_device_status(ctx.handle, 1)
+    got = batch_results(fhe, keep)
+    for i, (w, g) in enumerate(zip(want, got)):
+        assert (w == g).all(), (i, specs[i])
+    seen = set()
+    for k, g in zip(keep, got):
+        if k[0] == "hmult" and k[1] not in seen:
+            seen.add(k[1])
+            _, lg, nl, batch, a, b, evk, out = k
+            ha, hb = fhe.to_host(a), fhe.to_host(b)
+            oracle = C.hmult(prm[lg], nl, ha[:, :, batch - 1].astype(np.uint64), hb[:, :, batch - 1].astype(np.uint64),
+                             evk_h[lg].astype(np.uint64))
+            assert (g[:, :, batch - 1] == oracle).all(), (lg, nl)
+    reset_inputs(fhe, keep)
+    fhe.fhe_batch_capture(plan, scratch.data_ptr(), nbytes)
+    for _ in range(2):
+        reset_inputs(fhe, keep)
+        for k in keep:
+            if k[0] == "hmult":
+                k[7].fill_(-1)
+        fhe.fhe_batch_launch(plan, stream)
+        torch.cuda.synchronize()
+        fhe.fhe_device_status(ctx.handle, 1)
+        for i, (w, g) in enumerate(zip(want, batch_results(fhe, keep))):
+            assert (w == g).all(), (i, specs[i])
+    fhe.fhe_batch_destroy(plan)
+    ctx.close()
+
+
+def test_persistent_queue_wait_expires(fhe):
+    """The persistent kernel's dependency wait on a counter that nothing increments gives up
+    after its cycle limit, records FHE_ETIMEOUT in the context's status word and ends; the
+    context then runs a persistent plan correctly."""
+    import torch
+    qs, ps = P.default_moduli(4, 2)
+    ctx = fhe.Context(14, qs, ps, alpha=2)
+    fhe.fhe_selftest_queue_timeout(ctx.handle, 2_000_000, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    with pytest.raises(fhe.FheError) as e:
+        fhe.fhe_device_status(ctx.handle, 1)
+    assert e.value.code == fhe.FHE_ETIMEOUT
+    fhe.fhe_device_status(ctx.handle, 1)          # cleared
+    x = I.uniform_residues(1600, qs, 2, 1 << 14)
+    d = fhe.to_device(x)
+    plan = create(fhe, ctx, [fhe.FheOp(kind=fhe.FHE_OPK_NTT_FWD, logN=14, first_limb=0, n_limbs=len(qs), batch=2,
+                                       data=d.data_ptr())], "persistent")
+    nbytes = fhe.fhe_batch_scratch_bytes(plan)
+    scratch = torch.empty(max(4, nbytes // 4 + 4), dtype=torch.int32, device="cuda")
+    fhe.fhe_batch_run(plan, scratch.data_ptr(), nbytes, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    fhe.fhe_device_status(ctx.handle, 1)
+    ref, _ = ON.ntt_batch(x, qs, [P.psi(q, 1 << 14) for q in qs])
+    assert (fhe.to_host(d) == ref).all()
     fhe.fhe_batch_destroy(plan)
     ctx.close()

@@ -272,6 +272,43 @@ def test_concurrent_streams_share_a_context(fhe):
     ctx.close()
 
 
+@pytest.mark.parametrize("logn", [12, 15])
+def test_concurrent_streams_tensor_core_context(fhe, logn):
+    """HMULTs of one context whose default NTT path is the tensor-core one, on four streams at
+    once: each call's digit planes live in its own scratch, so every result equals the same
+    HMULT run alone; one pair is compared with the oracle."""
+    import torch
+    nl, K, batch = 6, 2, 3
+    n = 1 << logn
+    qs, ps = P.default_moduli(nl, K)
+    prm = C.Params(n, qs, ps, alpha=2)
+    s, evk = make_key(prm, 440 + logn)
+    ctx = fhe.Context(logn, qs, ps, alpha=2, default_path=fhe.FHE_NTT_TC)
+    dev_evk = fhe.to_device(evk.astype(np.uint32))
+    ins = [(fhe.to_device(batch_cts(prm, nl, batch, 450 + 2 * k)), fhe.to_device(batch_cts(prm, nl, batch, 451 + 2 * k)))
+           for k in range(4)]
+    alone = []
+    for a, b in ins:
+        alone.append(ctx.hmult(a, b, dev_evk, logn).clone())
+        torch.cuda.synchronize()
+    nbytes = fhe.fhe_scratch_bytes(ctx.handle, fhe.FHE_OP_HMULT, logn, nl, batch)
+    streams = [torch.cuda.Stream() for _ in ins]
+    scratch = [torch.empty(nbytes // 4 + 4, dtype=torch.int32, device="cuda") for _ in ins]
+    outs = [torch.empty_like(x) for x in alone]
+    for rep in range(3):
+        for k, (a, b) in enumerate(ins):
+            fhe.fhe_hmult(ctx.handle, logn, nl, batch, a.data_ptr(), b.data_ptr(), dev_evk.data_ptr(),
+                          outs[k].data_ptr(), scratch[k].data_ptr(), nbytes, streams[k].cuda_stream)
+        torch.cuda.synchronize()
+        for k in range(len(ins)):
+            assert torch.equal(outs[k], alone[k]), (rep, k)
+    got = fhe.to_host(alone[1])
+    a1, b1 = fhe.to_host(ins[1][0]), fhe.to_host(ins[1][1])
+    assert (got[:, :, 2] == C.hmult(prm, nl, a1[:, :, 2].astype(U64), b1[:, :, 2].astype(U64), evk)).all()
+    fhe.fhe_device_status(ctx.handle, 1)
+    ctx.close()
+
+
 def test_hmult_fused_rescale_tail_wide_shapes(fhe):
     """N = 2^16: the fused tail in the default two-pass shape (512-thread CTAs, C = 4) and in the
     256-thread shape with C = 8 sub-transforms per row (whose cross pass loads ks and d at the
