@@ -113,23 +113,31 @@ int fhe_ntt_inv(const fhe_ctx* ctx, int path, uint32_t logN, uint32_t* d, int fi
                 int n_limbs, int batch, void* stream);
 
 /*
- * Plain-path kernel variants (an interface of this library; the paper picks batch sizes per
- * kernel from the hardware in its API layer, Sec. IV-E, but gives no tuning procedure). A
- * variant fixes the CTA shape, how a thread-block cluster shares a limb, where last-round
- * twiddles live and the register budget; variants change only speed, never results.
+ * NTT variants (an interface of this library; the paper picks batch sizes per kernel from the
+ * hardware in its API layer, Sec. IV-E, but gives no tuning procedure). Ids 0..31 are
+ * plain-path variants: a CTA shape, how a thread-block cluster shares a limb, where last-round
+ * twiddles live and the register budget. FHE_NTT_VARIANT_TC64 and FHE_NTT_VARIANT_TC32 are the
+ * tensor-core path with output tiles of 64 or 32 columns. Variants change only speed, never
+ * results. Per ring degree and direction the context keeps the choice that FHE_NTT_DEFAULT
+ * runs (initially the context's default path: plain variants chosen per N, or TC64), the
+ * plain-path variant that FHE_NTT_U32 calls run and the tile width that FHE_NTT_TC calls run.
  * fhe_ntt_variant_count -- number of variant ids for logN (ids 0..count-1, not all of which
  *   apply at every logN), or -1 on bad input.
- * fhe_ntt_get_variant -- the variant used for logN by forward (inverse = 0) or inverse
- *   (inverse != 0) plain-path transforms of this context (HMULT included), or -1 on bad
- *   input.
- * fhe_ntt_set_variant -- select the forward and the inverse variant for logN; FHE_EINVAL if
- *   either does not apply. Must not race with calls that use the context.
- * fhe_autotune_ntt -- times every applicable variant on forward and inverse transforms of
+ * fhe_ntt_get_variant -- the choice FHE_NTT_DEFAULT runs for logN, forward (inverse = 0) or
+ *   inverse (inverse != 0), HMULT and the other CKKS operations included; -1 on bad input.
+ * fhe_ntt_set_variant -- select the forward and the inverse choice for logN (a plain id also
+ *   becomes the variant of FHE_NTT_U32 calls, a tensor-core id the tile width of FHE_NTT_TC
+ *   calls); FHE_EINVAL if either does not apply. Must not race with calls that use the
+ *   context. fhe_scratch_bytes grows where a tensor-core choice is made.
+ * fhe_autotune_ntt -- times every applicable choice on forward and inverse transforms of
  *   `d` (device (n_limbs, batch, N), limbs use moduli 0..n_limbs-1; restored bit-exactly on
- *   return), keeps the fastest for each direction, and writes milliseconds per call to host
- *   array ms_out[2 * fhe_ntt_variant_count] (nullable): forward times at [v], inverse times
- *   at [count + v], -1 where variant v does not apply. Synchronises `stream`.
+ *   return), keeps the fastest for each direction (and the fastest plain variant and tile
+ *   width for explicit-path calls), and writes milliseconds per call to host array
+ *   ms_out[2 * fhe_ntt_variant_count] (nullable): forward times at [v], inverse times at
+ *   [count + v], -1 where choice v does not apply. Synchronises `stream`.
  */
+#define FHE_NTT_VARIANT_TC64 32
+#define FHE_NTT_VARIANT_TC32 33
 int fhe_ntt_variant_count(const fhe_ctx* ctx, uint32_t logN);
 int fhe_ntt_get_variant(const fhe_ctx* ctx, uint32_t logN, int inverse);
 int fhe_ntt_set_variant(fhe_ctx* ctx, uint32_t logN, int fwd_variant, int inv_variant);

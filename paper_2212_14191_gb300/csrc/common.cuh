@@ -47,6 +47,11 @@ uint32_t root_2n(uint32_t q, uint32_t logN);  // primitive 2N-th root from the s
 // Plain-path kernel shapes per ring degree: threads per CTA T = 2^log_t and CTAs per
 // cluster C = 2^log_c with 32 * T * C = N (see ntt_u32.cu).
 constexpr int kNttVariants = 32;
+// Choice ids beyond the plain-path variants (fhe_ntt_set_variant, fhe_autotune_ntt): the
+// tensor-core path with output tiles of 64 or of 32 columns (NT).
+constexpr int kTcVariant64 = FHE_NTT_VARIANT_TC64, kTcVariant32 = FHE_NTT_VARIANT_TC32;
+static_assert(kTcVariant64 == kNttVariants && kTcVariant32 == kNttVariants + 1, "choice ids follow the plain variants");
+constexpr int kNttChoices = kNttVariants + 2;
 #ifndef FHE_NTT_CHUNK_MIB
 #define FHE_NTT_CHUNK_MIB 1024
 #endif
@@ -80,7 +85,8 @@ struct TcTables {
     uint16_t* mat[4] = {};     // digit planes (fp16) of W1 fwd, W3 fwd, W3 inv, W1 inv: [nmod][4][cols][4K]
     uint2* tw_fwd = nullptr;   // [nmod][N1][N2] (psi^((2k1+1) n2), shoup)
     uint2* tw_inv = nullptr;   // [nmod][N2][N1] (N^-1 psi^(-(2k1+1) n2), shoup)
-    CUtensorMap map_b[4];      // TMA maps over mat[kind]
+    CUtensorMap map_b[4];      // TMA maps over mat[kind], box of min(64, cols) rows (NT = 64 tiles)
+    CUtensorMap map_b32[4];    // the same with a box of 32 rows (NT = 32 tiles)
     CUtensorMap map_a[2];      // TMA maps over the plane buffer, inner extent 4*N1 / 4*N2
     int n1 = 0, n2 = 0;
     bool built = false;
@@ -108,7 +114,12 @@ struct fhe_ctx {
     int dnum = 0;
     std::vector<uint32_t> mods;  // q_0.., p_0..
     fhe::NttTables ntt[FHE_LOGN_MAX + 1];
-    int ntt_variant[2][FHE_LOGN_MAX + 1] = {};  // plain-path variant per direction (0 fwd, 1 inv) and logN
+    // per direction (0 fwd, 1 inv) and logN: the choice FHE_NTT_DEFAULT runs (a plain-path
+    // variant id, or kTcVariant64 / kTcVariant32), the plain-path variant of FHE_NTT_U32 calls
+    // and the tensor-core tile width of FHE_NTT_TC calls
+    int ntt_variant[2][FHE_LOGN_MAX + 1] = {};
+    int plain_variant[2][FHE_LOGN_MAX + 1] = {};
+    int tc_nt[2][FHE_LOGN_MAX + 1] = {};
     int conv_path = FHE_CONV_CUDA;              // basis-conversion kernel (fhe_conv_set_path)
     fhe::TcTables tc[FHE_LOGN_MAX + 1];
     // conv tables: modup[j][e] for slice j ending (exclusive) at limb e; moddown from P
@@ -155,10 +166,11 @@ struct NttScratch {
 size_t ntt_region_bytes(uint32_t logN, size_t rows);
 // Digit-plane buffer of the tensor-core NTT between its two GEMMs: the context's own buffer
 // (fhe_ntt_fwd / fhe_ntt_inv), and the most an operation's scratch region provides for it.
-// 64 MiB holds the planes of 2 limbs x 64 polynomials at N = 2^16, so that a chunk's planes
-// can stay in the 129 MB L2 between the two GEMMs.
+// 256 MiB holds the planes of 8 limbs x 64 polynomials at N = 2^16. Smaller buffers were
+// measured on a GB300 (64 and 128 MiB): every chunk costs two more launches and their tails,
+// and the planes still did not stay in L2 between the two GEMMs.
 #ifndef FHE_TC_PLANE_MIB
-#define FHE_TC_PLANE_MIB 64
+#define FHE_TC_PLANE_MIB 256
 #endif
 constexpr size_t kTcPlaneBytes = (size_t)FHE_TC_PLANE_MIB << 20;
 // The NTT region of a CKKS operation's scratch for NTT calls of up to `rows` rows on this

@@ -81,7 +81,7 @@ LimbMap contiguous_map(const fhe_ctx* ctx, int first, int n) {
 
 int ntt_any(const fhe_ctx* ctx, int path, uint32_t logN, bool inverse, uint32_t* d, int n_limbs,
             int batch, const LimbMap& map, cudaStream_t stream, NttScratch scr) {
-    if (path == FHE_NTT_DEFAULT) path = ctx->default_path;
+    if (path == FHE_NTT_DEFAULT) path = ctx->ntt_variant[inverse ? 1 : 0][logN] >= kNttVariants ? FHE_NTT_TC : FHE_NTT_U32;
     if (path == FHE_NTT_TC) return ntt_tc(ctx, logN, inverse, d, n_limbs, batch, map, stream, scr);
     return ntt_u32(ctx, logN, inverse, d, n_limbs, batch, map, stream, scr);
 }
@@ -94,7 +94,8 @@ size_t ntt_region_bytes(uint32_t logN, size_t rows) {
 
 size_t op_region_bytes(const fhe_ctx* ctx, uint32_t logN, size_t rows) {
     size_t b = ntt_region_bytes(logN, rows);
-    if (ctx->default_path == FHE_NTT_TC && rows > 0) {
+    const bool tc = ctx->ntt_variant[0][logN] >= kNttVariants || ctx->ntt_variant[1][logN] >= kNttVariants;
+    if (tc && rows > 0) {
         // the tensor-core path's digit planes: 8 bytes per residue of a chunk of rows
         const size_t tc = std::min(rows * ((size_t)8 << logN), kTcPlaneBytes);
         b = std::max(b, tc);
@@ -196,6 +197,22 @@ static int check_ntt_args(const fhe_ctx* ctx, int path, uint32_t logN, const uin
     return FHE_OK;
 }
 
+namespace {
+// A choice id the library accepts at logN: a plain-path variant with a kernel shape there, or
+// one of the two tensor-core tile widths.
+bool choice_valid(uint32_t logN, int v) {
+    int lt, lc;
+    return v == kTcVariant64 || v == kTcVariant32 || ntt_variant_shape(logN, v, &lt, &lc);
+}
+void set_choice(fhe_ctx* ctx, uint32_t logN, int dir, int v) {
+    ctx->ntt_variant[dir][logN] = v;
+    if (v < kNttVariants)
+        ctx->plain_variant[dir][logN] = v;
+    else
+        ctx->tc_nt[dir][logN] = v == kTcVariant64 ? 64 : 32;
+}
+}  // namespace
+
 }  // namespace fhe
 
 using namespace fhe;
@@ -272,9 +289,16 @@ int fhe_ctx_create(uint32_t logN_max, const uint32_t* q, int nq, const uint32_t*
         {6, 6},   // 2^16: two-pass (decimation-in-time forward), 512 threads, both directions
     };
     for (int l = 14; l <= 16; ++l) {
-        ctx->ntt_variant[0][l] = kDefaultVariant[l - 14][0];
-        ctx->ntt_variant[1][l] = kDefaultVariant[l - 14][1];
+        ctx->plain_variant[0][l] = kDefaultVariant[l - 14][0];
+        ctx->plain_variant[1][l] = kDefaultVariant[l - 14][1];
     }
+    // FHE_NTT_DEFAULT starts on the context's default path; fhe_ntt_set_variant and
+    // fhe_autotune_ntt may move a ring degree and direction to the other one
+    for (int dir = 0; dir < 2; ++dir)
+        for (int l = 0; l <= FHE_LOGN_MAX; ++l) {
+            ctx->tc_nt[dir][l] = 64;
+            ctx->ntt_variant[dir][l] = default_path == FHE_NTT_TC ? kTcVariant64 : ctx->plain_variant[dir][l];
+        }
     int rc = FHE_OK;
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
@@ -338,11 +362,9 @@ int fhe_device_status(const fhe_ctx* ctx, int clear) {
 
 int fhe_ntt_variant_count(const fhe_ctx* ctx, uint32_t logN) {
     if (!ctx || logN < FHE_LOGN_MIN || logN > ctx->logN_max) return -1;
-    int n = 0, lt, lc;
-    for (int v = 0; v < kNttVariants; ++v)
-        if (ntt_variant_shape(logN, v, &lt, &lc)) n = v + 1;
-    return n;
+    return kNttChoices;
 }
+
 
 int fhe_ntt_get_variant(const fhe_ctx* ctx, uint32_t logN, int inverse) {
     if (!ctx || logN < FHE_LOGN_MIN || logN > ctx->logN_max) return -1;
@@ -352,11 +374,10 @@ int fhe_ntt_get_variant(const fhe_ctx* ctx, uint32_t logN, int inverse) {
 int fhe_ntt_set_variant(fhe_ctx* ctx, uint32_t logN, int fwd_variant, int inv_variant) {
     FHE_CHECK(ctx != nullptr, "ctx is NULL");
     FHE_CHECK(logN >= FHE_LOGN_MIN && logN <= ctx->logN_max, "logN out of [10, logN_max]");
-    int lt, lc;
-    FHE_CHECK(ntt_variant_shape(logN, fwd_variant, &lt, &lc), "no such forward NTT variant for this logN");
-    FHE_CHECK(ntt_variant_shape(logN, inv_variant, &lt, &lc), "no such inverse NTT variant for this logN");
-    ctx->ntt_variant[0][logN] = fwd_variant;
-    ctx->ntt_variant[1][logN] = inv_variant;
+    FHE_CHECK(choice_valid(logN, fwd_variant), "no such forward NTT variant for this logN");
+    FHE_CHECK(choice_valid(logN, inv_variant), "no such inverse NTT variant for this logN");
+    set_choice(ctx, logN, 0, fwd_variant);
+    set_choice(ctx, logN, 1, inv_variant);
     return FHE_OK;
 }
 
@@ -376,26 +397,34 @@ int fhe_autotune_ntt(fhe_ctx* ctx, uint32_t logN, uint32_t* d, int n_limbs, int 
     FHE_CHECK(batch >= 1 && reps >= 1, "batch and reps must be >= 1");
     cudaStream_t st = (cudaStream_t)stream;
     const LimbMap map = contiguous_map(ctx, 0, n_limbs);
-    const int keep[2] = {ctx->ntt_variant[0][logN], ctx->ntt_variant[1][logN]};
-    int best[2] = {keep[0], keep[1]};
-    float best_ms[2] = {-1.0f, -1.0f};
+    int keep[3][2];
+    for (int dir = 0; dir < 2; ++dir) {
+        keep[0][dir] = ctx->ntt_variant[dir][logN];
+        keep[1][dir] = ctx->plain_variant[dir][logN];
+        keep[2][dir] = ctx->tc_nt[dir][logN];
+    }
+    // per direction: the fastest choice overall, the fastest plain-path variant and the
+    // fastest tensor-core tile width (the latter two serve explicit FHE_NTT_U32 / _TC calls)
+    int best[2] = {keep[0][0], keep[0][1]}, best_plain[2] = {keep[1][0], keep[1][1]};
+    int best_tc[2] = {keep[2][0] == 32 ? kTcVariant32 : kTcVariant64, keep[2][1] == 32 ? kTcVariant32 : kTcVariant64};
+    float best_ms[2] = {-1.0f, -1.0f}, best_plain_ms[2] = {-1.0f, -1.0f}, best_tc_ms[2] = {-1.0f, -1.0f};
     const int count = fhe_ntt_variant_count(ctx, logN);
     cudaEvent_t ev[3];
     for (int i = 0; i < 3; ++i) FHE_CUDA_TRY(cudaEventCreate(&ev[i]));
     for (int v = 0; v < count && rc == FHE_OK; ++v) {
-        int lt, lc;
-        if (!ntt_variant_shape(logN, v, &lt, &lc)) {
+        if (!choice_valid(logN, v)) {
             if (ms_out) ms_out[v] = ms_out[count + v] = -1.0f;
             continue;
         }
-        ctx->ntt_variant[0][logN] = ctx->ntt_variant[1][logN] = v;
+        set_choice(ctx, logN, 0, v);
+        set_choice(ctx, logN, 1, v);
         float sum[2] = {0.0f, 0.0f};
         // one untimed round trip, then `reps` timed ones (forward and inverse timed apart)
         for (int r = 0; r <= reps && rc == FHE_OK; ++r) {
             cudaEventRecord(ev[0], st);
-            rc = ntt_u32(ctx, logN, false, d, n_limbs, batch, map, st);
+            rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, false, d, n_limbs, batch, map, st);
             cudaEventRecord(ev[1], st);
-            if (rc == FHE_OK) rc = ntt_u32(ctx, logN, true, d, n_limbs, batch, map, st);
+            if (rc == FHE_OK) rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, true, d, n_limbs, batch, map, st);
             cudaEventRecord(ev[2], st);
             cudaError_t ce = cudaEventSynchronize(ev[2]);
             if (rc == FHE_OK && ce != cudaSuccess) rc = cuda_error(ce, "cudaEventSynchronize");
@@ -414,11 +443,25 @@ int fhe_autotune_ntt(fhe_ctx* ctx, uint32_t logN, uint32_t* d, int n_limbs, int 
                 best_ms[dir] = ms;
                 best[dir] = v;
             }
+            float& bk = v < kNttVariants ? best_plain_ms[dir] : best_tc_ms[dir];
+            if (bk < 0 || ms < bk) {
+                bk = ms;
+                (v < kNttVariants ? best_plain : best_tc)[dir] = v;
+            }
         }
     }
     for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
-    ctx->ntt_variant[0][logN] = (rc == FHE_OK) ? best[0] : keep[0];
-    ctx->ntt_variant[1][logN] = (rc == FHE_OK) ? best[1] : keep[1];
+    for (int dir = 0; dir < 2; ++dir) {
+        if (rc == FHE_OK) {
+            set_choice(ctx, logN, dir, best_plain[dir]);
+            set_choice(ctx, logN, dir, best_tc[dir]);
+            set_choice(ctx, logN, dir, best[dir]);
+        } else {
+            ctx->ntt_variant[dir][logN] = keep[0][dir];
+            ctx->plain_variant[dir][logN] = keep[1][dir];
+            ctx->tc_nt[dir][logN] = keep[2][dir];
+        }
+    }
     return rc;
 }
 

@@ -583,8 +583,12 @@ int build_tc_tables(fhe_ctx* ctx, uint32_t logN) {
                 }
         }
         if ((rc = dev_upload(ctx, &t.mat[kind], h))) return rc;
+        // the B tiles of a GEMM with NT-column output tiles are 4 TMA boxes of NT rows (one per
+        // digit plane), so each tile width has its own map
         if ((rc = make_map(&t.map_b[kind], t.mat[kind], (uint64_t)4 * K, (uint64_t)nmod * 4 * cols,
                            cols >= 64 ? 64 : 32)))
+            return rc;
+        if ((rc = make_map(&t.map_b32[kind], t.mat[kind], (uint64_t)4 * K, (uint64_t)nmod * 4 * cols, 32)))
             return rc;
     }
     // twiddles for the first-GEMM epilogue: forward [k1][n2] psi^((2k1+1) n2);
@@ -654,6 +658,7 @@ int ntt_tc(const fhe_ctx* cctx, uint32_t logN, bool inverse, uint32_t* d, int n_
     }
     const TcTables& t = ctx->tc[logN];
     const int n1 = t.n1, n2 = t.n2;
+    const int nt = ctx->tc_nt[inverse ? 1 : 0][logN];  // output tile width (64 or 32 columns)
     const size_t N = (size_t)1 << logN;
     // X: first-GEMM reduction size, Y: its rows per polynomial; the second GEMM swaps them.
     const int X1 = inverse ? n2 : n1, Y1 = inverse ? n1 : n2;
@@ -713,8 +718,8 @@ int ntt_tc(const fhe_ctx* cctx, uint32_t logN, bool inverse, uint32_t* d, int n_
             g.mode = 1;
             g.tw = inverse ? t.tw_inv : t.tw_fwd;
             g.planes = planes;
-            rc = cols1 >= 64 ? launch_gemm_fused<64>(ctx, src, t.map_b[kind1], g, nl, st)
-                             : launch_gemm_fused<32>(ctx, src, t.map_b[kind1], g, nl, st);
+            rc = (cols1 >= 64 && nt == 64) ? launch_gemm_fused<64>(ctx, src, t.map_b[kind1], g, nl, st)
+                                           : launch_gemm_fused<32>(ctx, src, t.map_b32[kind1], g, nl, st);
             if (rc) return rc;
             // Stages 4-5
             g.Y = cols1;
@@ -723,8 +728,8 @@ int ntt_tc(const fhe_ctx* cctx, uint32_t logN, bool inverse, uint32_t* d, int n_
             g.mode = 2;
             g.out = base;
             g.out_limb_stride = (size_t)batch * N;
-            rc = cols2 >= 64 ? launch_gemm<64>(ctx, *a2, t.map_b[kind2], g, nl, st)
-                             : launch_gemm<32>(ctx, *a2, t.map_b[kind2], g, nl, st);
+            rc = (cols2 >= 64 && nt == 64) ? launch_gemm<64>(ctx, *a2, t.map_b[kind2], g, nl, st)
+                                           : launch_gemm<32>(ctx, *a2, t.map_b32[kind2], g, nl, st);
             if (rc) return rc;
         }
     }

@@ -156,7 +156,7 @@ int ntt_u32_dispatch(const fhe_ctx* ctx, uint32_t logN, bool inverse, uint32_t* 
     if (rows_ll == 0) return FHE_OK;
     if (rows_ll > (1LL << 30)) return set_error(FHE_EINVAL, "too many rows");
     const int rows = (int)rows_ll;
-    const int v = ctx->ntt_variant[inverse ? 1 : 0][logN];
+    const int v = ctx->plain_variant[inverse ? 1 : 0][logN];
     int log_t, log_c;
     if (!ntt_variant_shape(logN, v, &log_t, &log_c)) return set_error(FHE_EINVAL, "logN out of range");
     if (log_c >= 2)

@@ -33,8 +33,7 @@ __global__ void __launch_bounds__(256) ntt_cross_inv_kernel(const L2Args a) {
 
 template <int LOG_T, int LOG_C>
 __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_quarter_inv_kernel(const L2Args a) {
-    extern __shared__ __align__(128) uint32_t work[];
-    quarter_inv<LOG_T, LOG_C, false>(a, blockIdx.y, blockIdx.x, work);
+    quarter_inv<LOG_T, LOG_C, false>(a, blockIdx.y, blockIdx.x);
 }
 
 template <int LOG_NC, int LOG_C, bool TAIL>
@@ -44,8 +43,7 @@ __global__ void __launch_bounds__(256) ntt_dit_cross_kernel(const L2Args a) {
 
 template <int LOG_T, int LOG_C, bool TAIL>
 __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_dit_local_kernel(const L2Args a) {
-    extern __shared__ __align__(128) uint32_t work[];
-    dit_local<LOG_T, LOG_C, TAIL, false>(a, blockIdx.y, blockIdx.x, work);
+    dit_local<LOG_T, LOG_C, TAIL, false>(a, blockIdx.y, blockIdx.x);
 }
 
 
@@ -138,9 +136,10 @@ int ntt_u32_l2(const fhe_ctx* ctx, uint32_t logN, int shape, bool inverse, uint3
 }
 
 bool ntt_tail_fusable(const fhe_ctx* ctx, int path, uint32_t logN) {
-    if (path == FHE_NTT_DEFAULT) path = ctx->default_path;
-    if (path != FHE_NTT_U32 || logN < 15 || logN > FHE_LOGN_MAX) return false;
-    const int v = ctx->ntt_variant[0][logN];
+    if (logN < 15 || logN > FHE_LOGN_MAX) return false;
+    if (path == FHE_NTT_DEFAULT && ctx->ntt_variant[0][logN] >= kNttVariants) return false;  // tensor cores
+    if (path != FHE_NTT_DEFAULT && path != FHE_NTT_U32) return false;
+    const int v = ctx->plain_variant[0][logN];
     int log_t, log_c;
     return ntt_variant_exchange(v) == 3 && ntt_variant_shape(logN, v, &log_t, &log_c) && log_c > 0;
 }
@@ -149,7 +148,7 @@ int ntt_u32_l2_tail(const fhe_ctx* ctx, uint32_t logN, int rows, int batch, cons
                     NttScratch scr, const HmultTail& tail) {
     if (!ntt_tail_fusable(ctx, FHE_NTT_U32, logN)) return set_error(FHE_EINVAL, "fused tail needs the two-pass NTT");
     if (rows == 0) return FHE_OK;
-    const int v = ctx->ntt_variant[0][logN];
+    const int v = ctx->plain_variant[0][logN];
     // the data pointer is not read or written by the TAIL kernels (rows come from y / go to out)
     return ntt_u32_l2_impl<true>(ctx, logN, v & 1, false, tail.out, rows, batch, map, nullptr, st, scr, &tail);
 }

@@ -45,13 +45,17 @@ __device__ __forceinline__ TailRow tail_row(const L2Args& a, int r) {
 // pass while the row's scratch is still in L2. Nothing waits: a CTA that is not last exits.
 __device__ __forceinline__ bool last_of_row(const L2Args& a, int i, int C) {
     __shared__ int s_last;
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&a.cnt[i], 1) == C - 1;
+    if (threadIdx.x == 0) {
+        // the barrier orders the CTA's scratch stores before this thread's fence (cumulative),
+        // so one fence releases all of them; the warps do not each wait for their own
+        __threadfence();
+        const bool last = atomicAdd(&a.cnt[i], 1) == C - 1;
+        if (last) __threadfence();
+        s_last = last;
+    }
     __syncthreads();
-    if (!s_last) return false;
-    __threadfence();
-    return true;
+    return s_last != 0;
 }
 
 template <int N>
@@ -155,20 +159,21 @@ template <int LOG_T>
 constexpr int kMinB = 2 * ((1 << (14 - LOG_T)) / 32 > 0 ? (1 << (14 - LOG_T)) / 32 : 1);
 
 // ---- quarter pass, inverse: row (stride C, quarter c's bit-reversed share) -> GS stages -> scratch
-// Row i of the chunk, quarter c, in a CTA of 2^LOG_T threads whose dynamic shared memory is
-// `work`. COH: the row is read through L2 (coherent with writes made earlier in the same
-// kernel by other CTAs) instead of the read-only path. With C = 1 (N = 2^(LOG_T + 5)) the
-// transform ends here: N^-1 is applied and the row is written in place.
+// Row i of the chunk, quarter c, in a CTA of 2^LOG_T threads whose dynamic shared memory holds
+// PadLayout<LOG_T>::kWords words. COH: the row is read through L2 (coherent with writes made
+// earlier in the same kernel by other CTAs) instead of the read-only path. With C = 1
+// (N = 2^(LOG_T + 5)) the transform ends here: N^-1 is applied and the row is written in place.
 template <int LOG_T, int LOG_C, bool COH>
-__device__ __forceinline__ void quarter_inv(const L2Args& a, int i, int c, uint32_t* work) {
+__device__ __forceinline__ void quarter_inv(const L2Args& a, int i, int c) {
     constexpr int T = 1 << LOG_T, C = 1 << LOG_C, NC = 32 * T, N = NC * C, RB = LOG_T - 5;
+    extern __shared__ __align__(128) uint32_t work[];
     const int tid = threadIdx.x;
     const int rc = rbits<LOG_C>(c);
     using L = PadLayout<LOG_T>;
     const int pA = L::pad(tid);
     uint32_t q;
     int mod;
-    uint32_t* row = l2_row<N>(a, a.r0 + i, &q, &mod);
+    const uint32_t* row = l2_row<N>(a, a.r0 + i, &q, &mod);
     uint32_t* tmp = a.temp + (size_t)i * N + c * NC;
     const uint2* tw = a.tw + (size_t)mod * N;
     uint32_t v[32];
@@ -226,8 +231,9 @@ __device__ __forceinline__ void quarter_inv(const L2Args& a, int i, int c, uint3
     }
     if constexpr (C == 1) {
         const uint2 ni = __ldg(&a.ninv[mod]);
+        uint32_t* out = const_cast<uint32_t*>(row);  // the in-place transform of this row ends here
 #pragma unroll
-        for (int e = 0; e < 32; ++e) row[tid + T * e] = mul_shoup(v[e], ni.x, ni.y, q);
+        for (int e = 0; e < 32; ++e) out[tid + T * e] = mul_shoup(v[e], ni.x, ni.y, q);
     } else {
 #pragma unroll
         for (int e = 0; e < 32; ++e) __stcg(&tmp[tid + T * e], v[e]);
@@ -354,11 +360,12 @@ __device__ __forceinline__ void dit_cross_row(const L2Args& a, int i, int p0, in
     }
 }
 
-// Local pass of row i, sub-transform j (see quarter_inv for `work` and COH). With C = 1 and no
-// tail the transform ends here and the row is written in place, in natural order.
+// Local pass of row i, sub-transform j (see quarter_inv for the shared memory and COH). With
+// C = 1 and no tail the transform ends here and the row is written in place, in natural order.
 template <int LOG_T, int LOG_C, bool TAIL, bool COH>
-__device__ __forceinline__ void dit_local(const L2Args& a, int i, int j, uint32_t* work) {
+__device__ __forceinline__ void dit_local(const L2Args& a, int i, int j) {
     constexpr int T = 1 << LOG_T, C = 1 << LOG_C, NC = 32 * T, N = NC * C, RB = LOG_T - 5;
+    extern __shared__ __align__(128) uint32_t work[];
     const int tid = threadIdx.x;
     using L = PadLayout<LOG_T>;
     const int pA = L::pad(tid);

@@ -121,13 +121,13 @@ __device__ __forceinline__ void copy_args(const Slot<T>* src, TileArgs* dst) {
 }
 
 template <int LC>
-__device__ __forceinline__ void run_ntt(const L2Args& a, uint16_t sub, int row, int part, uint32_t* work) {
+__device__ __forceinline__ void run_ntt(const L2Args& a, uint16_t sub, int row, int part) {
     if (sub & kSubInv)
-        quarter_inv<kLogPT, LC, true>(a, row, part, work);
+        quarter_inv<kLogPT, LC, true>(a, row, part);
     else if (sub & kSubTail)
-        dit_local<kLogPT, LC, true, true>(a, row, part, work);
+        dit_local<kLogPT, LC, true, true>(a, row, part);
     else
-        dit_local<kLogPT, LC, false, true>(a, row, part, work);
+        dit_local<kLogPT, LC, false, true>(a, row, part);
 }
 
 template <int NS>
@@ -171,11 +171,11 @@ __device__ void run_tile(const PParams& p, const PTile& t, TileArgs* sa, uint32_
             __syncthreads();
             const int lc = t.sub & 3;
             if (lc == 0)
-                run_ntt<0>(sa->ntt, t.sub, t.x, t.y, work);
+                run_ntt<0>(sa->ntt, t.sub, t.x, t.y);
             else if (lc == 1)
-                run_ntt<1>(sa->ntt, t.sub, t.x, t.y, work);
+                run_ntt<1>(sa->ntt, t.sub, t.x, t.y);
             else
-                run_ntt<2>(sa->ntt, t.sub, t.x, t.y, work);
+                run_ntt<2>(sa->ntt, t.sub, t.x, t.y);
             break;
         }
         case PK_TENSOR:

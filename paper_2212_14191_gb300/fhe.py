@@ -18,6 +18,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "fhe.h")
 
 FHE_OK, FHE_EINVAL, FHE_ENOMEM, FHE_ECUDA, FHE_ETIMEOUT = 0, 1, 2, 3, 4
 FHE_NTT_DEFAULT, FHE_NTT_U32, FHE_NTT_TC = 0, 1, 2
+FHE_NTT_VARIANT_TC64, FHE_NTT_VARIANT_TC32 = 32, 33
 FHE_CONV_CUDA, FHE_CONV_TC = 0, 1
 FHE_OP_HMULT, FHE_OP_KEYSWITCH, FHE_OP_RESCALE, FHE_OP_HMULT_RELIN, FHE_OP_HROTATE = 1, 2, 3, 4, 5
 FHE_OP_HROTATE_HOISTED = 6

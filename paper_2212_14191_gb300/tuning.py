@@ -1,11 +1,11 @@
-"""Autotune cache for the plain-path NTT variants (the autotuned kernel shapes of Sec. IV-E).
+"""Autotune cache for the NTT variants (the autotuned kernel shapes of Sec. IV-E).
 
-fhe_autotune_ntt times every applicable variant of a ring degree on the caller's data and
-keeps the fastest forward and inverse variants in the context. This module stores those
-choices in a JSON file keyed by (GPU name, ring degree, limbs, batch), so that a later
-process on the same kind of GPU and workload sets them directly instead of timing every
-variant again. The file holds plain variant ids; a stored id that the library no longer
-offers is ignored and the autotuner runs again.
+fhe_autotune_ntt times every applicable variant of a ring degree on the caller's data (the
+plain-path kernel shapes and the tensor-core path's two output tile widths) and keeps the
+fastest forward and inverse choices in the context. This module stores those choices in a
+JSON file keyed by (GPU name, ring degree, limbs, batch), so that a later process on the same
+kind of GPU and workload sets them directly instead of timing every variant again. A stored
+id that the library no longer offers is ignored and the autotuner runs again.
 """
 import json
 import os

@@ -60,6 +60,13 @@ def test_variant_names(v):
     assert ("two-pass" in name) == (((v >> 1) & 3) == 3)
 
 
+@pytest.mark.parametrize("v", [32, 33])
+def test_tensor_core_variant_names(v):
+    name = bench.variant_name(v)
+    assert name.startswith("variant %d:" % v) and "tensor-core" in name
+    assert ("64-column" in name) == (v == 32)
+
+
 def test_host_cpu_description():
     d = bench.host_cpu()
     assert "logical cores" in d and str(os.cpu_count()) in d

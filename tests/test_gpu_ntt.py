@@ -68,6 +68,35 @@ def test_fwd_inv_match_oracle(fhe, ctx, logn, path, variant):
     fhe.fhe_ntt_set_variant(ctx.handle, logn, 0)
 
 
+@pytest.mark.parametrize("choice", [32, 33])
+@pytest.mark.parametrize("logn", [10, 11, 12, 13, 14, 15, 16])
+def test_tensor_core_choices(fhe, ctx, logn, choice):
+    """The tensor-core path as the choice of FHE_NTT_DEFAULT (variant ids FHE_NTT_VARIANT_TC64 /
+    TC32: output tiles of 64 or 32 columns, the latter with its own 32-row constant-matrix tensor
+    maps where the matrices are 64 or more columns wide): bit-exact forward and inverse, the
+    explicit FHE_NTT_TC path taking the same tile width, and FHE_NTT_U32 keeping its plain
+    variant."""
+    import torch
+    keep = (fhe.fhe_ntt_get_variant(ctx.handle, logn, 0), fhe.fhe_ntt_get_variant(ctx.handle, logn, 1))
+    fhe.fhe_ntt_set_variant(ctx.handle, logn, choice, choice)
+    assert fhe.fhe_ntt_get_variant(ctx.handle, logn, 0) == choice
+    n = 1 << logn
+    first, nl, batch = 40, 6, 5
+    mods = MODS[first:first + nl]
+    x = I.uniform_residues(900 + logn + choice, mods, batch, n)
+    want, _ = ON.ntt_batch(x, mods, psis(mods, n))
+    for path in (fhe.FHE_NTT_DEFAULT, fhe.FHE_NTT_TC, fhe.FHE_NTT_U32):
+        d = fhe.to_device(x)
+        ctx.ntt_fwd(d, logn, first_limb=first, path=path)
+        torch.cuda.synchronize()
+        assert (fhe.to_host(d) == want).all(), path
+        ctx.ntt_inv(d, logn, first_limb=first, path=path)
+        torch.cuda.synchronize()
+        assert (fhe.to_host(d) == x).all(), path
+    fhe.fhe_device_status(ctx.handle, 1)
+    fhe.fhe_ntt_set_variant(ctx.handle, logn, keep[0], keep[1])
+
+
 @pytest.mark.parametrize("path", PATHS)
 def test_plain_ntt_config_n4096(fhe, path):
     """N = 2^12, one prime q_0, 16 polynomials uniform in [0, q), seed 0."""
