@@ -72,6 +72,7 @@ struct NttTables {
     uint2* fwdC[2] = {};  // per shape: [nmod][C][31][T] last-round twiddles, per-thread order
     uint2* invC[2] = {};
     uint2* ninv = nullptr;  // [nmod] (N^-1 mod q, shoup)
+    uint2* ninv_w1 = nullptr;  // [nmod] (N^-1 inv[1] mod q, shoup): the two-pass inverse's last stage
     // decimation-in-time two-pass forward (N >= 2^15), per shape with C = N / NC sub-NTTs of
     // NC points: twist[nmod][C-1][NC] = psi^((2k'+1) j) for j = 1..C-1, and omega[nmod][C/2] =
     // (psi^(2 NC))^m, the C-th roots of unity of the C-point DFT (all with Shoup quotients)

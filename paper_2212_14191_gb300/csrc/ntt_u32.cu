@@ -51,7 +51,7 @@ int build_ntt_tables(fhe_ctx* ctx, uint32_t logN) {
     const int nmod = (int)ctx->mods.size();
     const uint32_t N = 1u << logN;
     std::vector<uint2> fwd((size_t)nmod * N), inv((size_t)nmod * N);
-    std::vector<uint2> ninv(nmod);
+    std::vector<uint2> ninv(nmod), ninv_w1(nmod);
     for (int m = 0; m < nmod; ++m) {
         const uint32_t q = ctx->mods[m];
         const uint32_t psi = root_2n(q, logN);
@@ -71,6 +71,8 @@ int build_ntt_tables(fhe_ctx* ctx, uint32_t logN) {
         }
         uint32_t ni = invmod_h(N % q, q);
         ninv[m] = make_uint2(ni, shoup_h(ni, q));
+        const uint32_t niw = mulmod_h(ni, inv[(size_t)m * N + 1].x, q);
+        ninv_w1[m] = make_uint2(niw, shoup_h(niw, q));
     }
     NttTables& t = ctx->ntt[logN];
     int rc;
@@ -99,6 +101,7 @@ int build_ntt_tables(fhe_ctx* ctx, uint32_t logN) {
     if ((rc = dev_upload(ctx, &t.fwd, fwd))) return rc;
     if ((rc = dev_upload(ctx, &t.inv, inv))) return rc;
     if ((rc = dev_upload(ctx, &t.ninv, ninv))) return rc;
+    if ((rc = dev_upload(ctx, &t.ninv_w1, ninv_w1))) return rc;
     // two-pass decimation-in-time forward: twists and C-th roots of unity per shape
     for (int v = 0; v < 2 && logN >= 15; ++v) {
         int log_t, log_c;

@@ -72,6 +72,7 @@ int run_l2(const fhe_ctx* ctx, const NttTables& t, int shape, bool inverse, uint
     a.tw = inverse ? t.inv : t.fwd;
     a.twC = inverse ? t.invC[shape] : t.fwdC[shape];
     a.ninv = t.ninv;
+    a.ninv_w1 = t.ninv_w1;
     a.tw_sub = ts.fwd;
     a.twC_sub = ts.fwdC[0];
     a.twist = t.dit_twist[shape];

@@ -21,6 +21,7 @@ struct L2Args {
     const uint2* tw;     // [nmod][N]
     const uint2* twC;    // [nmod][C][31][T]
     const uint2* ninv;   // [nmod]
+    const uint2* ninv_w1;    // [nmod] N^-1 times tw[1] of the inverse tables (the last cross stage's twiddle)
     const uint2* tw_sub;     // decimation-in-time forward: tables of the NC-point ring degree
     const uint2* twC_sub;    // [nmod][1][31][T]
     const uint2* twist;      // [nmod][C-1][NC]
@@ -93,7 +94,10 @@ __device__ __forceinline__ void gs2(uint32_t& x, uint32_t& y, uint2 w, uint32_t 
 }
 
 // ---- inverse cross pass: grid (blocks over NC/4 quad positions, chunk rows); 4 positions per
-// thread; the last log2(C) Gentleman-Sande stages and the N^-1 scaling
+// thread; the last log2(C) Gentleman-Sande stages and the N^-1 scaling. The scaling rides on the
+// last stage: its outputs are (x + y) N^-1 and (x - y) (w N^-1), one Shoup product each, where
+// the stage and the scaling would take three (x + y < 4q and x - y + 2q < 4q are valid Shoup
+// inputs, and the products come out canonical).
 template <int LOG_NC, int LOG_C>
 __device__ __forceinline__ void cross_inv_row(const L2Args& a, int i, int p0, int pstep) {
     constexpr int NC = 1 << LOG_NC, C = 1 << LOG_C, N = NC * C;
@@ -103,6 +107,7 @@ __device__ __forceinline__ void cross_inv_row(const L2Args& a, int i, int p0, in
     const uint32_t* tmp = a.temp + (size_t)i * N;
     const uint2* tw = a.tw + (size_t)mod * N;
     const uint2 ni = __ldg(&a.ninv[mod]);
+    const uint2 niw = __ldg(&a.ninv_w1[mod]);
     for (int p4 = p0; p4 < NC / 4; p4 += pstep) {
         uint4 x[C];
 #pragma unroll
@@ -113,15 +118,26 @@ __device__ __forceinline__ void cross_inv_row(const L2Args& a, int i, int p0, in
 #pragma unroll
             for (int qq = 0; qq < C; ++qq) y[qq] = k == 0 ? x[qq].x : k == 1 ? x[qq].y : k == 2 ? x[qq].z : x[qq].w;
 #pragma unroll
-            for (int s = LOG_C - 1; s >= 0; --s) {
+            for (int s = LOG_C - 1; s >= 1; --s) {
                 const int tq = C >> (s + 1);
 #pragma unroll
                 for (int qq = 0; qq < C; ++qq)
                     if ((qq / tq) % 2 == 0) gs2(y[qq], y[qq + tq], __ldg(&tw[(1 << s) + qq / (2 * tq)]), q);
             }
+            if constexpr (C > 1) {
+                // the last stage (pairs qq, qq + C/2, all with twiddle tw[1]) and N^-1 at once
+#pragma unroll
+                for (int qq = 0; qq < C / 2; ++qq) {
+                    const uint32_t u = y[qq], w = y[qq + C / 2];
+                    y[qq] = mul_shoup(u + w, ni.x, ni.y, q);
+                    y[qq + C / 2] = mul_shoup(u - w + 2 * q, niw.x, niw.y, q);
+                }
+            } else {
+                y[0] = mul_shoup(y[0], ni.x, ni.y, q);
+            }
 #pragma unroll
             for (int qq = 0; qq < C; ++qq) {
-                const uint32_t v = mul_shoup(y[qq], ni.x, ni.y, q);
+                const uint32_t v = y[qq];
                 if (k == 0) x[qq].x = v;
                 else if (k == 1) x[qq].y = v;
                 else if (k == 2) x[qq].z = v;
@@ -303,7 +319,7 @@ __device__ __forceinline__ void dit_cross_row(const L2Args& a, int i, int p0, in
             for (int jj = 1; jj < C; ++jj) {
                 const uint4 t4 = tw2[2 * (jj - 1) + (k >> 1)];
                 const uint2 w = (k & 1) ? make_uint2(t4.z, t4.w) : make_uint2(t4.x, t4.y);
-                y[jj] = mul_shoup(y[jj], w.x, w.y, q);  // [0, q)
+                y[jj] = mul_shoup_lazy(y[jj], w.x, w.y, q);  // [0, 2q)
             }
             // C-point cyclic DFT, radix-2 decimation in frequency: position p ends up holding
             // output t = rev(p); values stay in [0, 2q)
@@ -449,8 +465,10 @@ __device__ __forceinline__ void dit_local(const L2Args& a, int i, int j) {
 #pragma unroll
         for (int e = 0; e < 32; ++e) row[rbits<5>(e) * T + tid] = csub(csub(v[e], 2 * q), q);
     } else {
+        // the cross pass takes its inputs in [0, 2q) (twists are lazy Shoup products, the DFT's
+        // butterflies keep [0, 2q)), so one conditional subtraction suffices here
 #pragma unroll
-        for (int e = 0; e < 32; ++e) __stcg(&tmp[rbits<5>(e) * T + tid], csub(csub(v[e], 2 * q), q));
+        for (int e = 0; e < 32; ++e) __stcg(&tmp[rbits<5>(e) * T + tid], csub(v[e], 2 * q));
         if (a.fuse && last_of_row(a, i, C)) dit_cross_row<LOG_T + 5, LOG_C, TAIL, COH>(a, i, tid, T);
     }
 }

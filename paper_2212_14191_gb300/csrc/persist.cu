@@ -330,6 +330,7 @@ uint32_t ntt_stage(Builder& b, uint32_t logN, bool inverse, uint32_t* data, int 
     a.tw = inverse ? t.inv : t.fwd;
     a.twC = inverse ? t.invC[0] : t.fwdC[0];
     a.ninv = t.ninv;
+    a.ninv_w1 = t.ninv_w1;
     a.tw_sub = ts.fwd;
     a.twC_sub = ts.fwdC[0];
     a.twist = t.dit_twist[0];

@@ -135,3 +135,79 @@ def test_64bit_reduction_and_accumulation_bounds():
                       15 * (q - 1) ** 2, 15 * (q - 1) ** 2 + q - 1], dtype=U64)])
         got = reduce_red(x, q)
         np.testing.assert_array_equal(got, np.array([int(v) % q for v in x], dtype=U64))
+
+
+def _bitrev_small(x, bits):
+    return int(format(x, "0%db" % bits)[::-1], 2) if bits else 0
+
+
+@pytest.mark.parametrize("log_c", [1, 2, 3])
+def test_two_pass_forward_cross_pass_ranges(log_c):
+    """The forward two-pass cross pass at the largest accepted prime with every input of the C
+    streams anywhere in [0, 2q) (the local pass stores with one conditional subtraction): the
+    twists are lazy Shoup products in [0, 2q), the C-point cyclic DFT's butterflies (trivial ones
+    at omega^0, Gentleman-Sande ones otherwise) keep [0, 2q), and after one final conditional
+    subtraction output t equals sum_j omega^(t j) twist_j y_j mod q, canonical."""
+    C = 1 << log_c
+    q = P.ntt_primes(1, logn_max=16)[0]
+    rng = np.random.default_rng(40 + log_c)
+    omega = pow(P.psi(q, 1 << 16), (1 << 16) * 2 // C, q)          # a primitive C-th root of unity
+    om = [pow(omega, m, q) for m in range(C // 2)]
+    om_q = [shoup_quotient(w, q) for w in om]
+    for trial in range(4):
+        y0 = rng.integers(0, 2 * q, (C, 256), dtype=np.int64).astype(U64)
+        if trial == 1:
+            y0[:] = 2 * q - 1
+        if trial == 2:
+            y0[:] = 0
+        tw = rng.integers(1, q, C, dtype=np.int64)
+        y = y0.copy()
+        for j in range(1, C):
+            y[j] = mul_shoup_lazy(y[j], U64(tw[j]), shoup_quotient(int(tw[j]), q), q)
+        assert y.max() < 2 * q
+        for s in range(log_c):
+            h = C >> (s + 1)
+            for b in range(0, C, 2 * h):
+                for jj in range(h):
+                    m = jj << s
+                    x, z = y[b + jj].copy(), y[b + jj + h].copy()
+                    if m == 0:
+                        y[b + jj] = csub((x + z) & M32, 2 * q)
+                        y[b + jj + h] = csub((x - z + U64(2 * q)) & M32, 2 * q)
+                    else:
+                        y[b + jj] = csub(x + z, 2 * q)
+                        y[b + jj + h] = mul_shoup_lazy((x - z + U64(2 * q)) & M32, U64(om[m]), om_q[m], q)
+            assert y.max() < 2 * q
+        out = csub(y, q)
+        tw_all = [1] + [int(t) for t in tw[1:]]
+        for t in range(C):
+            want = sum(pow(omega, t * j, q) * tw_all[j] * y0[j].astype(object) for j in range(C)) % q
+            got = out[_bitrev_small(t, log_c)]
+            assert (got.astype(object) == want).all(), (t, trial)
+
+
+def test_two_pass_inverse_last_stage_with_scaling():
+    """The inverse two-pass cross pass's last Gentleman-Sande stage with N^-1 folded in, at the
+    largest accepted prime and inputs anywhere in [0, 2q): (u + w) N^-1 and (u - w + 2q) (tw N^-1)
+    as single Shoup products are canonical and equal to the stage followed by the scaling."""
+    q = P.ntt_primes(1, logn_max=16)[0]
+    n = 1 << 16
+    rng = np.random.default_rng(7)
+    ninv = pow(n, -1, q)
+    tw = int(rng.integers(1, q))
+    niw = ninv * tw % q
+    u = rng.integers(0, 2 * q, 4096, dtype=np.int64).astype(U64)
+    w = rng.integers(0, 2 * q, 4096, dtype=np.int64).astype(U64)
+    u[:2], w[:2] = [2 * q - 1, 0], [0, 2 * q - 1]
+    folded_x = csub(mul_shoup_lazy(u + w, U64(ninv), shoup_quotient(ninv, q), q), q)
+    folded_y = csub(mul_shoup_lazy(u - w + U64(2 * q), U64(niw), shoup_quotient(niw, q), q), q)
+    s = csub(u + w, 2 * q)
+    d = mul_shoup_lazy(u - w + U64(2 * q), U64(tw), shoup_quotient(tw, q), q)
+    sep_x = csub(mul_shoup_lazy(s, U64(ninv), shoup_quotient(ninv, q), q), q)
+    sep_y = csub(mul_shoup_lazy(d, U64(ninv), shoup_quotient(ninv, q), q), q)
+    assert folded_x.max() < q and folded_y.max() < q
+    np.testing.assert_array_equal(folded_x, sep_x)
+    np.testing.assert_array_equal(folded_y, sep_y)
+    uo, wo = u.astype(object), w.astype(object)
+    assert (folded_x.astype(object) == (uo + wo) * ninv % q).all()
+    assert (folded_y.astype(object) == (uo - wo) * tw * ninv % q).all()
