@@ -92,6 +92,21 @@ __device__ __forceinline__ void gs2(uint32_t& x, uint32_t& y, uint2 w, uint32_t 
     x = s;
     y = mul_shoup_lazy(d, w.x, w.y, q);
 }
+// The first stage of a transform whose inputs are canonical residues (below q), as the rows
+// of every call are: the forward's x needs no reduction below 2q, the inverse's x + y is
+// already below 2q. Outputs stay in the ranges of ct2 ([0, 4q)) and gs2 ([0, 2q)).
+__device__ __forceinline__ void ct2_first(uint32_t& x, uint32_t& y, uint2 w, uint32_t q) {
+    uint32_t t = mul_shoup_lazy(y, w.x, w.y, q);
+    uint32_t x0 = x;
+    x = x0 + t;
+    y = x0 - t + 2 * q;
+}
+__device__ __forceinline__ void gs2_first(uint32_t& x, uint32_t& y, uint2 w, uint32_t q) {
+    uint32_t s = x + y;
+    uint32_t d = x - y + 2 * q;
+    x = s;
+    y = mul_shoup_lazy(d, w.x, w.y, q);
+}
 
 // ---- inverse cross pass: grid (blocks over NC/4 quad positions, chunk rows); 4 positions per
 // thread; the last log2(C) Gentleman-Sande stages and the N^-1 scaling. The scaling rides on the
@@ -205,8 +220,13 @@ __device__ __forceinline__ void quarter_inv(const L2Args& a, int i, int c) {
             const int half = 1 << k, kf = 4 - k;
 #pragma unroll
             for (int e = 0; e < 32; ++e)
-                if ((e & half) == 0)
-                    gs2(v[e], v[e + half], __ldg(&twc[(size_t)((1 << kf) - 1 + (e >> (5 - kf))) * T]), q);
+                if ((e & half) == 0) {
+                    const uint2 w = __ldg(&twc[(size_t)((1 << kf) - 1 + (e >> (5 - kf))) * T]);
+                    if (k == 0)
+                        gs2_first(v[e], v[e + half], w, q);
+                    else
+                        gs2(v[e], v[e + half], w, q);
+                }
         }
 #pragma unroll
         for (int e = 0; e < 32; ++e) work[pC + e] = v[e];
@@ -417,7 +437,13 @@ __device__ __forceinline__ void dit_local(const L2Args& a, int i, int j) {
         const int half = 16 >> k;
 #pragma unroll
         for (int e = 0; e < 32; ++e)
-            if ((e & half) == 0) ct2(v[e], v[e + half], __ldg(&tw[(1 << k) + (e >> (5 - k))]), q);
+            if ((e & half) == 0) {
+                const uint2 w = __ldg(&tw[(1 << k) + (e >> (5 - k))]);
+                if (k == 0)
+                    ct2_first(v[e], v[e + half], w, q);
+                else
+                    ct2(v[e], v[e + half], w, q);
+            }
     }
 #pragma unroll
     for (int e = 0; e < 32; ++e) work[pA + L::kSA * e] = v[e];

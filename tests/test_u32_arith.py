@@ -46,7 +46,8 @@ def forward_lazy(a, q, psi):
         t //= 2
         v = a.reshape(m, 2, t)
         w, wq = psi_rev[m:2 * m, None], psi_rev_q[m:2 * m, None]
-        x2 = csub(v[:, 0, :], 2 * q)
+        # the kernels' first stage takes canonical inputs and skips this reduction
+        x2 = v[:, 0, :].copy() if m == 1 else csub(v[:, 0, :], 2 * q)
         tt = mul_shoup_lazy(v[:, 1, :], w, wq, q)
         assert x2.max() < 2 * q and tt.max() < 2 * q
         x, y = x2 + tt, x2 - tt + U64(2 * q)
@@ -70,7 +71,7 @@ def inverse_lazy(A, q, psi):
         v = a.reshape(h, 2, t)
         w, wq = pinv_rev[h:2 * h, None], pinv_rev_q[h:2 * h, None]
         x, y = v[:, 0, :], v[:, 1, :]
-        s = csub(x + y, 2 * q)
+        s = x + y if m == n else csub(x + y, 2 * q)   # first stage: canonical inputs, x + y < 2q
         d = x - y + U64(2 * q)
         assert s.max() < 2 * q and d.max() < 4 * q and d.min() > 0
         v[:, 0, :], v[:, 1, :] = s, mul_shoup_lazy(d, w, wq, q)
