@@ -335,6 +335,7 @@ __device__ __forceinline__ void dit_cross_row(const L2Args& a, int i, int p0, in
             uint32_t y[C];
 #pragma unroll
             for (int jj = 0; jj < C; ++jj) y[jj] = k == 0 ? x[jj].x : k == 1 ? x[jj].y : k == 2 ? x[jj].z : x[jj].w;
+            y[0] = csub(y[0], 2 * q);  // the local pass stores [0, 4q)
 #pragma unroll
             for (int jj = 1; jj < C; ++jj) {
                 const uint4 t4 = tw2[2 * (jj - 1) + (k >> 1)];
@@ -491,10 +492,11 @@ __device__ __forceinline__ void dit_local(const L2Args& a, int i, int j) {
 #pragma unroll
         for (int e = 0; e < 32; ++e) row[rbits<5>(e) * T + tid] = csub(csub(v[e], 2 * q), q);
     } else {
-        // the cross pass takes its inputs in [0, 2q) (twists are lazy Shoup products, the DFT's
-        // butterflies keep [0, 2q)), so one conditional subtraction suffices here
+        // stored as they are, in [0, 4q): the cross pass's twists (lazy Shoup products, any
+        // 32-bit input) bring streams j >= 1 below 2q and it reduces stream 0 itself, after
+        // which its DFT keeps [0, 2q)
 #pragma unroll
-        for (int e = 0; e < 32; ++e) __stcg(&tmp[rbits<5>(e) * T + tid], csub(v[e], 2 * q));
+        for (int e = 0; e < 32; ++e) __stcg(&tmp[rbits<5>(e) * T + tid], v[e]);
         if (a.fuse && last_of_row(a, i, C)) dit_cross_row<LOG_T + 5, LOG_C, TAIL, COH>(a, i, tid, T);
     }
 }

@@ -145,10 +145,11 @@ def _bitrev_small(x, bits):
 @pytest.mark.parametrize("log_c", [1, 2, 3])
 def test_two_pass_forward_cross_pass_ranges(log_c):
     """The forward two-pass cross pass at the largest accepted prime with every input of the C
-    streams anywhere in [0, 2q) (the local pass stores with one conditional subtraction): the
-    twists are lazy Shoup products in [0, 2q), the C-point cyclic DFT's butterflies (trivial ones
-    at omega^0, Gentleman-Sande ones otherwise) keep [0, 2q), and after one final conditional
-    subtraction output t equals sum_j omega^(t j) twist_j y_j mod q, canonical."""
+    streams anywhere in [0, 4q) (the local pass stores its Cooley-Tukey outputs unreduced): stream
+    0 gets one conditional subtraction of 2q, the twists of the other streams are lazy Shoup
+    products in [0, 2q), the C-point cyclic DFT's butterflies (trivial ones at omega^0,
+    Gentleman-Sande ones otherwise) keep [0, 2q), and after one final conditional subtraction
+    output t equals sum_j omega^(t j) twist_j y_j mod q, canonical."""
     C = 1 << log_c
     q = P.ntt_primes(1, logn_max=16)[0]
     rng = np.random.default_rng(40 + log_c)
@@ -156,13 +157,14 @@ def test_two_pass_forward_cross_pass_ranges(log_c):
     om = [pow(omega, m, q) for m in range(C // 2)]
     om_q = [shoup_quotient(w, q) for w in om]
     for trial in range(4):
-        y0 = rng.integers(0, 2 * q, (C, 256), dtype=np.int64).astype(U64)
+        y0 = rng.integers(0, 4 * q, (C, 256), dtype=np.int64).astype(U64)
         if trial == 1:
-            y0[:] = 2 * q - 1
+            y0[:] = 4 * q - 1
         if trial == 2:
             y0[:] = 0
         tw = rng.integers(1, q, C, dtype=np.int64)
         y = y0.copy()
+        y[0] = csub(y[0], 2 * q)
         for j in range(1, C):
             y[j] = mul_shoup_lazy(y[j], U64(tw[j]), shoup_quotient(int(tw[j]), q), q)
         assert y.max() < 2 * q
