@@ -40,6 +40,7 @@ struct NttArgs {
     const uint2* tw;    // [nmod][N]
     const uint2* twC;   // [nmod][C][31][T]
     const uint2* ninv;  // [nmod]
+    const uint2* ninv_w1;  // [nmod] N^-1 tw[1] (the single-CTA inverse's last stage, scaling folded in)
     int* status;        // device error word (FHE_ETIMEOUT on an expired wait)
     int contiguous;     // row order: 0 = interleaved across clusters, 1 = contiguous ranges
     const RowRef* rowtab;    // if set: row r is rowtab[r] (any buffer, any modulus) ...
@@ -83,6 +84,21 @@ __device__ __forceinline__ void ct_bfly(uint32_t& x, uint32_t& y, uint2 w, uint3
 // Inverse Gentleman-Sande butterfly (Harvey): x, y in [0, 2q) -> [0, 2q).
 __device__ __forceinline__ void gs_bfly(uint32_t& x, uint32_t& y, uint2 w, uint32_t q) {
     uint32_t s = csub(x + y, 2 * q);
+    uint32_t d = x - y + 2 * q;
+    x = s;
+    y = mul_shoup_lazy(d, w.x, w.y, q);
+}
+
+// First stages on canonical residues (below q), as loaded from a row: the forward's x needs no
+// reduction below 2q and the inverse's x + y is already below 2q.
+__device__ __forceinline__ void ct_bfly_first(uint32_t& x, uint32_t& y, uint2 w, uint32_t q) {
+    uint32_t t = mul_shoup_lazy(y, w.x, w.y, q);
+    uint32_t x0 = x;
+    x = x0 + t;
+    y = x0 - t + 2 * q;
+}
+__device__ __forceinline__ void gs_bfly_first(uint32_t& x, uint32_t& y, uint2 w, uint32_t q) {
+    uint32_t s = x + y;
     uint32_t d = x - y + 2 * q;
     x = s;
     y = mul_shoup_lazy(d, w.x, w.y, q);
@@ -245,7 +261,8 @@ ntt_fwd_kernel(const NttArgs a) {
             for (int e = 0; e < 32; ++e) v[e] = __ldg(&data[tid + T * e]);
         }
 
-        // ---- round A: 5 stages, element e at p = tid + T*e
+        // ---- round A: 5 stages, element e at p = tid + T*e (with C = 1 the first stage takes the
+        // row's canonical residues)
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
             const int half = 16 >> k;
@@ -253,7 +270,10 @@ ntt_fwd_kernel(const NttArgs a) {
             for (int e = 0; e < 32; ++e) {
                 if ((e & half) == 0) {
                     uint2 w = __ldg(&tw[(1 << k) * (C + c) + (e >> (5 - k))]);
-                    ct_bfly(v[e], v[e + half], w, q);
+                    if (C == 1 && k == 0)
+                        ct_bfly_first(v[e], v[e + half], w, q);
+                    else
+                        ct_bfly(v[e], v[e + half], w, q);
                 }
             }
         }
@@ -419,7 +439,10 @@ ntt_inv_kernel(const NttArgs a) {
                 for (int e = 0; e < 32; ++e) {
                     if ((e & half) == 0) {
                         uint2 w = twc[(1 << kf) - 1 + (e >> (5 - kf))];
-                        gs_bfly(v[e], v[e + half], w, q);
+                        if (k == 0)
+                            gs_bfly_first(v[e], v[e + half], w, q);  // the row's canonical residues
+                        else
+                            gs_bfly(v[e], v[e + half], w, q);
                     }
                 }
             }
@@ -460,7 +483,7 @@ ntt_inv_kernel(const NttArgs a) {
 #pragma unroll
         for (int e = 0; e < 32; ++e) v[e] = work[pA + L::kSA * e];
 #pragma unroll
-        for (int k = 4; k >= 0; --k) {
+        for (int k = 4; k >= (C == 1 ? 1 : 0); --k) {
             const int half = 16 >> k;
 #pragma unroll
             for (int e = 0; e < 32; ++e) {
@@ -472,8 +495,17 @@ ntt_inv_kernel(const NttArgs a) {
         }
         const uint2 ni = __ldg(&a.ninv[mod]);
         if constexpr (C == 1) {
+            // the last stage (pairs e, e + 16, twiddle tw[1]) with N^-1 folded in: (x + y) N^-1
+            // and (x - y) (tw[1] N^-1), one Shoup product each, canonical
+            const uint2 niw = __ldg(&a.ninv_w1[mod]);
 #pragma unroll
-            for (int e = 0; e < 32; ++e) data[tid + T * e] = mul_shoup(v[e], ni.x, ni.y, q);
+            for (int e = 0; e < 16; ++e) {
+                const uint32_t x = v[e], y = v[e + 16];
+                v[e] = mul_shoup(x + y, ni.x, ni.y, q);
+                v[e + 16] = mul_shoup(x - y + 2 * q, niw.x, niw.y, q);
+            }
+#pragma unroll
+            for (int e = 0; e < 32; ++e) data[tid + T * e] = v[e];
             __syncthreads();
         } else {
             constexpr int PER = NC / C;
@@ -717,6 +749,7 @@ int launch(const fhe_ctx* ctx, const NttTables& t, int variant, bool inverse, ui
     args.tw = inverse ? t.inv : t.fwd;
     args.twC = inverse ? t.invC[variant & 1] : t.fwdC[variant & 1];
     args.ninv = t.ninv;
+    args.ninv_w1 = t.ninv_w1;
     args.status = ctx->d_status;
     args.contiguous = TWS ? 1 : 0;
     args.rowtab = rowtab;
