@@ -40,6 +40,10 @@ namespace {
 constexpr int kLogPT = 9;
 constexpr int kPT = 1 << kLogPT;           // threads per CTA
 constexpr size_t kChunk4 = 4096;           // 16-byte words per elementwise tile (16384 residues)
+// Conv tiles are shorter: each converts 4096 coefficients into every destination limb (up to
+// 64), so with the 16384 of the other stages one tile would run for far longer than any other
+// and hold up the transforms that wait for it.
+constexpr size_t kConvChunk2 = 2048;       // 8-byte words per Conv tile
 constexpr uint32_t kNoDep = 0xffffffffu;
 constexpr size_t kAlign = 256;
 
@@ -138,7 +142,7 @@ __device__ __forceinline__ void run_conv_ns(const ConvArgs& c, const uint32_t* s
 __device__ __forceinline__ void run_conv(const ConvArgs& c, uint32_t* work, uint32_t chunk) {
     conv_load_hat(c, c.nsrc, work);
     __syncthreads();
-    const size_t L2 = c.L4 * 2, n0 = (size_t)chunk * kChunk4 * 2, n1 = min(L2, n0 + kChunk4 * 2);
+    const size_t L2 = c.L4 * 2, n0 = (size_t)chunk * kConvChunk2, n1 = min(L2, n0 + kConvChunk2);
     switch (c.nsrc) {
         case 1: run_conv_ns<1>(c, work, n0, n1); break;
         case 2: run_conv_ns<2>(c, work, n0, n1); break;
@@ -251,7 +255,7 @@ struct HmInst {
     int op;
     uint32_t logN;
     int nl, B, dnum, ext, C;
-    size_t N, limb, L4, nch, nch2;  // residues per limb (B N), 16-byte words, tiles per limb (4- and 2-word units)
+    size_t N, limb, L4, nch, nconv;  // residues per limb (B N), 16-byte words, elementwise and Conv tiles per limb
     int nd[16];                     // destination limbs of slice j's ModUp Conv
     size_t rows_t0, rows_t1;        // rows of the two shared NTT temporaries
     size_t bytes;                   // scratch of one instance
@@ -453,7 +457,7 @@ void hm_build(Builder& b, const HmInst& h, uint8_t* sb, uint32_t pred_ctr, uint3
         const uint32_t cd = (uint32_t)(b.P.conv.size() - 1);
         const uint32_t c_conv = b.counter();
         size_t m = b.P.tiles.size();
-        for (size_t c = 0; c < h.nch2; ++c) b.tile(PK_CONV, 0, cd, 0, (uint32_t)c, c_intt, n_intt, kNoDep, 0, c_conv);
+        for (size_t c = 0; c < h.nconv; ++c) b.tile(PK_CONV, 0, cd, 0, (uint32_t)c, c_intt, n_intt, kNoDep, 0, c_conv);
         take(2, m);
         LimbMap lm;
         memset(&lm, 0, sizeof(lm));
@@ -463,7 +467,7 @@ void hm_build(Builder& b, const HmInst& h, uint8_t* sb, uint32_t pred_ctr, uint3
         }
         const uint32_t d = ntt_stage(b, h.logN, false, dst, B, &lm, nullptr, (size_t)nd * B, tj[j], nullptr);
         m = b.P.tiles.size();
-        ntt_tiles(b, d, (uint16_t)log_c_of(h.logN), (size_t)nd * B, C, c_conv, (uint32_t)h.nch2, c_modup);
+        ntt_tiles(b, d, (uint16_t)log_c_of(h.logN), (size_t)nd * B, C, c_conv, (uint32_t)h.nconv, c_modup);
         take(3, m);
         n_modup += (uint32_t)((size_t)nd * B * C);
     }
@@ -532,7 +536,7 @@ void hm_build(Builder& b, const HmInst& h, uint8_t* sb, uint32_t pred_ctr, uint3
             b.P.conv.push_back(conv_args(ctx, ctx->moddown, ks + ((size_t)c * ext + nl) * limb, K, smod,
                                          y + (size_t)c * nl * limb, nl, dmod, limb, ctx->p_inv, qlinv, nl - 1));
             const size_t m = b.P.tiles.size();
-            for (size_t ch = 0; ch < h.nch2; ++ch)
+            for (size_t ch = 0; ch < h.nconv; ++ch)
                 b.tile(PK_CONV, 0, (uint32_t)(b.P.conv.size() - 1), 0, (uint32_t)ch, c_pintt[c],
                        (uint32_t)((size_t)K * B * C), kNoDep, 0, c_md);
             take(6, m);
@@ -553,7 +557,7 @@ void hm_build(Builder& b, const HmInst& h, uint8_t* sb, uint32_t pred_ctr, uint3
         for (int c = 0; c < 2; ++c)
             for (size_t ch = 0; ch < h.nch; ++ch)
                 b.tile(PK_LAST_FIX, 0, last_desc, c, (uint32_t)ch, c_lintt, (uint32_t)(2 * (size_t)B * C), c_md,
-                       (uint32_t)(2 * h.nch2), c_fix);
+                       (uint32_t)(2 * h.nconv), c_fix);
         take(7, m);
     }
     // stage 8: forward NTT of z' with the fused RESCALE tail, writing the output
@@ -733,7 +737,7 @@ int persist_create(const fhe_ctx* ctx, const fhe_op* ops, int n, const std::vect
             h.limb = h.N * h.B;
             h.L4 = h.limb / 4;
             h.nch = (h.L4 + kChunk4 - 1) / kChunk4;
-            h.nch2 = (2 * h.L4 + 2 * kChunk4 - 1) / (2 * kChunk4);
+            h.nconv = (2 * h.L4 + kConvChunk2 - 1) / kConvChunk2;
             for (int j = 0; j < h.dnum; ++j)
                 h.nd[j] = h.ext - (std::min(h.nl, (j + 1) * ctx->alpha) - j * ctx->alpha);
             h.bytes = hm_bytes(ctx, h);
@@ -747,7 +751,7 @@ int persist_create(const fhe_ctx* ctx, const fhe_op* ops, int n, const std::vect
     P->slot_bytes = P->hm.empty() ? 0 : P->hm[0].bytes;
     if (!P->hm.empty()) {
         size_t s = std::max<size_t>(1, slot_budget / P->slot_bytes);
-        P->slots = (int)std::min<size_t>(std::min<size_t>(s, 64), P->hm.size());
+        P->slots = (int)std::min<size_t>(s, P->hm.size());
         for (size_t k = 0; k < P->hm.size(); ++k) P->hm[k].slot = (int)(k % P->slots);
     }
     int rc = build_tables(*P, nullptr);  // sizes and tile order only
