@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--serving-seconds", type=float, default=2.0, help="seconds of arrivals per serving run")
     ap.add_argument("--batch-ops", type=int, default=1000)
     ap.add_argument("--e2e-limbs", type=int, default=E2E_LIMBS, help="limbs per chunk of the end-to-end pipeline")
+    ap.add_argument("--ntt-batch", type=int, default=NTT_BATCH,
+                    help="polynomials per limb of the NTT step (smaller for counter captures)")
     ap.add_argument("--hmult-batch", type=int, default=HM_BATCH,
                     help="ciphertext pairs per HMULT call (and ciphertexts per HROTATE / CMULT / HADD call)")
     return ap.parse_args()
@@ -541,9 +543,11 @@ def ours(args):
             "vs_baseline": None,
             "dtype": "u32",
             "data": "synthetic",
-            "config": {"workload": "batched negacyclic NTT+INTT, N=2^16, 44 RNS limbs (30-bit primes), "
-                                   "64 polynomials (704 MiB); one op = one limb transform",
-                       "path": head, "l2": "inputs larger than L2 (704 MiB), no flush",
+            "config": {"workload": "batched negacyclic NTT+INTT, N=2^16, %d RNS limbs (30-bit primes), "
+                                   "%d polynomials (%d MiB); one op = one limb transform"
+                                   % (NTT_LIMBS, NTT_BATCH, rows * N * 4 >> 20),
+                       "path": head, "l2": ("inputs larger than L2 (%d MiB), no flush" if rows * N * 4 > 129e6 else
+                              "inputs of %d MiB, which fit in L2; no flush") % (rows * N * 4 >> 20),
                        "parallelism": "replicas" if ws > 1 else "1 GPU"},
             "paths": results,
             "hmult": hm,
@@ -833,7 +837,9 @@ def serving_bench(args, fhe, qs, ps):
 
 
 def main():
+    global NTT_BATCH
     args = parse()
+    NTT_BATCH = args.ntt_batch
     if args.impl == "reference":
         reference_arm(args)
     else:

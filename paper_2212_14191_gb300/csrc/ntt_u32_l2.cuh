@@ -418,15 +418,25 @@ __device__ __forceinline__ void dit_local(const L2Args& a, int i, int j) {
         const uint32_t* yr = a.tail.y + (((size_t)t.c * a.tail.nl + t.i) * a.batch + t.p) * N;
         const uint32_t* lr = a.tail.last + ((size_t)t.c * a.batch + t.p) * N;
         const uint2 qlinv = __ldg(&a.tail.qlinv[t.i]);
-        const uint32_t ql = a.tail.ql, half = (ql - 1) / 2, qlm = ql % q;
-        const bool one_sub = ql <= 2 * (uint64_t)q;  // last < q_l <= 2q: one subtraction reduces it
+        if (tid == 0 && a.fuse) {
+            // the row's cross pass, run by the last of its C local passes, reads all of the
+            // row's ks and d: each local pass brings its own part of them into L2 meanwhile
+            const size_t part = (size_t)j * NC;
+            ptx::prefetch_l2(a.tail.ks + (((size_t)t.c * a.tail.ext + t.i) * a.batch + t.p) * N + part, NC * 4);
+            ptx::prefetch_l2(a.tail.d + (((size_t)t.c * a.tail.nl + t.i) * a.batch + t.p) * N + part, NC * 4);
+        }
+        // The Shoup product takes any 32-bit word, so the centred last limb needs no reduction
+        // first: x = last + (q - q_l mod q) stands for last - q_l (x < 2^31). The first
+        // butterfly stage pairs e with e + 16 and takes x-side inputs below 2q and y-side
+        // inputs of any size, so only e < 16 is brought from [0, 3q) below 2q.
+        const uint32_t half = (a.tail.ql - 1) / 2, lift = q - a.tail.ql % q;
 #pragma unroll
         for (int e = 0; e < 32; ++e) {
             const size_t idx = (size_t)(tid + T * e) * C + j;
             const uint32_t lv = ld_tail<COH>(&lr[idx]), yv = ld_tail<COH>(&yr[idx]);
-            const uint32_t vm = one_sub ? csub(lv, q) : lv % q;
-            const uint32_t x = csub(lv > half ? vm + q - qlm : vm, q);
-            v[e] = csub(yv + mul_shoup(x, qlinv.x, qlinv.y, q), q);
+            const uint32_t x = lv > half ? lv + lift : lv;
+            const uint32_t z = yv + mul_shoup_lazy(x, qlinv.x, qlinv.y, q);
+            v[e] = e < 16 ? csub(z, q) : z;
         }
     } else {
 #pragma unroll

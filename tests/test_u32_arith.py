@@ -214,3 +214,37 @@ def test_two_pass_inverse_last_stage_with_scaling():
     uo, wo = u.astype(object), w.astype(object)
     assert (folded_x.astype(object) == (uo + wo) * ninv % q).all()
     assert (folded_y.astype(object) == (uo - wo) * tw * ninv % q).all()
+
+
+@pytest.mark.parametrize("ql_side", ["above", "below"])
+def test_fused_tail_load_without_reductions(ql_side):
+    """The fused RESCALE tail's load side (Sec. II-B: z_i = y_i + [last]_i q_l^-1 with the last
+    limb centred) as the local pass computes it: x = last, plus q - (q_l mod q) where last stands
+    for last - q_l, goes into a lazy Shoup product unreduced (x < 2^31), z = y + that product
+    lies in [0, 3q), and only the first half of the sub-transform (the x side of the first
+    butterfly stage) gets one conditional subtraction to [0, 2q). Checked with q_l above and
+    below q (the largest accepted prime as one of them) against exact integers, then as the input of a whole lazy forward transform
+    (its first stage asserts x < 2q), whose output must equal the oracle's transform of z."""
+    primes = sorted(P.ntt_primes(3, logn_max=16))        # primes[2] is the largest accepted
+    q, ql = (primes[1], primes[2]) if ql_side == "above" else (primes[2], primes[0])
+    assert (ql > q) == (ql_side == "above")
+    n = 1 << 10
+    rng = np.random.default_rng(11 if ql_side == "above" else 12)
+    last = rng.integers(0, ql, n, dtype=np.int64).astype(U64)
+    last[:4] = [0, (ql - 1) // 2, (ql - 1) // 2 + 1, ql - 1]       # both sides of the centring
+    y = rng.integers(0, q, n, dtype=np.int64).astype(U64)
+    y[4:6] = q - 1
+    qlinv = pow(ql, -1, q)
+    half, lift = (ql - 1) // 2, q - ql % q
+    x = np.where(last > U64(half), last + U64(lift), last)
+    assert x.max() < (1 << 31)
+    z = y + mul_shoup_lazy(x, U64(qlinv), shoup_quotient(qlinv, q), q)
+    assert z.max() < 3 * q
+    v = z.copy()
+    v[:n // 2] = csub(v[:n // 2], q)
+    assert v[:n // 2].max() < 2 * q
+    centred = [int(l) - ql if int(l) > half else int(l) for l in last]
+    want = np.array([(int(yy) + c * qlinv) % q for yy, c in zip(y, centred)], dtype=U64)
+    np.testing.assert_array_equal(v % U64(q), want)
+    psi = P.psi(q, n)
+    np.testing.assert_array_equal(forward_lazy(v, q, psi), O.ntt(want.astype(np.uint32), q, psi).astype(U64))
