@@ -240,18 +240,23 @@ size_t ks_scratch_limbs(int nl, int K, int alpha) {
     return (size_t)nl + dnum * (nl + K) + 2 * (size_t)(nl + K) + 2 * (size_t)nl;
 }
 
-// KS-1..KS-3: INTT of d2c (nl limbs, in place, NTT form in) and, per slice j, Conv
+// KS-1..KS-3: INTT into d2c (nl limbs: of src when given, else of d2c in place; NTT form in)
+// and, per slice j, Conv
 // Q_j -> (Q_l \ Q_j) u P and the NTT of the converted limbs into `digits` (dnum, ext, B, N):
 // slice j's converted limbs at j * ext, the q limbs outside the slice first, then P.
 int ks_modup(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, uint32_t* d2c, uint32_t* digits,
-             cudaStream_t st, NttScratch ns) {
+             cudaStream_t st, NttScratch ns, const uint32_t* src = nullptr) {
     const size_t N = 1ull << logN, limb = N * batch, L4 = limb / 4;
     const int K = ctx->np, ext = nl + K, alpha = ctx->alpha, nq = ctx->nq;
     const int nmod = (int)ctx->mods.size();
     const int dnum = (nl + alpha - 1) / alpha;
     int rc;
     // KS-1: INTT(d2)
-    if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, true, d2c, nl, batch, contiguous_map(ctx, 0, nl), st, ns))) return rc;
+    if (src)
+        rc = ntt_inv_from(ctx, logN, d2c, src, nl, batch, contiguous_map(ctx, 0, nl), st, ns);
+    else
+        rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, true, d2c, nl, batch, contiguous_map(ctx, 0, nl), st, ns);
+    if (rc) return rc;
     for (int j = 0; j < dnum; ++j) {
         const int lo = j * alpha, hi = std::min(nl, (j + 1) * alpha);
         uint32_t* tmp = digits + (size_t)j * ext * limb;
@@ -384,7 +389,8 @@ int ks_finish(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint32
 }
 
 // Key switching of d2 (NTT form) into `out` (2, nl, B, N); accumulate != 0 adds to out.
-// d2c (nl limbs of scratch) may already hold a copy of d2 when d2c_ready != 0.
+// d2c (nl limbs of scratch) may already hold a copy of d2 when d2c_ready != 0; otherwise the
+// INTT reads d2 itself (or a copy of it, where the inverse cannot run out of place).
 // scale_lt > 0 (the fused HMULT + RESCALE tail, out == nullptr): q limbs t < scale_lt of ks and
 // of y come out multiplied by P^-1 q_{nl-1}^-1, the factors the tail would otherwise apply.
 // Scratch: d2c (nl limbs), ModUp digits (dnum (nl + K)), ks (2 (nl + K)), y (2 nl).
@@ -399,8 +405,7 @@ int keyswitch_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const u
     uint32_t* ks = tmp_all + (size_t)dnum * ext * limb;
     uint32_t* y = ks + 2 * (size_t)ext * limb;
     int rc;
-    if (!d2c_ready) FHE_CUDA_TRY(cudaMemcpyAsync(d2c, d2, (size_t)nl * limb * 4, cudaMemcpyDeviceToDevice, st));
-    if ((rc = ks_modup(ctx, logN, nl, batch, d2c, tmp_all, st, ns))) return rc;
+    if ((rc = ks_modup(ctx, logN, nl, batch, d2c, tmp_all, st, ns, d2c_ready ? nullptr : d2))) return rc;
     return ks_finish(ctx, logN, nl, batch, d2, tmp_all, evk, out, accumulate, ks, y, st, ns, scale_lt);
 }
 
@@ -453,10 +458,14 @@ int hmult_relin_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const
     uint32_t* ks_scratch = d2 + (size_t)nl * limb;  // begins with d2c
     int qidx[kMaxLimbs];
     for (int i = 0; i < nl; ++i) qidx[i] = i;
-    k_tensor<<<stream_grid(ctx, L4, nl), 256, 0, st>>>(TensorArgs{a, b, out, out + (size_t)nl * limb, d2, ks_scratch,
+    // the tensor product writes the copy of d2 that the INTT transforms in place, unless the
+    // INTT can read d2 itself
+    const bool oop = ntt_inv_out_of_place(ctx, logN);
+    k_tensor<<<stream_grid(ctx, L4, nl), 256, 0, st>>>(TensorArgs{a, b, out, out + (size_t)nl * limb, d2,
+                                                                oop ? nullptr : ks_scratch,
                                                                 L4, (size_t)nl * L4, modvec(ctx, qidx, nl), nullptr, 0});
     FHE_CUDA_TRY(cudaGetLastError());
-    return keyswitch_impl(ctx, logN, nl, batch, d2, evk, out, 1, ks_scratch, true, st, ns);
+    return keyswitch_impl(ctx, logN, nl, batch, d2, evk, out, 1, ks_scratch, !oop, st, ns);
 }
 
 // HMULT + RESCALE with the fused tail (k_relin_last .. k_hmult_final above): one forward NTT of
@@ -482,10 +491,12 @@ int hmult_fused(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint
     // P^-1 q_l^-1 on ks and y (folded into HBM-bound passes and into Conv's constants), so that
     // the combine below needs no multiplication
     const uint2* qlinv = ctx->ql_inv + (size_t)(nl - 1) * ctx->nq;
-    k_tensor<<<stream_grid(ctx, L4, nl), 256, 0, st>>>(TensorArgs{a, b, dd, dd + (size_t)nl * limb, d2, ksx, L4,
-                                                                (size_t)nl * L4, modvec(ctx, qidx, nl), qlinv, nl - 1});
+    const bool oop = ntt_inv_out_of_place(ctx, logN);  // else the tensor product also writes d2c
+    k_tensor<<<stream_grid(ctx, L4, nl), 256, 0, st>>>(TensorArgs{a, b, dd, dd + (size_t)nl * limb, d2,
+                                                                oop ? nullptr : ksx, L4, (size_t)nl * L4,
+                                                                modvec(ctx, qidx, nl), qlinv, nl - 1});
     FHE_CUDA_TRY(cudaGetLastError());
-    int rc = keyswitch_impl(ctx, logN, nl, batch, d2, evk, nullptr, 0, ksx, true, st, ns, nl - 1);
+    int rc = keyswitch_impl(ctx, logN, nl, batch, d2, evk, nullptr, 0, ksx, !oop, st, ns, nl - 1);
     if (rc) return rc;
     const uint32_t ql = ctx->mods[nl - 1];
     const uint2 pinv_l = ctx->p_inv_h[nl - 1];
@@ -642,8 +653,7 @@ int hrotate_hoisted_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, i
     uint32_t* ks = dk + (size_t)dnum * ext * limb;
     uint32_t* y = ks + 2 * (size_t)ext * limb;
     int rc;
-    FHE_CUDA_TRY(cudaMemcpyAsync(c1c, ct + (size_t)nl * limb, (size_t)nl * limb * 4, cudaMemcpyDeviceToDevice, st));
-    if ((rc = ks_modup(ctx, logN, nl, batch, c1c, digits, st, ns))) return rc;
+    if ((rc = ks_modup(ctx, logN, nl, batch, c1c, digits, st, ns, ct + (size_t)nl * limb))) return rc;
     for (int r = 0; r < nrot; ++r) {
         const uint32_t k = galois[r];
         uint32_t* o = out + (size_t)r * 2 * nl * limb;

@@ -79,7 +79,7 @@ struct TensorArgs {
     uint32_t* d0;
     uint32_t* d1;
     uint32_t* d2;
-    uint32_t* d2c;
+    uint32_t* d2c;  // a second copy of d2, or null
     size_t L4, comp4;
     ModVec m;
     const uint2* dscale;
@@ -111,7 +111,7 @@ __device__ __forceinline__ void tensor_range(const TensorArgs& t, int l, size_t 
         st4(t.d0, idx, r0);
         st4(t.d1, idx, r1);
         st4(t.d2, idx, r2);
-        st4(t.d2c, idx, r2);
+        if (t.d2c) st4(t.d2c, idx, r2);
     }
 }
 

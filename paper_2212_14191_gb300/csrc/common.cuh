@@ -204,6 +204,14 @@ struct HmultTail {
     uint32_t ql;
     int nl, nout, ext;
 };
+// True when the inverse NTT of this ring degree runs the two-pass plain kernels, which can read
+// their input from another buffer than the one they write.
+bool ntt_inv_out_of_place(const fhe_ctx* ctx, uint32_t logN);
+// Inverse NTT of src (n_limbs x batch rows, NTT domain, limb moduli from map) into dst: read
+// directly by the two-pass kernels where ntt_inv_out_of_place holds, else copied into dst and
+// transformed there. src is left unchanged either way.
+int ntt_inv_from(const fhe_ctx* ctx, uint32_t logN, uint32_t* dst, const uint32_t* src, int n_limbs, int batch,
+                 const LimbMap& map, cudaStream_t st, NttScratch scr);
 // True when the forward NTT of this ring degree runs the two-pass plain kernels (the only ones
 // with the fused tail); the tail then runs as one call to ntt_u32_l2_tail.
 bool ntt_tail_fusable(const fhe_ctx* ctx, int path, uint32_t logN);

@@ -50,12 +50,13 @@ __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_dit_local_kernel
 template <int LOG_T, int LOG_C, bool TAIL>
 int run_l2(const fhe_ctx* ctx, const NttTables& t, int shape, bool inverse, uint32_t* d, int rows, int batch,
            const LimbMap& map, const RowRef* rowtab, cudaStream_t st, uint32_t* temp, size_t temp_bytes,
-           const HmultTail* tail) {
+           const HmultTail* tail, const uint32_t* src) {
     constexpr int T = 1 << LOG_T, C = 1 << LOG_C, NC = 32 * T, N = NC * C;
     constexpr int smem = PadLayout<LOG_T>::kWords * 4;
     // forward: decimation in time (local NC-point transforms, then twist + C-point DFT);
     // inverse: decimation in frequency (quarter pass, then cross stages with N^-1)
     if (TAIL && (inverse || rowtab || !tail)) return set_error(FHE_EINVAL, "fused tail: forward, limb-map rows only");
+    if (src && (!inverse || rowtab)) return set_error(FHE_EINVAL, "out-of-place two-pass NTT: inverse, limb-map rows only");
     auto qk = inverse ? ntt_quarter_inv_kernel<LOG_T, LOG_C> : ntt_dit_local_kernel<LOG_T, LOG_C, TAIL>;
     FHE_CUDA_TRY(cudaFuncSetAttribute(qk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int carve = (int)((kMinB<LOG_T> * (smem + 1024) * 100 + 228 * 1024 - 1) / (228 * 1024));
@@ -78,6 +79,7 @@ int run_l2(const fhe_ctx* ctx, const NttTables& t, int shape, bool inverse, uint
     a.twist = t.dit_twist[shape];
     a.omega = t.dit_omega[shape];
     a.map = map;
+    a.src_off = src ? src - d : 0;
     memset(&a.tail, 0, sizeof(a.tail));
     if (TAIL) a.tail = *tail;
     // chunk rows: N residues of scratch and one completion counter each
@@ -111,7 +113,8 @@ int run_l2(const fhe_ctx* ctx, const NttTables& t, int shape, bool inverse, uint
 namespace {
 template <bool TAIL>
 int ntt_u32_l2_impl(const fhe_ctx* ctx, uint32_t logN, int shape, bool inverse, uint32_t* d, int rows, int batch,
-                    const LimbMap& map, const RowRef* rowtab, cudaStream_t st, NttScratch scr, const HmultTail* tail) {
+                    const LimbMap& map, const RowRef* rowtab, cudaStream_t st, NttScratch scr, const HmultTail* tail,
+                    const uint32_t* src = nullptr) {
     const NttTables& t = ctx->ntt[logN];
     uint32_t* temp = scr.p ? scr.p : ctx->ntt_temp;
     const size_t temp_bytes = scr.p ? scr.bytes : kNttTempBytes;
@@ -120,13 +123,13 @@ int ntt_u32_l2_impl(const fhe_ctx* ctx, uint32_t logN, int shape, bool inverse, 
     if (!ntt_variant_shape(logN, shape, &log_t, &log_c) || log_c == 0)
         return set_error(FHE_EINVAL, "two-pass NTT needs N >= 2^15");
     if (log_t == 9 && log_c == 2)
-        return run_l2<9, 2, TAIL>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes, tail);
+        return run_l2<9, 2, TAIL>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes, tail, src);
     if (log_t == 9 && log_c == 1)
-        return run_l2<9, 1, TAIL>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes, tail);
+        return run_l2<9, 1, TAIL>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes, tail, src);
     if (log_t == 8 && log_c == 3)
-        return run_l2<8, 3, TAIL>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes, tail);
+        return run_l2<8, 3, TAIL>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes, tail, src);
     if (log_t == 8 && log_c == 2)
-        return run_l2<8, 2, TAIL>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes, tail);
+        return run_l2<8, 2, TAIL>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes, tail, src);
     return set_error(FHE_EINVAL, "no two-pass kernel for this shape");
 }
 }  // namespace
@@ -134,6 +137,25 @@ int ntt_u32_l2_impl(const fhe_ctx* ctx, uint32_t logN, int shape, bool inverse, 
 int ntt_u32_l2(const fhe_ctx* ctx, uint32_t logN, int shape, bool inverse, uint32_t* d, int rows, int batch,
                const LimbMap& map, const RowRef* rowtab, cudaStream_t st, NttScratch scr) {
     return ntt_u32_l2_impl<false>(ctx, logN, shape, inverse, d, rows, batch, map, rowtab, st, scr, nullptr);
+}
+
+bool ntt_inv_out_of_place(const fhe_ctx* ctx, uint32_t logN) {
+    if (logN < 15 || logN > FHE_LOGN_MAX || ctx->ntt_variant[1][logN] >= kNttVariants) return false;
+    const int v = ctx->plain_variant[1][logN];
+    int log_t, log_c;
+    return ntt_variant_exchange(v) == 3 && ntt_variant_shape(logN, v, &log_t, &log_c) && log_c > 0;
+}
+
+int ntt_inv_from(const fhe_ctx* ctx, uint32_t logN, uint32_t* dst, const uint32_t* src, int n_limbs, int batch,
+                 const LimbMap& map, cudaStream_t st, NttScratch scr) {
+    if (ntt_inv_out_of_place(ctx, logN)) {
+        if (n_limbs == 0 || batch == 0) return FHE_OK;
+        const int v = ctx->plain_variant[1][logN];
+        return ntt_u32_l2_impl<false>(ctx, logN, v & 1, true, dst, n_limbs * batch, batch, map, nullptr, st, scr,
+                                      nullptr, src);
+    }
+    FHE_CUDA_TRY(cudaMemcpyAsync(dst, src, ((size_t)n_limbs * batch << logN) * 4, cudaMemcpyDeviceToDevice, st));
+    return ntt_any(ctx, FHE_NTT_DEFAULT, logN, true, dst, n_limbs, batch, map, st, scr);
 }
 
 bool ntt_tail_fusable(const fhe_ctx* ctx, int path, uint32_t logN) {

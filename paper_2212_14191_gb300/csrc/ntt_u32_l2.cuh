@@ -26,19 +26,27 @@ struct L2Args {
     const uint2* twC_sub;    // [nmod][1][31][T]
     const uint2* twist;      // [nmod][C-1][NC]
     const uint2* omega;      // [nmod][C/2]
+    ptrdiff_t src_off;       // inverse, limb-map rows: read row r at data + r N + src_off (0: in place)
     int* cnt;                // per chunk row: local-pass CTAs finished (zeroed before each chunk)
     int fuse;                // 1: the last local-pass CTA of a row runs its cross pass
     LimbMap map;
     HmultTail tail;          // TAIL instantiations of the forward kernels only
 };
 
-// Row r of a TAIL transform: component c, output limb i, polynomial p.
+// Row r of a TAIL transform: component c, polynomial p, output limb i, with i fastest, so that
+// the rows in flight together share the last limb's row (c, p), which each of them reads
+// whole; the row's modulus is entry c nout + i of the limb map.
 struct TailRow {
     int c, i, p;
 };
 __device__ __forceinline__ TailRow tail_row(const L2Args& a, int r) {
-    const int limb = r / a.batch;
-    return {limb / a.tail.nout, limb % a.tail.nout, r % a.batch};
+    const int cp = r / a.tail.nout;
+    return {cp / a.batch, r % a.tail.nout, cp % a.batch};
+}
+__device__ __forceinline__ void tail_mod(const L2Args& a, const TailRow& t, uint32_t* q, int* mod) {
+    const int l = t.c * a.tail.nout + t.i;
+    *q = a.map.q[l];
+    *mod = a.map.mod[l];
 }
 
 // The C local-pass CTAs of a row each count themselves in cnt[i] once their scratch stores
@@ -205,11 +213,12 @@ __device__ __forceinline__ void quarter_inv(const L2Args& a, int i, int c) {
     uint32_t q;
     int mod;
     const uint32_t* row = l2_row<N>(a, a.r0 + i, &q, &mod);
+    const uint32_t* src = row + a.src_off;
     uint32_t* tmp = a.temp + (size_t)i * N + c * NC;
     const uint2* tw = a.tw + (size_t)mod * N;
     uint32_t v[32];
 #pragma unroll
-    for (int e = 0; e < 32; ++e) v[e] = ld_row<COH>(&row[(rbits<5>(e) * T + tid) * C + rc]);
+    for (int e = 0; e < 32; ++e) v[e] = ld_row<COH>(&src[(rbits<5>(e) * T + tid) * C + rc]);
     // round C'
     {
         const int gidx = rbits<LOG_T>(tid);
@@ -297,6 +306,7 @@ __device__ __forceinline__ void dit_cross_row(const L2Args& a, int i, int p0, in
     const uint32_t* dr = nullptr;
     if constexpr (TAIL) {
         const TailRow t = tail_row(a, a.r0 + i);
+        tail_mod(a, t, &q, &mod);
         ksr = a.tail.ks + (((size_t)t.c * a.tail.ext + t.i) * a.batch + t.p) * N;
         dr = a.tail.d + (((size_t)t.c * a.tail.nl + t.i) * a.batch + t.p) * N;
         row = a.tail.out + (((size_t)t.c * a.tail.nout + t.i) * a.batch + t.p) * N;
@@ -410,11 +420,15 @@ __device__ __forceinline__ void dit_local(const L2Args& a, int i, int j) {
     int mod;
     uint32_t* row = l2_row<N>(a, a.r0 + i, &q, &mod);
     uint32_t* tmp = a.temp + (size_t)i * N + (size_t)j * NC;
+    TailRow t{};
+    if constexpr (TAIL) {
+        t = tail_row(a, a.r0 + i);
+        tail_mod(a, t, &q, &mod);
+    }
     const uint2* tw = a.tw_sub + (size_t)mod * NC;
     uint32_t v[32];
     if constexpr (TAIL) {
         // z' = y' + [last]_q q_l^-1 (last centred: values above (q_l - 1) / 2 stand for last - q_l)
-        const TailRow t = tail_row(a, a.r0 + i);
         const uint32_t* yr = a.tail.y + (((size_t)t.c * a.tail.nl + t.i) * a.batch + t.p) * N;
         const uint32_t* lr = a.tail.last + ((size_t)t.c * a.batch + t.p) * N;
         const uint2 qlinv = __ldg(&a.tail.qlinv[t.i]);

@@ -316,9 +316,11 @@ struct Builder {
 };
 
 // An NTT stage over `rows` rows (limb-map mode when rowtab is null: row r is limb r / batch of
-// data), with its scratch rows at `temp`; returns its descriptor index.
+// data), with its scratch rows at `temp`; an inverse in limb-map mode reads its rows from src
+// instead when given. Returns its descriptor index.
 uint32_t ntt_stage(Builder& b, uint32_t logN, bool inverse, uint32_t* data, int batch, const LimbMap* map,
-                   const RowRef* rowtab, size_t rows, uint32_t* temp, const HmultTail* tail) {
+                   const RowRef* rowtab, size_t rows, uint32_t* temp, const HmultTail* tail,
+                   const uint32_t* src = nullptr) {
     const fhe_ctx* ctx = b.P.ctx;
     const NttTables& t = ctx->ntt[logN];
     const NttTables& ts = ctx->ntt[kLogPT + 5];
@@ -342,6 +344,7 @@ uint32_t ntt_stage(Builder& b, uint32_t logN, bool inverse, uint32_t* data, int 
     a.fuse = 1;
     if (map) a.map = *map;
     if (tail) a.tail = *tail;
+    if (src) a.src_off = src - data;
     b.cnt_fix.push_back({nullptr, b.rowcnt_words});
     b.rowcnt_words += rows;
     b.P.ntt.push_back(a);
@@ -422,7 +425,7 @@ void hm_build(Builder& b, const HmInst& h, uint8_t* sb, uint32_t pred_ctr, uint3
     for (int i = 0; i < nl; ++i) qidx[i] = i;
     // stage 0: tensor product (the first tiles wait for the slot's previous instance)
     const uint32_t c_ten = b.counter();
-    b.P.ten.push_back(TensorArgs{o.a, o.b, dd, dd + (size_t)nl * limb, d2, ksx, L4, (size_t)nl * L4,
+    b.P.ten.push_back(TensorArgs{o.a, o.b, dd, dd + (size_t)nl * limb, d2, nullptr, L4, (size_t)nl * L4,
                                  modvec(ctx, qidx, nl), qlinv, nl - 1});
     const uint32_t ten_desc = (uint32_t)(b.P.ten.size() - 1);
     for (int l = 0; l < nl; ++l)
@@ -430,11 +433,11 @@ void hm_build(Builder& b, const HmInst& h, uint8_t* sb, uint32_t pred_ctr, uint3
             b.tile(PK_TENSOR, 0, ten_desc, l, (uint32_t)c, pred_ctr, pred_need, kNoDep, 0, c_ten);
     const uint32_t n_ten = (uint32_t)(nl * h.nch);
     take(0, mark0);
-    // stage 1: INTT of d2c
+    // stage 1: INTT of d2 into d2c (the local passes read d2, the cross passes write d2c)
     const uint32_t c_intt = b.counter();
     {
         LimbMap lm = contiguous_map(ctx, 0, nl);
-        const uint32_t d = ntt_stage(b, h.logN, true, ksx, B, &lm, nullptr, (size_t)nl * B, t0, nullptr);
+        const uint32_t d = ntt_stage(b, h.logN, true, ksx, B, &lm, nullptr, (size_t)nl * B, t0, nullptr, d2);
         const size_t m = b.P.tiles.size();
         ntt_tiles(b, d, (uint16_t)(log_c_of(h.logN) | kSubInv), (size_t)nl * B, C, c_ten, n_ten, c_intt);
         take(1, m);
