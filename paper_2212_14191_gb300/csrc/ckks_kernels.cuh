@@ -13,10 +13,10 @@ namespace fhe {
 namespace {
 
 // Per-limb moduli with the constants of reduce_red: r32 = 2^32 mod q with its Shoup quotient,
-// m32 = floor(2^32 / q).
+// m32 = floor(2^32 / q); and qinv = q^-1 mod 2^32 for the Montgomery step of Conv.
 struct ModVec {
     uint32_t q[kMaxLimbs];
-    uint32_t r32[kMaxLimbs], r32s[kMaxLimbs], m32[kMaxLimbs];
+    uint32_t r32[kMaxLimbs], r32s[kMaxLimbs], m32[kMaxLimbs], qinv[kMaxLimbs];
 };
 
 inline ModVec modvec(const fhe_ctx* ctx, const int* mod_idx, int n) {
@@ -28,6 +28,9 @@ inline ModVec modvec(const fhe_ctx* ctx, const int* mod_idx, int n) {
         m.r32[l] = (uint32_t)((1ull << 32) % q);
         m.r32s[l] = shoup_h(m.r32[l], q);
         m.m32[l] = (uint32_t)((1ull << 32) / q);
+        uint32_t x = q;  // q^-1 mod 2^32 by Newton's iteration (q odd; each step doubles the bits)
+        for (int k = 0; k < 5; ++k) x *= 2u - q * x;
+        m.qinv[l] = x;
     }
     return m;
 }
@@ -44,6 +47,18 @@ __device__ __forceinline__ uint32_t reduce_red(uint64_t x, const Red& r) {
     const uint32_t t = mul_shoup_lazy((uint32_t)(x >> 32), r.r32, r.r32s, r.q);
     const uint32_t u = xl - __umulhi(xl, r.m32) * r.q;
     return csub(csub(t + u, 2 * r.q), r.q);
+}
+// Montgomery step: for x < 2^64, m = x_lo q^-1 mod 2^32 makes m q agree with x in its low word,
+// so x_hi - floor(m q / 2^32) is exactly (x - m q) / 2^32, congruent to x 2^-32 mod q and above
+// -q. Returned as that value plus q (GUARD false: the caller knows x_hi + q < 2^32), or plus q
+// only where it is negative (GUARD true).
+template <bool GUARD>
+__device__ __forceinline__ uint32_t redc(uint64_t x, uint32_t q, uint32_t qinv) {
+    const uint32_t hi = (uint32_t)(x >> 32), u = __umulhi((uint32_t)x * qinv, q);
+    if constexpr (GUARD)
+        return hi - u + (hi < u ? q : 0u);
+    else
+        return hi - u + q;
 }
 // v mod q for v < 2^32 (32-bit Barrett, one correction above [0, 2q)).
 __device__ __forceinline__ uint32_t reduce32(uint32_t v, const Red& r) {
@@ -139,7 +154,8 @@ struct ConvArgs {
 };
 
 // The constants [B/b_i]_t of every (source, destination) pair, scaled where asked, into the
-// CTA's shared memory s_hat[nsrc][ndst]. The caller synchronises the CTA before using them.
+// CTA's shared memory s_hat[nsrc][ndst], in Montgomery form (times 2^32 mod q_t: conv_range
+// reduces its sums with one Montgomery step). The caller synchronises the CTA before using them.
 __device__ __forceinline__ void conv_load_hat(const ConvArgs& a, int nsrc, uint32_t* s_hat) {
     for (int k = threadIdx.x; k < nsrc * a.ndst; k += blockDim.x) {
         int i = k / a.ndst, t = k % a.ndst;
@@ -149,7 +165,7 @@ __device__ __forceinline__ void conv_load_hat(const ConvArgs& a, int nsrc, uint3
             const uint2 u = a.s1[a.dst_mod[t]], v = a.s2[a.dst_mod[t]];
             h = mul_shoup(mul_shoup(h, u.x, u.y, q), v.x, v.y, q);
         }
-        s_hat[k] = h;
+        s_hat[k] = mul_shoup(h, a.dm.r32[t], a.dm.r32s[t], a.dm.q[t]);
     }
 }
 
@@ -184,6 +200,7 @@ __device__ __forceinline__ void stv(uint32_t* p, size_t i, const uint32_t (&v)[V
 template <int NS, bool COH, int VW = 4>
 __device__ __forceinline__ void conv_range(const ConvArgs& a, const uint32_t* s_hat, size_t n, size_t end,
                                            size_t step) {
+    static_assert(NS >= 1 && NS <= 15, "the 64-bit sums hold at most 15 products below 2^60");
     for (; n < end; n += step) {
         uint32_t y[NS][VW];
 #pragma unroll
@@ -205,10 +222,12 @@ __device__ __forceinline__ void conv_range(const ConvArgs& a, const uint32_t* s_
 #pragma unroll
                 for (int k = 0; k < VW; ++k) acc[k] += (uint64_t)y[i][k] * h;
             }
+            // acc < NS 2^30 q_t (y_i < 2^30, constants below q_t), so its high word is below
+            // NS q_t / 4: the Montgomery step leaves [0, 4 q_t) (for NS > 12 with its guard)
             uint32_t r[VW];
-            const Red rd = red_of(a.dm, t);
+            const uint32_t q = a.dm.q[t], qinv = a.dm.qinv[t];
 #pragma unroll
-            for (int k = 0; k < VW; ++k) r[k] = reduce_red(acc[k], rd);
+            for (int k = 0; k < VW; ++k) r[k] = csub(csub(redc<(NS > 12)>(acc[k], q, qinv), 2 * q), q);
             stv<VW>(a.dst, t * (a.dst_stride / VW) + n, r);
         }
     }

@@ -248,3 +248,47 @@ def test_fused_tail_load_without_reductions(ql_side):
     np.testing.assert_array_equal(v % U64(q), want)
     psi = P.psi(q, n)
     np.testing.assert_array_equal(forward_lazy(v, q, psi), O.ntt(want.astype(np.uint32), q, psi).astype(U64))
+
+
+def redc_lazy(t, q, qinv, guarded=False):
+    """Montgomery reduction as Conv does it: m = t_lo q^-1 mod 2^32, then t_hi - floor(m q / 2^32)
+    (m q has the same low word as t, so the subtraction is exact), congruent to t 2^-32 mod q and
+    above -q; q is added always, or (guarded) only where t_hi < floor(m q / 2^32)."""
+    m = ((t & M32) * U64(qinv)) & M32
+    hi, u = t >> U64(32), (m * U64(q)) >> U64(32)
+    if guarded:
+        return (hi - u + np.where(hi < u, U64(q), U64(0))) & M32
+    return (hi - u + U64(q)) & M32
+
+
+@pytest.mark.parametrize("ns", [1, 8, 12, 15])
+def test_conv_montgomery_reduction(ns):
+    """Conv's sum over NS source limbs, out_t = sum_i y_i [B/b_i]_t mod p (Sec. IV-A), with the
+    constants taken in Montgomery form ([B/b_i]_t 2^32 mod p, folded in once per CTA) and the
+    64-bit sum reduced by one Montgomery step: every y_i < 2^30 and constant < p keep the sum
+    below NS 2^30 p, so its high word is below NS p / 4. For NS <= 12 the step adds p always
+    and stays below 4p < 2^32; above 12 that could pass 2^32, so p is added only where the
+    subtraction went below zero, leaving [0, NS p / 4) below 4p. Two conditional subtractions
+    (2p, p) then give the canonical residue. Checked at the largest and a small accepted prime,
+    with every source and constant at its maximum among the cases."""
+    rng = np.random.default_rng(50 + ns)
+    for p in (P.ntt_primes(1, logn_max=16)[0], P.ntt_primes(40, logn_max=16)[-1]):
+        qinv = pow(p, -1, 1 << 32)
+        srcq = P.ntt_primes(ns + 1, logn_max=16)[1:]
+        for trial in range(3):
+            y = np.stack([rng.integers(0, q, 4096, dtype=np.int64) for q in srcq]).astype(U64)
+            h = rng.integers(0, p, ns, dtype=np.int64)
+            if trial == 1:
+                y = np.stack([np.full(4096, q - 1, dtype=np.int64) for q in srcq]).astype(U64)
+                h[:] = p - 1
+            hm = [(int(v) << 32) % p for v in h]                # Montgomery form of the constants
+            acc = np.zeros(4096, dtype=U64)
+            for i in range(ns):
+                acc += y[i] * U64(hm[i])                        # no wrap: < ns 2^30 p < 2^64
+            assert int(acc.max()) < ns * (1 << 30) * p
+            assert int(acc.max() >> U64(32)) < ns * p / 4
+            r = redc_lazy(acc, p, qinv, guarded=ns > 12)
+            assert int(r.max()) < 4 * p
+            r = csub(csub(r, 2 * p), p)
+            want = sum(y[i].astype(object) * int(h[i]) for i in range(ns)) % p
+            assert (r.astype(object) == want).all(), (p, trial)
