@@ -331,9 +331,7 @@ int ks_finish(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint32
         ia.L4 = L4;
         ia.N4 = N / 4;
         ia.m = ext_m;
-        ia.s1 = ctx->p_inv;
-        ia.s2 = scale_lt > 0 ? ctx->ql_inv + (size_t)(nl - 1) * nq : nullptr;
-        ia.scale_lt = scale_lt;
+        ip_set_post(ctx, ia, nl, ext, scale_lt);
         k_inner_product<<<stream_grid(ctx, L4, ext), 256, 0, st>>>(ia);
         FHE_CUDA_TRY(cudaGetLastError());
     }

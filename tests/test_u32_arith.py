@@ -292,3 +292,31 @@ def test_conv_montgomery_reduction(ns):
             r = csub(csub(r, 2 * p), p)
             want = sum(y[i].astype(object) * int(h[i]) for i in range(ns)) % p
             assert (r.astype(object) == want).all(), (p, trial)
+
+
+@pytest.mark.parametrize("dnum", [1, 3, 12, 13, 15])
+def test_inner_product_montgomery_with_post_factor(dnum):
+    """The key-switching inner product's reduction (Sec. IV-A Hada-Mult + Ele-Add): each sum of
+    dnum products of residues below q (at most 15 before a mid-way reduction) takes one guarded
+    Montgomery step, then a lazy Shoup product by 2^32 s mod q (s = P^-1 q_l^-1 on the limbs the
+    fused tail scales, else 1) and one conditional subtraction: the result must be the
+    canonical sum times s. Checked at the largest and a small accepted prime, with every
+    operand at its maximum among the cases."""
+    rng = np.random.default_rng(70 + dnum)
+    for q in (P.ntt_primes(1, logn_max=16)[0], P.ntt_primes(40, logn_max=16)[-1]):
+        qinv = pow(q, -1, 1 << 32)
+        for scale in (1, int(rng.integers(2, q))):
+            post = ((1 << 32) * scale) % q
+            post_q = shoup_quotient(post, q)
+            for trial in range(2):
+                x = rng.integers(0, q, (dnum, 4096), dtype=np.int64).astype(U64)
+                w = rng.integers(0, q, (dnum, 4096), dtype=np.int64).astype(U64)
+                if trial == 1:
+                    x[:], w[:] = q - 1, q - 1
+                acc = np.zeros(4096, dtype=U64)
+                for j in range(dnum):
+                    acc += x[j] * w[j]                          # < 15 q^2 < 2^64
+                m = redc_lazy(acc, q, qinv, guarded=True)
+                r = csub(mul_shoup_lazy(m, U64(post), post_q, q), q)
+                want = sum(x[j].astype(object) * w[j].astype(object) for j in range(dnum)) * scale % q
+                assert (r.astype(object) == want).all(), (q, scale, trial)
