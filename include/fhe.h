@@ -235,8 +235,10 @@ int fhe_hmult(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const u
  *   key from s(X^k) to s in the layout of `evk` above. Scratch: fhe_scratch_bytes(
  *   FHE_OP_HROTATE); ct_out must not overlap ct_in. No rescale.
  * fhe_hrotate_hoisted -- n_rot HROTATEs of one ciphertext batch sharing one ModUp (hoisted
- *   rotations): ModUp of c1 is formed once in the NTT domain and each rotation applies its
- *   automorphism to those digits before the inner product and ModDown. The approximate Conv
+ *   rotations): ModUp of c1 is formed once in the NTT domain and each rotation key-switches
+ *   those digits permuted by its automorphism (computed as the inner product of the unpermuted
+ *   digits with the key permuted by the inverse automorphism, then permuted: the same values,
+ *   since the product is pointwise), followed by ModDown. The approximate Conv
  *   does not commute exactly with X -> X^k, so each result is a valid key switch of c1(X^k)
  *   but not bit-identical to fhe_hrotate's: the automorphism of ModUp(c1) differs from ModUp
  *   of c1(X^k) by B_j times the number of nonzero Conv terms at every negated coefficient.

@@ -300,13 +300,19 @@ int ks_modup(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, uint32_t* d2c
     return FHE_OK;
 }
 
+int launch_automorph(const fhe_ctx* ctx, const uint32_t* in, uint32_t* out, uint32_t k, uint32_t logN, size_t rows,
+                     cudaStream_t st);
+
 // KS-4, KS-5: the inner product of the ModUp digits with evk (slice j's own limbs taken from d2,
 // NTT form) and ModDown into `out` (2, nl, B, N); accumulate != 0 adds to out. ks (2 ext limbs)
 // and y (2 nl limbs) are scratch. scale_lt > 0 (the fused HMULT + RESCALE tail, out == nullptr):
 // q limbs t < scale_lt of ks and of y come out multiplied by P^-1 q_{nl-1}^-1.
+// galois != 0 (hoisted rotations): the inner product writes ks_pre (2 ext limbs), whose
+// automorphism X -> X^galois then becomes ks; with evk permuted by the inverse automorphism this
+// equals the inner product of the permuted digits with evk, since the product is pointwise.
 int ks_finish(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint32_t* d2, const uint32_t* digits,
               const uint32_t* evk, uint32_t* out, int accumulate, uint32_t* ks, uint32_t* y, cudaStream_t st,
-              NttScratch ns, int scale_lt) {
+              NttScratch ns, int scale_lt, uint32_t galois = 0, uint32_t* ks_pre = nullptr) {
     const size_t N = 1ull << logN, limb = N * batch, L4 = limb / 4;
     const int K = ctx->np, ext = nl + K, alpha = ctx->alpha, nq = ctx->nq;
     const int nmod = (int)ctx->mods.size();
@@ -321,7 +327,7 @@ int ks_finish(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint32
         ia.d2 = d2;
         ia.tmp = digits;
         ia.evk = evk;
-        ia.ks = ks;
+        ia.ks = galois ? ks_pre : ks;
         ia.nl = nl;
         ia.alpha = alpha;
         ia.dnum = dnum;
@@ -334,6 +340,7 @@ int ks_finish(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint32
         ip_set_post(ctx, ia, nl, ext, scale_lt);
         k_inner_product<<<stream_grid(ctx, L4, ext), 256, 0, st>>>(ia);
         FHE_CUDA_TRY(cudaGetLastError());
+        if (galois && (rc = launch_automorph(ctx, ks_pre, ks, galois, logN, 2 * (size_t)ext * batch, st))) return rc;
     }
     // KS-5: ModDown of ks0, ks1
     LimbMap pm = contiguous_map(ctx, nq, K);
@@ -626,45 +633,57 @@ int hrotate_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, uint32_t 
 }
 
 // Hoisted HROTATE: n_rot rotations of one ciphertext share one ModUp. The NTT-domain digits
-// ModUp_j(c1) are formed once; for each Galois element k the automorphism (a permutation of
-// NTT-domain values, the same under every modulus) is applied to c0, to c1 (the digits'
-// own-slice limbs) and to every slice's converted limbs, then the inner product with that
-// rotation's key and ModDown finish as in hrotate_impl. The approximate Conv does not commute
-// exactly with X -> X^k (where a coefficient is negated, its lift changes by a multiple of
-// Q_j), so this is a valid key switch of c1(X^k) that differs from hrotate_impl's result.
-// Scratch: c1 (copy, then coefficients; nl limbs), digits (dnum ext), c1(X^k) (nl), permuted
-// digits (dnum ext), ks (2 ext), y (2 nl); the per-rotation buffers are reused in turn.
-size_t hoisted_scratch_limbs(int nl, int K, int alpha) {
-    const size_t dnum = (size_t)((nl + alpha - 1) / alpha), ext = (size_t)(nl + K);
-    return 2 * (size_t)nl + 2 * dnum * ext + 2 * ext + 2 * (size_t)nl;
+// ModUp_j(c1) are formed once; each rotation's key switch is that of the digits permuted by
+// the automorphism X -> X^k (a permutation of NTT-domain values, the same under every
+// modulus). Since the inner product is pointwise, sum_j d_j[sigma(n)] evk_j[n] is ks'[sigma(n)]
+// with ks'[m] = sum_j d_j[m] evk_j[sigma^-1(m)]: each rotation permutes its key by the inverse
+// automorphism (once, shared by the whole batch), takes the inner product of the unpermuted
+// digits and c1 (the own-slice limbs), and permutes the 2 (nl + K) limbs of ks' instead of the
+// nl + dnum (nl + K) - nl limbs of c1 and the digits; c0 is permuted into the output, and
+// ModDown finishes as in hrotate_impl. The approximate Conv does not commute exactly with
+// X -> X^k (where a coefficient is negated, its lift changes by a multiple of Q_j), so this is
+// a valid key switch of c1(X^k) that differs from hrotate_impl's result.
+// Scratch: c1 (coefficients; nl limbs), digits (dnum ext), ks' (2 ext), ks (2 ext), y (2 nl),
+// then the permuted key (dnum x 2 x nmod rows of N words, in whole limbs of the batch).
+size_t hoisted_key_limbs(const fhe_ctx* ctx, int nl, int batch) {
+    const size_t dnum = (size_t)((nl + ctx->alpha - 1) / ctx->alpha);
+    const size_t rows = dnum * 2 * ctx->mods.size();
+    return batch > 0 ? (rows + batch - 1) / batch : 0;
+}
+size_t hoisted_scratch_limbs(const fhe_ctx* ctx, int nl, int batch) {
+    const size_t dnum = (size_t)((nl + ctx->alpha - 1) / ctx->alpha), ext = (size_t)(nl + ctx->np);
+    return (size_t)nl + dnum * ext + 4 * ext + 2 * (size_t)nl + hoisted_key_limbs(ctx, nl, batch);
+}
+
+// The inverse of an odd k modulo 2^bits (bits <= 32), by Newton's iteration.
+uint32_t inv_pow2(uint32_t k, int bits) {
+    uint32_t x = k;
+    for (int i = 0; i < 5; ++i) x *= 2u - k * x;
+    return bits >= 32 ? x : x & ((1u << bits) - 1);
 }
 
 int hrotate_hoisted_impl(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, int nrot, const uint32_t* galois,
                          const uint32_t* ct, const uint32_t* const* ksk, uint32_t* out, uint32_t* scratch,
                          cudaStream_t st, NttScratch ns) {
-    const size_t limb = ((size_t)1 << logN) * batch, rows = (size_t)nl * batch;
+    const size_t N = (size_t)1 << logN, limb = N * batch, rows = (size_t)nl * batch;
     const int ext = nl + ctx->np, alpha = ctx->alpha, dnum = (nl + alpha - 1) / alpha;
+    const uint32_t* c1 = ct + (size_t)nl * limb;
     uint32_t* c1c = scratch;
     uint32_t* digits = c1c + (size_t)nl * limb;
-    uint32_t* c1k = digits + (size_t)dnum * ext * limb;
-    uint32_t* dk = c1k + (size_t)nl * limb;
-    uint32_t* ks = dk + (size_t)dnum * ext * limb;
+    uint32_t* kp = digits + (size_t)dnum * ext * limb;
+    uint32_t* ks = kp + 2 * (size_t)ext * limb;
     uint32_t* y = ks + 2 * (size_t)ext * limb;
+    uint32_t* key = y + 2 * (size_t)nl * limb;
+    const size_t key_rows = (size_t)dnum * 2 * ctx->mods.size();
     int rc;
-    if ((rc = ks_modup(ctx, logN, nl, batch, c1c, digits, st, ns, ct + (size_t)nl * limb))) return rc;
+    if ((rc = ks_modup(ctx, logN, nl, batch, c1c, digits, st, ns, c1))) return rc;
     for (int r = 0; r < nrot; ++r) {
         const uint32_t k = galois[r];
         uint32_t* o = out + (size_t)r * 2 * nl * limb;
+        if ((rc = launch_automorph(ctx, ksk[r], key, inv_pow2(k, (int)logN + 1), logN, key_rows, st))) return rc;
         if ((rc = launch_automorph(ctx, ct, o, k, logN, rows, st))) return rc;
-        if ((rc = launch_automorph(ctx, ct + (size_t)nl * limb, c1k, k, logN, rows, st))) return rc;
-        for (int j = 0; j < dnum; ++j) {
-            const int own = std::min(nl, (j + 1) * alpha) - j * alpha;
-            const size_t off = (size_t)j * ext * limb;
-            if ((rc = launch_automorph(ctx, digits + off, dk + off, k, logN, (size_t)(ext - own) * batch, st)))
-                return rc;
-        }
         FHE_CUDA_TRY(cudaMemsetAsync(o + (size_t)nl * limb, 0, (size_t)nl * limb * 4, st));
-        if ((rc = ks_finish(ctx, logN, nl, batch, c1k, dk, ksk[r], o, 1, ks, y, st, ns, 0))) return rc;
+        if ((rc = ks_finish(ctx, logN, nl, batch, c1, digits, key, o, 1, ks, y, st, ns, 0, k, kp))) return rc;
     }
     return FHE_OK;
 }
@@ -689,7 +708,7 @@ int check_ptrs(std::initializer_list<const void*> ps) {
 // RESCALE chunks through its own buffers (rescale_impl) and needs none.
 size_t ntt_rows(const fhe_ctx* ctx, int op, int nl) { return op == FHE_OP_RESCALE ? 0 : 2 * ((size_t)nl + ctx->np); }
 
-size_t scratch_limbs(const fhe_ctx* ctx, int op, int nl) {
+size_t scratch_limbs(const fhe_ctx* ctx, int op, int nl, int batch) {
     const int K = ctx->np;
     switch (op) {
         case FHE_OP_KEYSWITCH: return ks_scratch_limbs(nl, K, ctx->alpha);
@@ -697,7 +716,7 @@ size_t scratch_limbs(const fhe_ctx* ctx, int op, int nl) {
         case FHE_OP_RESCALE: return rescale_scratch_limbs(nl);
         case FHE_OP_HMULT: return 2 * (size_t)nl + (size_t)nl + ks_scratch_limbs(nl, K, ctx->alpha);
         case FHE_OP_HROTATE: return hrotate_scratch_limbs(nl, K, ctx->alpha);
-        case FHE_OP_HROTATE_HOISTED: return hoisted_scratch_limbs(nl, K, ctx->alpha);
+        case FHE_OP_HROTATE_HOISTED: return hoisted_scratch_limbs(ctx, nl, batch);
         default: return 0;
     }
 }
@@ -706,7 +725,7 @@ size_t scratch_limbs(const fhe_ctx* ctx, int op, int nl) {
 NttScratch op_ntt_scratch(const fhe_ctx* ctx, int op, uint32_t logN, int nl, int batch, void* scratch) {
     NttScratch s;
     s.bytes = op_region_bytes(ctx, logN, ntt_rows(ctx, op, nl) * batch);
-    if (s.bytes) s.p = (uint32_t*)((uint8_t*)scratch + scratch_limbs(ctx, op, nl) * ((size_t)batch << logN) * 4);
+    if (s.bytes) s.p = (uint32_t*)((uint8_t*)scratch + scratch_limbs(ctx, op, nl, batch) * ((size_t)batch << logN) * 4);
     return s;
 }
 
@@ -722,7 +741,7 @@ size_t fhe_scratch_bytes(const fhe_ctx* ctx, int op, uint32_t logN, int n_limbs,
         n_limbs > ctx->nq || batch < 0)
         return 0;
     if ((op == FHE_OP_RESCALE || op == FHE_OP_HMULT) && n_limbs < 2) return 0;
-    const size_t limbs = scratch_limbs(ctx, op, n_limbs);
+    const size_t limbs = scratch_limbs(ctx, op, n_limbs, batch);
     if (limbs == 0) return 0;
     // the operation's limbs, then the two-pass NTT region of its NTT calls
     return limbs * ((size_t)batch << logN) * 4 + op_region_bytes(ctx, logN, ntt_rows(ctx, op, n_limbs) * batch);
