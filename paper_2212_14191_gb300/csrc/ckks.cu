@@ -321,6 +321,13 @@ int ks_finish(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint32
     for (int t = 0; t < ext; ++t) ext_mod[t] = t < nl ? t : nq + (t - nl);
     ModVec ext_m = modvec(ctx, ext_mod, ext);
     int rc;
+    // The combine out += (ks - NTT(y)) P^-1 can ride on the forward NTT of y, as the HMULT's
+    // RESCALE tail does (z' = y' loaded, out = ks' + out - z'^ stored): the inner product then
+    // writes ks' = ks P^-1 on the q limbs and ModDown's Conv y' = y P^-1, so that neither NTT(y)
+    // nor a separate combine pass reaches HBM.
+    const bool fuse_combine = out != nullptr && accumulate && scale_lt == 0 &&
+                              ntt_tail_fusable(ctx, FHE_NTT_DEFAULT, logN);
+    const int ip_scale = fuse_combine ? nl : scale_lt;
     // KS-4: inner product over all slices
     {
         IpArgs ia;
@@ -337,7 +344,7 @@ int ks_finish(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint32
         ia.L4 = L4;
         ia.N4 = N / 4;
         ia.m = ext_m;
-        ip_set_post(ctx, ia, nl, ext, scale_lt);
+        ip_set_post(ctx, ia, nl, ext, ip_scale, !fuse_combine);
         k_inner_product<<<stream_grid(ctx, L4, ext), 256, 0, st>>>(ia);
         FHE_CUDA_TRY(cudaGetLastError());
         if (galois && (rc = launch_automorph(ctx, ks_pre, ks, galois, logN, 2 * (size_t)ext * batch, st))) return rc;
@@ -351,7 +358,7 @@ int ks_finish(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint32
         ConvArgs ca;
         ca.s1 = ctx->p_inv;
         ca.s2 = scale_lt > 0 ? ctx->ql_inv + (size_t)(nl - 1) * nq : nullptr;
-        ca.scale_lt = scale_lt;
+        ca.scale_lt = ip_scale;
         ca.src = ks + ((size_t)c * ext + nl) * limb;
         ca.src_stride = limb;
         ca.nsrc = K;
@@ -384,6 +391,20 @@ int ks_finish(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint32
         }
     // the caller fuses the ModDown combine into RESCALE and takes y in the coefficient domain
     if (out == nullptr) return FHE_OK;
+    if (fuse_combine) {
+        HmultTail tl;
+        tl.y = y;
+        tl.last = nullptr;
+        tl.ks = ks;
+        tl.d = out;
+        tl.out = out;
+        tl.qlinv = nullptr;
+        tl.ql = 0;
+        tl.nl = nl;
+        tl.nout = nl;
+        tl.ext = ext;
+        return ntt_u32_l2_tail(ctx, logN, 2 * nl * batch, batch, qm2, st, ns, tl);
+    }
     if ((rc = ntt_any(ctx, FHE_NTT_DEFAULT, logN, false, y, 2 * nl, batch, qm2, st, ns))) return rc;
     int qidx[kMaxLimbs];
     for (int i = 0; i < nl; ++i) qidx[i] = i;

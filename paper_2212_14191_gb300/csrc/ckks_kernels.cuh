@@ -147,7 +147,7 @@ struct ConvArgs {
     ModVec dm;
     size_t L4;  // residues per limb / 4
     // destinations t < scale_lt come out multiplied by s1[t] s2[t] (Shoup pairs mod q_t, folded
-    // into the constants [B/b_i]_t); 0 leaves every destination unscaled
+    // into the constants [B/b_i]_t; s2 may be null); 0 leaves every destination unscaled
     const uint2* s1;
     const uint2* s2;
     int scale_lt;
@@ -162,8 +162,12 @@ __device__ __forceinline__ void conv_load_hat(const ConvArgs& a, int nsrc, uint3
         uint32_t h = a.hat_mod[(size_t)i * a.nmod + a.dst_mod[t]];
         if (t < a.scale_lt) {
             const uint32_t q = a.dm.q[t];
-            const uint2 u = a.s1[a.dst_mod[t]], v = a.s2[a.dst_mod[t]];
-            h = mul_shoup(mul_shoup(h, u.x, u.y, q), v.x, v.y, q);
+            const uint2 u = a.s1[a.dst_mod[t]];
+            h = mul_shoup(h, u.x, u.y, q);
+            if (a.s2) {
+                const uint2 v = a.s2[a.dst_mod[t]];
+                h = mul_shoup(h, v.x, v.y, q);
+            }
         }
         s_hat[k] = mul_shoup(h, a.dm.r32[t], a.dm.r32s[t], a.dm.q[t]);
     }
@@ -246,19 +250,19 @@ struct IpArgs {
     ModVec m;             // per extended limb t < ext
     // per extended limb t: 2^32 s_t mod q_t with its Shoup quotient, the factor each sum takes
     // after its Montgomery step (which leaves it times 2^-32); s_t = P^-1 q_l^-1 on the limbs the
-    // fused HMULT tail scales (t < scale_lt), else 1 (ip_set_post)
+    // fused HMULT tail scales, P^-1 on those of a fused ModDown combine, else 1 (ip_set_post)
     uint2 post[kMaxLimbs];
 };
 
 // The post factors of an inner product over ext extended limbs whose first nl are q limbs,
-// with the fused tail's P^-1 q_l^-1 (l = nl - 1) on limbs t < scale_lt.
-inline void ip_set_post(const fhe_ctx* ctx, IpArgs& ia, int nl, int ext, int scale_lt) {
+// with P^-1 on limbs t < scale_lt, times q_l^-1 (l = nl - 1) for the fused HMULT tail (with_ql).
+inline void ip_set_post(const fhe_ctx* ctx, IpArgs& ia, int nl, int ext, int scale_lt, bool with_ql) {
     for (int t = 0; t < ext; ++t) {
         const uint32_t q = ia.m.q[t];
         uint32_t c = (uint32_t)((1ull << 32) % q);
         if (t < scale_lt) {
             c = mulmod_h(c, ctx->p_inv_h[t].x, q);
-            c = mulmod_h(c, invmod_h(ctx->mods[nl - 1] % q, q), q);
+            if (with_ql) c = mulmod_h(c, invmod_h(ctx->mods[nl - 1] % q, q), q);
         }
         ia.post[t] = make_uint2(c, shoup_h(c, q));
     }

@@ -196,7 +196,8 @@ int ntt_u32_l2(const fhe_ctx* ctx, uint32_t logN, int shape, bool inverse, uint3
 // P^-1 q_l^-1, P^-1 q_l^-1 and q_l^-1 (limbs i < l).
 struct HmultTail {
     const uint32_t* y;     // (2, nl, batch, N): y', coefficient domain
-    const uint32_t* last;  // (2, batch, N): the relinearised last limb, coefficient domain, [0, q_l)
+    const uint32_t* last;  // (2, batch, N): the relinearised last limb, coefficient domain, [0, q_l);
+                           // null: no last-limb term (z' = y', the ModDown combine of key switching)
     const uint32_t* ks;    // (2, ext, batch, N): ks', NTT domain
     const uint32_t* d;     // (2, nl, batch, N): d0', d1', NTT domain
     uint32_t* out;         // (2, nout, batch, N)

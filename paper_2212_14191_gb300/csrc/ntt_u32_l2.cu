@@ -41,9 +41,9 @@ __global__ void __launch_bounds__(256) ntt_dit_cross_kernel(const L2Args a) {
     dit_cross_row<LOG_NC, LOG_C, TAIL>(a, blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
-template <int LOG_T, int LOG_C, bool TAIL>
+template <int LOG_T, int LOG_C, bool TAIL, bool LAST = true>
 __global__ void __launch_bounds__(1 << LOG_T, kMinB<LOG_T>) ntt_dit_local_kernel(const L2Args a) {
-    dit_local<LOG_T, LOG_C, TAIL, false>(a, blockIdx.y, blockIdx.x);
+    dit_local<LOG_T, LOG_C, TAIL, false, LAST>(a, blockIdx.y, blockIdx.x);
 }
 
 
@@ -57,7 +57,9 @@ int run_l2(const fhe_ctx* ctx, const NttTables& t, int shape, bool inverse, uint
     // inverse: decimation in frequency (quarter pass, then cross stages with N^-1)
     if (TAIL && (inverse || rowtab || !tail)) return set_error(FHE_EINVAL, "fused tail: forward, limb-map rows only");
     if (src && (!inverse || rowtab)) return set_error(FHE_EINVAL, "out-of-place two-pass NTT: inverse, limb-map rows only");
-    auto qk = inverse ? ntt_quarter_inv_kernel<LOG_T, LOG_C> : ntt_dit_local_kernel<LOG_T, LOG_C, TAIL>;
+    auto qk = inverse ? ntt_quarter_inv_kernel<LOG_T, LOG_C>
+                      : (TAIL && !tail->last) ? ntt_dit_local_kernel<LOG_T, LOG_C, TAIL, false>
+                                              : ntt_dit_local_kernel<LOG_T, LOG_C, TAIL>;
     FHE_CUDA_TRY(cudaFuncSetAttribute(qk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int carve = (int)((kMinB<LOG_T> * (smem + 1024) * 100 + 228 * 1024 - 1) / (228 * 1024));
     FHE_CUDA_TRY(cudaFuncSetAttribute(qk, cudaFuncAttributePreferredSharedMemoryCarveout, carve > 100 ? 100 : carve));

@@ -409,7 +409,9 @@ __device__ __forceinline__ void dit_cross_row(const L2Args& a, int i, int p0, in
 
 // Local pass of row i, sub-transform j (see quarter_inv for the shared memory and COH). With
 // C = 1 and no tail the transform ends here and the row is written in place, in natural order.
-template <int LOG_T, int LOG_C, bool TAIL, bool COH>
+// LAST (TAIL only): the tail has the relinearised last limb's term (the HMULT's RESCALE tail);
+// false: z' = y' (the ModDown combine of key switching, a.tail.last null).
+template <int LOG_T, int LOG_C, bool TAIL, bool COH, bool LAST = true>
 __device__ __forceinline__ void dit_local(const L2Args& a, int i, int j) {
     constexpr int T = 1 << LOG_T, C = 1 << LOG_C, NC = 32 * T, N = NC * C, RB = LOG_T - 5;
     extern __shared__ __align__(128) uint32_t work[];
@@ -428,10 +430,11 @@ __device__ __forceinline__ void dit_local(const L2Args& a, int i, int j) {
     const uint2* tw = a.tw_sub + (size_t)mod * NC;
     uint32_t v[32];
     if constexpr (TAIL) {
-        // z' = y' + [last]_q q_l^-1 (last centred: values above (q_l - 1) / 2 stand for last - q_l)
+        // z' = y' + [last]_q q_l^-1 (last centred: values above (q_l - 1) / 2 stand for last - q_l),
+        // or z' = y' without a last limb (the ModDown combine of key switching)
         const uint32_t* yr = a.tail.y + (((size_t)t.c * a.tail.nl + t.i) * a.batch + t.p) * N;
-        const uint32_t* lr = a.tail.last + ((size_t)t.c * a.batch + t.p) * N;
-        const uint2 qlinv = __ldg(&a.tail.qlinv[t.i]);
+        const uint32_t* lr = LAST ? a.tail.last + ((size_t)t.c * a.batch + t.p) * N : nullptr;
+        const uint2 qlinv = LAST ? __ldg(&a.tail.qlinv[t.i]) : make_uint2(0, 0);
         if (tid == 0 && a.fuse) {
             // the row's cross pass, run by the last of its C local passes, reads all of the
             // row's ks and d: each local pass brings its own part of them into L2 meanwhile
@@ -443,14 +446,19 @@ __device__ __forceinline__ void dit_local(const L2Args& a, int i, int j) {
         // first: x = last + (q - q_l mod q) stands for last - q_l (x < 2^31). The first
         // butterfly stage pairs e with e + 16 and takes x-side inputs below 2q and y-side
         // inputs of any size, so only e < 16 is brought from [0, 3q) below 2q.
-        const uint32_t half = (a.tail.ql - 1) / 2, lift = q - a.tail.ql % q;
+        if constexpr (LAST) {
+            const uint32_t half = (a.tail.ql - 1) / 2, lift = q - a.tail.ql % q;
 #pragma unroll
-        for (int e = 0; e < 32; ++e) {
-            const size_t idx = (size_t)(tid + T * e) * C + j;
-            const uint32_t lv = ld_tail<COH>(&lr[idx]), yv = ld_tail<COH>(&yr[idx]);
-            const uint32_t x = lv > half ? lv + lift : lv;
-            const uint32_t z = yv + mul_shoup_lazy(x, qlinv.x, qlinv.y, q);
-            v[e] = e < 16 ? csub(z, q) : z;
+            for (int e = 0; e < 32; ++e) {
+                const size_t idx = (size_t)(tid + T * e) * C + j;
+                const uint32_t lv = ld_tail<COH>(&lr[idx]), yv = ld_tail<COH>(&yr[idx]);
+                const uint32_t x = lv > half ? lv + lift : lv;
+                const uint32_t z = yv + mul_shoup_lazy(x, qlinv.x, qlinv.y, q);
+                v[e] = e < 16 ? csub(z, q) : z;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) v[e] = ld_tail<COH>(&yr[(size_t)(tid + T * e) * C + j]);
         }
     } else {
 #pragma unroll

@@ -494,7 +494,7 @@ void hm_build(Builder& b, const HmInst& h, uint8_t* sb, uint32_t pred_ctr, uint3
         ia.L4 = L4;
         ia.N4 = N / 4;
         ia.m = modvec(ctx, ext_mod, ext);
-        ip_set_post(ctx, ia, nl, ext, nl - 1);
+        ip_set_post(ctx, ia, nl, ext, nl - 1, true);
         b.P.ip.push_back(ia);
         const size_t m = b.P.tiles.size();
         for (int t = 0; t < ext; ++t)

@@ -219,3 +219,73 @@ def test_hrotate_hoisted_full_size_config(fhe):
             assert (got[r, :, :, b] == want[r]).all(), (b, r)
     fhe.fhe_device_status(ctx.handle, 1)
     ctx.close()
+
+
+def test_intt_out_of_place_and_copy_fallback(fhe):
+    """N = 2^15, 6 + 2 limbs, 2 ciphertexts: key switching's INTT reads d2 (HMULT) and c1 (hoisted
+    rotations) in place when the inverse runs the two-pass kernels (variant 6), and transforms a
+    copy when it runs a cluster variant (0). Both give the same results, which also match the
+    oracle (HMULT on one pair, the hoisted rotation on one ciphertext)."""
+    import torch
+    logn, nl, K, batch = 15, 6, 2, 2
+    n = 1 << logn
+    qs, ps = P.default_moduli(nl, K)
+    prm = C.Params(n, qs, ps, alpha=2)
+    s = I.ternary_secret(8, n, hamming_weight=64)
+    ctx = fhe.Context(logn, qs, ps, alpha=2)
+    A, B = batch_cts(prm, nl, batch, 720), batch_cts(prm, nl, batch, 721)
+    evk = I.uniform_residues(722, qs + ps, prm.dnum(nl) * 2, n).reshape(
+        len(qs) + len(ps), prm.dnum(nl), 2, n).transpose(1, 2, 0, 3).copy()
+    ks = [C.galois_rotation(3, n)]
+    keys = [rot_key(prm, s, k, 730) for k in ks]
+    da, db, de = fhe.to_device(A), fhe.to_device(B), fhe.to_device(evk)
+    dk = [fhe.to_device(k.astype(np.uint32)) for k in keys]
+    res = {}
+    for inv in (6, 0):
+        fhe.fhe_ntt_set_variant(ctx.handle, logn, 6, inv)
+        res[inv] = (ctx.hmult(da, db, de, logn).clone(), ctx.hrotate_hoisted(da, dk, logn, ks).clone())
+    torch.cuda.synchronize()
+    assert torch.equal(res[6][0], res[0][0]) and torch.equal(res[6][1], res[0][1])
+    got_h, got_r = fhe.to_host(res[6][0]), fhe.to_host(res[6][1])
+    want_h = C.hmult(prm, nl, A[:, :, 1].astype(U64), B[:, :, 1].astype(U64), evk.astype(U64))
+    assert (got_h[:, :, 1] == want_h).all()
+    want_r = C.hrotate_hoisted(prm, nl, A[:, :, 0].astype(U64), keys, ks)
+    assert (got_r[0, :, :, 0] == want_r[0]).all()
+    fhe.fhe_device_status(ctx.handle, 1)
+    ctx.close()
+
+
+def test_moddown_combine_fused_matches_separate(fhe):
+    """N = 2^15, 6 + 2 limbs, 2 ciphertexts: with the two-pass forward NTT (variant 6) the ModDown
+    combine of key switching, out += (ks - NTT(y)) P^-1, rides on the forward NTT of y (ks and y
+    pre-scaled by P^-1); with a cluster forward (variant 0) it runs as separate passes. HMULT
+    without rescale, HROTATE and hoisted rotations give identical results both ways, and match
+    the oracle on one ciphertext; key switching alone (no accumulation) keeps the separate form."""
+    import torch
+    logn, nl, K, batch = 15, 6, 2, 2
+    n = 1 << logn
+    qs, ps = P.default_moduli(nl, K)
+    prm = C.Params(n, qs, ps, alpha=2)
+    s = I.ternary_secret(9, n, hamming_weight=64)
+    ctx = fhe.Context(logn, qs, ps, alpha=2)
+    A, B = batch_cts(prm, nl, batch, 740), batch_cts(prm, nl, batch, 741)
+    evk = I.uniform_residues(742, qs + ps, prm.dnum(nl) * 2, n).reshape(
+        len(qs) + len(ps), prm.dnum(nl), 2, n).transpose(1, 2, 0, 3).copy()
+    ks = [C.galois_rotation(5, n), C.galois_conjugation(n)]
+    keys = [rot_key(prm, s, k, 750 + i) for i, k in enumerate(ks)]
+    da, db, de = fhe.to_device(A), fhe.to_device(B), fhe.to_device(evk)
+    dk = [fhe.to_device(k.astype(np.uint32)) for k in keys]
+    res = {}
+    for fwd in (6, 0):
+        fhe.fhe_ntt_set_variant(ctx.handle, logn, fwd, 6)
+        res[fwd] = [ctx.hmult_relin(da, db, de, logn).clone(), ctx.hrotate(da, dk[0], logn, ks[0]).clone(),
+                    ctx.hrotate_hoisted(da, dk, logn, ks).clone()]
+    torch.cuda.synchronize()
+    for x, y in zip(res[6], res[0]):
+        assert torch.equal(x, y)
+    relin, rot = fhe.to_host(res[6][0]), fhe.to_host(res[6][1])
+    want = C.hmult_relin(prm, nl, A[:, :, 1].astype(U64), B[:, :, 1].astype(U64), evk.astype(U64))
+    assert (relin[:, :, 1] == want).all()
+    assert (rot[:, :, 0] == C.hrotate(prm, nl, A[:, :, 0].astype(U64), keys[0], ks[0])).all()
+    fhe.fhe_device_status(ctx.handle, 1)
+    ctx.close()
