@@ -50,18 +50,18 @@ __device__ __forceinline__ void tail_mod(const L2Args& a, const TailRow& t, uint
 }
 
 // The C local-pass CTAs of a row each count themselves in cnt[i] once their scratch stores
-// are visible (fence, then atomic); the one that completes the count runs the row's cross
+// are visible (an acquire-release atomic); the one that completes the count runs the row's cross
 // pass while the row's scratch is still in L2. Nothing waits: a CTA that is not last exits.
 __device__ __forceinline__ bool last_of_row(const L2Args& a, int i, int C) {
     __shared__ int s_last;
     __syncthreads();
     if (threadIdx.x == 0) {
-        // the barrier orders the CTA's scratch stores before this thread's fence (cumulative),
-        // so one fence releases all of them; the warps do not each wait for their own
-        __threadfence();
-        const bool last = atomicAdd(&a.cnt[i], 1) == C - 1;
-        if (last) __threadfence();
-        s_last = last;
+        // the barrier orders the CTA's scratch stores before this thread's release
+        // (cumulative), so one acquire-release count publishes all of them and, for the last
+        // CTA, makes the others' visible; the warps do not each wait for their own
+        int old;
+        asm volatile("atom.add.acq_rel.gpu.s32 %0, [%1], 1;" : "=r"(old) : "l"(&a.cnt[i]) : "memory");
+        s_last = old == C - 1;
     }
     __syncthreads();
     return s_last != 0;
