@@ -237,10 +237,10 @@ __global__ void __launch_bounds__(kPT, 2) k_persist(const PParams p) {
         if (!s_skip) run_tile(p, tile, &s_args, work);
         const int next = s_next;
         __syncthreads();  // the tile's stores are done, shared memory may be reused
-        if (threadIdx.x == 0 && tile.done != kNoDep) {
-            __threadfence();
-            atomicAdd(&p.ctr[tile.done], 1u);
-        }
+        // one release increment publishes the CTA's stores (cumulative through the barrier) to the
+        // tiles that wait on this counter with acquire loads
+        if (threadIdx.x == 0 && tile.done != kNoDep)
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&p.ctr[tile.done]) : "memory");
         t = next;
     }
 }
