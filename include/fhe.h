@@ -287,9 +287,11 @@ int fhe_hadd(const fhe_ctx* ctx, uint32_t logN, int n_limbs, int batch, const ui
  *       fhe_device_status). HMULTs run in scratch slots of at most `slot_bytes` in total
  *       (0: 8 GiB; at least one slot); an HMULT waits for the previous one of its slot.
  *       Operations at N < 2^14 run in the grouped form below, before the persistent launch.
+ *       The transforms inside the persistent launch are plain 32-bit two-pass tiles whatever
+ *       the context's default path (results are identical on either path).
  *     FHE_BATCH_GROUPED: every limb transform of one (N, direction) becomes a row of one NTT
- *       launch; HMULTs sharing (N, n_limbs, evk) are gathered into one batched fhe_hmult;
- *       the groups run one after another.
+ *       launch (plain path); HMULTs sharing (N, n_limbs, evk) are gathered into one batched
+ *       fhe_hmult, which follows the context's default path; the groups run one after another.
  *   fhe_batch_scratch_bytes -- device scratch needed by fhe_batch_run / _capture.
  *   fhe_batch_run -- enqueues the plan on `stream` (capturable in a CUDA graph). A persistent
  *     plan's first run on a scratch buffer (and the first after a change of buffer) uploads
