@@ -66,8 +66,9 @@ int run_conv(const fhe_ctx* ctx, const ConvArgs& ca, const ConvTable& ct, dim3 g
     return launch_conv(ca, grid, smem, st);
 }
 
-// ---- KS-4: inner product with the evaluation key (ip_range in ckks_kernels.cuh)
-__global__ void k_inner_product(const IpArgs a) {
+// ---- KS-4: inner product with the evaluation key (ip_range in ckks_kernels.cuh). It waits on
+// memory, so it is built for eight CTAs per SM (32 registers; 38 unbounded, six CTAs).
+__global__ void __launch_bounds__(256, 8) k_inner_product(const IpArgs a) {
     ip_range<false>(a, blockIdx.y, blockIdx.x * (size_t)blockDim.x + threadIdx.x, a.L4, (size_t)gridDim.x * blockDim.x);
 }
 
