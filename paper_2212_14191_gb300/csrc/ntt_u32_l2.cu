@@ -64,7 +64,7 @@ int run_l2(const fhe_ctx* ctx, const NttTables& t, int shape, bool inverse, uint
     int carve = (int)((kMinB<LOG_T> * (smem + 1024) * 100 + 228 * 1024 - 1) / (228 * 1024));
     FHE_CUDA_TRY(cudaFuncSetAttribute(qk, cudaFuncAttributePreferredSharedMemoryCarveout, carve > 100 ? 100 : carve));
     const NttTables& ts = ctx->ntt[LOG_T + 5];  // the NC-point ring degree of the local passes
-    if (!inverse && (!ts.fwd || !ts.fwdC[0] || !t.dit_twist[shape] || !t.dit_omega[shape]))
+    if (!inverse && (!ts.fwd || !ts.fwdC[0] || (C > 1 && (!t.dit_twist[shape] || !t.dit_omega[shape]))))
         return set_error(FHE_EINVAL, "two-pass forward tables missing");
     L2Args a;
     a.data = d;
@@ -122,8 +122,14 @@ int ntt_u32_l2_impl(const fhe_ctx* ctx, uint32_t logN, int shape, bool inverse, 
     const size_t temp_bytes = scr.p ? scr.bytes : kNttTempBytes;
     if (!temp) return set_error(FHE_EINVAL, "no two-pass scratch in this context");
     int log_t, log_c;
-    if (!ntt_variant_shape(logN, shape, &log_t, &log_c) || log_c == 0)
+    if (!ntt_variant_shape(logN, shape, &log_t, &log_c) || (log_c == 0 && !TAIL))
         return set_error(FHE_EINVAL, "two-pass NTT needs N >= 2^15");
+    // N = 2^14 with a tail: one 512-thread CTA per row runs the whole transform and then the
+    // tail's store side as a one-part cross pass
+    if constexpr (TAIL)
+        if (log_t == 9 && log_c == 0)
+            return run_l2<9, 0, TAIL>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes, tail,
+                                      src);
     if (log_t == 9 && log_c == 2)
         return run_l2<9, 2, TAIL>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes, tail, src);
     if (log_t == 9 && log_c == 1)
@@ -161,9 +167,10 @@ int ntt_inv_from(const fhe_ctx* ctx, uint32_t logN, uint32_t* dst, const uint32_
 }
 
 bool ntt_tail_fusable(const fhe_ctx* ctx, int path, uint32_t logN) {
-    if (logN < 15 || logN > FHE_LOGN_MAX) return false;
+    if (logN < 14 || logN > FHE_LOGN_MAX) return false;
     if (path == FHE_NTT_DEFAULT && ctx->ntt_variant[0][logN] >= kNttVariants) return false;  // tensor cores
     if (path != FHE_NTT_DEFAULT && path != FHE_NTT_U32) return false;
+    if (logN == 14) return ctx->ntt[14].fwd != nullptr;  // the one-CTA-per-row shape, whatever the variant
     const int v = ctx->plain_variant[0][logN];
     int log_t, log_c;
     return ntt_variant_exchange(v) == 3 && ntt_variant_shape(logN, v, &log_t, &log_c) && log_c > 0;
@@ -175,7 +182,8 @@ int ntt_u32_l2_tail(const fhe_ctx* ctx, uint32_t logN, int rows, int batch, cons
     if (rows == 0) return FHE_OK;
     const int v = ctx->plain_variant[0][logN];
     // the data pointer is not read or written by the TAIL kernels (rows come from y / go to out)
-    return ntt_u32_l2_impl<true>(ctx, logN, v & 1, false, tail.out, rows, batch, map, nullptr, st, scr, &tail);
+    return ntt_u32_l2_impl<true>(ctx, logN, logN == 14 ? 0 : v & 1, false, tail.out, rows, batch, map, nullptr, st, scr,
+                                 &tail);
 }
 
 }  // namespace fhe

@@ -255,14 +255,17 @@ def test_intt_out_of_place_and_copy_fallback(fhe):
     ctx.close()
 
 
-def test_moddown_combine_fused_matches_separate(fhe):
-    """N = 2^15, 6 + 2 limbs, 2 ciphertexts: with the two-pass forward NTT (variant 6) the ModDown
-    combine of key switching, out += (ks - NTT(y)) P^-1, rides on the forward NTT of y (ks and y
-    pre-scaled by P^-1); with a cluster forward (variant 0) it runs as separate passes. HMULT
-    without rescale, HROTATE and hoisted rotations give identical results both ways, and match
-    the oracle on one ciphertext; key switching alone (no accumulation) keeps the separate form."""
+@pytest.mark.parametrize("logn", [14, 15])
+def test_moddown_combine_fused_matches_separate(fhe, logn):
+    """6 + 2 limbs, 2 ciphertexts: with the plain forward NTT in its fused form (the two-pass
+    kernels at 2^15, the one-CTA-per-row shape at 2^14) the ModDown combine of key switching,
+    out += (ks - NTT(y)) P^-1, rides on the forward NTT of y (ks and y pre-scaled by P^-1), and
+    the HMULT's RESCALE tail likewise; in the other form (a cluster forward variant at 2^15, the
+    tensor-core path at 2^14) they run as separate passes. HMULT with and without rescale,
+    HROTATE and hoisted rotations give identical results both ways, and match the oracle on one
+    ciphertext; key switching alone (no accumulation) keeps the separate form."""
     import torch
-    logn, nl, K, batch = 15, 6, 2, 2
+    nl, K, batch = 6, 2, 2
     n = 1 << logn
     qs, ps = P.default_moduli(nl, K)
     prm = C.Params(n, qs, ps, alpha=2)
@@ -275,17 +278,19 @@ def test_moddown_combine_fused_matches_separate(fhe):
     keys = [rot_key(prm, s, k, 750 + i) for i, k in enumerate(ks)]
     da, db, de = fhe.to_device(A), fhe.to_device(B), fhe.to_device(evk)
     dk = [fhe.to_device(k.astype(np.uint32)) for k in keys]
+    fused, separate = ((6, 6), (0, 6)) if logn == 15 else ((0, 0), (fhe.FHE_NTT_VARIANT_TC64,) * 2)
     res = {}
-    for fwd in (6, 0):
-        fhe.fhe_ntt_set_variant(ctx.handle, logn, fwd, 6)
-        res[fwd] = [ctx.hmult_relin(da, db, de, logn).clone(), ctx.hrotate(da, dk[0], logn, ks[0]).clone(),
-                    ctx.hrotate_hoisted(da, dk, logn, ks).clone()]
+    for name, (fwd, inv) in (("fused", fused), ("separate", separate)):
+        fhe.fhe_ntt_set_variant(ctx.handle, logn, fwd, inv)
+        res[name] = [ctx.hmult_relin(da, db, de, logn).clone(), ctx.hrotate(da, dk[0], logn, ks[0]).clone(),
+                     ctx.hrotate_hoisted(da, dk, logn, ks).clone(), ctx.hmult(da, db, de, logn).clone()]
     torch.cuda.synchronize()
-    for x, y in zip(res[6], res[0]):
+    for x, y in zip(res["fused"], res["separate"]):
         assert torch.equal(x, y)
-    relin, rot = fhe.to_host(res[6][0]), fhe.to_host(res[6][1])
+    relin, rot, hm = fhe.to_host(res["fused"][0]), fhe.to_host(res["fused"][1]), fhe.to_host(res["fused"][3])
     want = C.hmult_relin(prm, nl, A[:, :, 1].astype(U64), B[:, :, 1].astype(U64), evk.astype(U64))
     assert (relin[:, :, 1] == want).all()
     assert (rot[:, :, 0] == C.hrotate(prm, nl, A[:, :, 0].astype(U64), keys[0], ks[0])).all()
+    assert (hm[:, :, 0] == C.hmult(prm, nl, A[:, :, 0].astype(U64), B[:, :, 0].astype(U64), evk.astype(U64))).all()
     fhe.fhe_device_status(ctx.handle, 1)
     ctx.close()
