@@ -163,7 +163,7 @@ struct NttScratch {
     uint32_t* p = nullptr;
     size_t bytes = 0;
 };
-// Bytes of that region for NTT calls of up to `rows` rows at 2^logN (0 below 2^14).
+// Bytes of that region for NTT calls of up to `rows` rows at 2^logN (0 below 2^12).
 size_t ntt_region_bytes(uint32_t logN, size_t rows);
 // Digit-plane buffer of the tensor-core NTT between its two GEMMs: the context's own buffer
 // (fhe_ntt_fwd / fhe_ntt_inv), and the most an operation's scratch region provides for it.

@@ -87,9 +87,9 @@ int ntt_any(const fhe_ctx* ctx, int path, uint32_t logN, bool inverse, uint32_t*
 }
 
 size_t ntt_region_bytes(uint32_t logN, size_t rows) {
-    // from 2^14: the two-pass kernels, and at 2^14 the one-CTA-per-row shape that carries the
-    // fused HMULT tail and ModDown combine
-    if (logN < 14 || rows == 0) return 0;
+    // from 2^15 the two-pass kernels; from 2^12 to 2^14 the one-CTA-per-row shape of the same
+    // kernels that carries the fused HMULT tail and ModDown combine
+    if (logN < 12 || rows == 0) return 0;
     const size_t b = rows * (((size_t)4 << logN) + 4);  // residues and a completion counter per row
     return b < kNttTempBytes ? b : kNttTempBytes;
 }

@@ -124,12 +124,19 @@ int ntt_u32_l2_impl(const fhe_ctx* ctx, uint32_t logN, int shape, bool inverse, 
     int log_t, log_c;
     if (!ntt_variant_shape(logN, shape, &log_t, &log_c) || (log_c == 0 && !TAIL))
         return set_error(FHE_EINVAL, "two-pass NTT needs N >= 2^15");
-    // N = 2^14 with a tail: one 512-thread CTA per row runs the whole transform and then the
-    // tail's store side as a one-part cross pass
-    if constexpr (TAIL)
+    // N <= 2^14 with a tail: one CTA of N / 32 threads per row runs the whole transform and
+    // then the tail's store side as a one-part cross pass
+    if constexpr (TAIL) {
         if (log_t == 9 && log_c == 0)
             return run_l2<9, 0, TAIL>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes, tail,
                                       src);
+        if (log_t == 8 && log_c == 0)
+            return run_l2<8, 0, TAIL>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes, tail,
+                                      src);
+        if (log_t == 7 && log_c == 0)
+            return run_l2<7, 0, TAIL>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes, tail,
+                                      src);
+    }
     if (log_t == 9 && log_c == 2)
         return run_l2<9, 2, TAIL>(ctx, t, shape, inverse, d, rows, batch, map, rowtab, st, temp, temp_bytes, tail, src);
     if (log_t == 9 && log_c == 1)
@@ -167,10 +174,10 @@ int ntt_inv_from(const fhe_ctx* ctx, uint32_t logN, uint32_t* dst, const uint32_
 }
 
 bool ntt_tail_fusable(const fhe_ctx* ctx, int path, uint32_t logN) {
-    if (logN < 14 || logN > FHE_LOGN_MAX) return false;
+    if (logN < 12 || logN > FHE_LOGN_MAX) return false;
     if (path == FHE_NTT_DEFAULT && ctx->ntt_variant[0][logN] >= kNttVariants) return false;  // tensor cores
     if (path != FHE_NTT_DEFAULT && path != FHE_NTT_U32) return false;
-    if (logN == 14) return ctx->ntt[14].fwd != nullptr;  // the one-CTA-per-row shape, whatever the variant
+    if (logN <= 14) return ctx->ntt[logN].fwd != nullptr;  // the one-CTA-per-row shape, whatever the variant
     const int v = ctx->plain_variant[0][logN];
     int log_t, log_c;
     return ntt_variant_exchange(v) == 3 && ntt_variant_shape(logN, v, &log_t, &log_c) && log_c > 0;
@@ -182,7 +189,7 @@ int ntt_u32_l2_tail(const fhe_ctx* ctx, uint32_t logN, int rows, int batch, cons
     if (rows == 0) return FHE_OK;
     const int v = ctx->plain_variant[0][logN];
     // the data pointer is not read or written by the TAIL kernels (rows come from y / go to out)
-    return ntt_u32_l2_impl<true>(ctx, logN, logN == 14 ? 0 : v & 1, false, tail.out, rows, batch, map, nullptr, st, scr,
+    return ntt_u32_l2_impl<true>(ctx, logN, logN <= 14 ? 0 : v & 1, false, tail.out, rows, batch, map, nullptr, st, scr,
                                  &tail);
 }
 
