@@ -16,7 +16,10 @@ mathematics, not against itself:
   CMULT / HADD decrypt exactly to the schoolbook product / the sum;
 * hoisted rotations: the permuted ModUp digits differ from ModUp of the permuted
   c1 by exactly -B_j times the count of nonzero y_i at negated coefficients (big
-  ints), k = 1 reproduces HROTATE, and every rotation decrypts within the bound.
+  ints), k = 1 reproduces HROTATE, and every rotation decrypts within the bound;
+* the inverse Galois element by Newton's iteration equals the modular inverse, and
+  permuting the key by sigma_{k^-1} and the inner product by sigma_k reproduces the
+  hoisted rotation bit for bit.
 """
 import math
 
@@ -459,6 +462,60 @@ def test_hoisted_rotations_decrypt_to_rotations(small):
         slots = C.decode(np.array(dec, dtype=float), delta)
         target = np.roll(z, -rs[i]) if i < len(rs) else np.conj(z)
         assert np.abs(slots - target).max() < 1e-2
+
+
+def _newton_inv_pow2(k, bits):
+    """Inverse of an odd k modulo 2^bits (bits <= 32) by Newton's iteration x <- x (2 - k x)
+    in 32-bit wrap-around arithmetic: x = k is right to 3 bits (k^2 = 1 mod 8) and each step
+    doubles that, so five steps give 96 >= 32 bits."""
+    x = k
+    for _ in range(5):
+        x = (x * ((2 - k * x) % 2 ** 32)) % 2 ** 32
+    return x % (2 ** bits)
+
+
+def test_newton_inverse_of_galois_elements():
+    """The inverse Galois element k^-1 mod 2N for every odd k at N = 2^10 and a sample at
+    2^16: k k^-1 = 1 mod 2N and it equals Python's modular inverse."""
+    for logn in (10, 16):
+        two_n = 2 ** (logn + 1)
+        ks = range(1, two_n, 2) if logn == 10 else [1, 3, 5, 25, 5 ** 7 % two_n, two_n - 1, 2 ** logn + 1]
+        for k in ks:
+            kinv = _newton_inv_pow2(k, logn + 1)
+            assert (k * kinv) % two_n == 1
+            assert kinv == pow(k, -1, two_n)
+
+
+def test_hoisted_key_permutation_order(small):
+    """The hoisted rotation can permute each key by sigma_{k^-1} once, take the inner product
+    with the unpermuted ModUp digits and permute that sum by sigma_k: since sigma_k only
+    permutes NTT slots it commutes with the slot-wise product, so
+    sum_j sigma_k(d_j) (.) e_j = sigma_k(sum_j d_j (.) sigma_{k^-1}(e_j)) exactly. With ModDown
+    and c0(X^k) added, this order reproduces hrotate_hoisted bit for bit (k a rotation and
+    the conjugation); sigma_{k^-1} sigma_k is the identity on the extended limbs."""
+    prm, s, _ = small
+    nl, N = 7, prm.N
+    mods, psis = prm.qs[:nl], prm.psi_q[:nl]
+    emods = prm.qs[:nl] + prm.ps
+    epsis = prm.psi_q[:nl] + prm.psi_p
+    ct = I.uniform_residues(320, mods, 2, N, dtype=np.uint64).transpose(1, 0, 2)
+    c1_coeff = C.intt(ct[1], mods, psis)
+    digits = [C.modup(prm, nl, ct[1], c1_coeff, j) for j in range(prm.dnum(nl))]
+    for i, k in enumerate((C.galois_rotation(3, N), C.galois_conjugation(N))):
+        key = _rot_key(prm, s, k, 330 + 2 * i)
+        kinv = _newton_inv_pow2(k, int(math.log2(N)) + 1)
+        assert (C.automorph(C.automorph(digits[0], emods, epsis, k), emods, epsis, kinv) == digits[0]).all()
+        ks = []
+        for c in range(2):
+            acc = np.zeros((nl + prm.K, N), dtype=U64)
+            for j, dt in enumerate(digits):
+                ek = C.evk_at_level(prm, key, j, nl)[c]
+                acc = C.add(acc, C.hada(dt, C.automorph(ek, emods, epsis, kinv), emods), emods)
+            ks.append(C.automorph(acc, emods, epsis, k))
+        c0 = C.automorph(ct[0], mods, psis, k)
+        got = np.stack([C.add(c0, C.moddown(prm, nl, ks[0]), mods),
+                        C.moddown(prm, nl, ks[1]) % np.array(mods, dtype=U64)[:, None]])
+        assert (got == C.hrotate_hoisted(prm, nl, ct, [key], [k])[0]).all()
 
 
 def test_conv_hand_worked_example():
