@@ -623,6 +623,7 @@ def other_ops(args, fhe, hctx, a, b, evk, st, barrier, max_over_ranks, ws):
 # into L ciphertext limbs and K special primes with P > Q (one key-switching slice, dnum = 1).
 HEAX_SETS = tuple((h.name, h.logN, h.L, h.K) for h in CFG.HEAX_SETS)
 HEAX_BATCH = CFG.HEAX_BATCH
+HEAX_BATCH_SWEEP = CFG.HEAX_BATCH_SWEEP
 PAPER_A100 = {"Set_A": (910134, 913267, 88048), "Set_B": (449974, 449084, 27564), "Set_C": (209337, 209178, 3825)}
 
 
@@ -630,11 +631,25 @@ def heax_sets(args, fhe, st, barrier, max_over_ranks, ws):
     """#NTT/s, #INTT/s (one op = one limb transform) and #HMULT/s (HMULT + relinearisation +
     rescale, one op = one ciphertext pair) at the paper's HEAX comparison sets, 1024
     ciphertexts per call, on the plain path with autotuned variants. The paper's A100 numbers
-    are context, not targets."""
+    are context, not targets. `batch_sweep` gives #NTT/s and #HMULT/s of each set at 32 to 1024
+    ciphertexts per call (the batch-size study of Sec. VI-E), with the variants tuned at 1024."""
     import torch
     from paper_2212_14191_gb300 import inputs as I
     allp = fhe.fhe_gen_primes(16, 30, 16)
     res = {"config": "L ciphertext limbs + K special primes of 30 bits, dnum=1, %d ciphertexts per call" % HEAX_BATCH}
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        barrier()
+        return max_over_ranks(e0.elapsed_time(e1) / 1e3) / reps
+
     for name, logn, L, K in HEAX_SETS:
         n = 1 << logn
         ps, qs = allp[:K], allp[K:K + L]
@@ -675,6 +690,20 @@ def heax_sets(args, fhe, st, barrier, max_over_ranks, ws):
         t = max_over_ranks(e0.elapsed_time(e1) / 1e3) / 10
         r["hmult_per_s"] = HEAX_BATCH * ws / t
         r["paper_a100"] = dict(zip(("ntt_per_s", "intt_per_s", "hmult_per_s"), PAPER_A100[name]))
+        sweep = {}
+        for nb in HEAX_BATCH_SWEEP:
+            if nb >= HEAX_BATCH:
+                sweep[str(HEAX_BATCH)] = {"ntt_per_s": r["ntt_per_s"], "hmult_per_s": r["hmult_per_s"]}
+                continue
+            xs = x[:, :nb].contiguous()
+            an, bn = a[:, :, :nb].contiguous(), b[:, :, :nb].contiguous()
+            on = torch.empty((2, L - 1, nb, n), dtype=torch.int32, device="cuda")
+            tn = timed(lambda: fhe.fhe_ntt_fwd(c.handle, fhe.FHE_NTT_U32, logn, xs.data_ptr(), 0, 4, nb,
+                                               st.cuda_stream), 20)
+            th = timed(lambda: c.hmult(an, bn, evk, logn, out=on), 10)
+            sweep[str(nb)] = {"ntt_per_s": 4 * nb * ws / tn, "hmult_per_s": nb * ws / th}
+            del xs, an, bn, on
+        r["batch_sweep"] = sweep
         fhe.fhe_device_status(c.handle, 1)
         res[name] = r
         c.close()

@@ -74,3 +74,5 @@ SERVING = ServingStream(rate_per_s=50000.0, logNs=(15, 16), limb_range=(3, 24), 
                         streams=4, max_batch=32)
 HEAX_SETS = (HeaxSet("Set_A", 12, 2, 2), HeaxSet("Set_B", 13, 4, 4), HeaxSet("Set_C", 14, 7, 8))
 HEAX_BATCH = 1024
+# batch sizes of the sets' batch-size sensitivity (Sec. VI-E: 32 to 1024 ciphertexts per call)
+HEAX_BATCH_SWEEP = (32, 64, 128, 256, 512, 1024)

@@ -24,6 +24,10 @@ def test_bench_reads_the_sets():
     assert (bench.HM_LIMBS, bench.HM_K, bench.HM_ALPHA, bench.HM_BATCH) == (
         CFG.HMULT_FULL.limbs, CFG.HMULT_FULL.special, CFG.HMULT_FULL.alpha, CFG.HMULT_FULL.batch)
     assert bench.HEAX_SETS == tuple((s.name, s.logN, s.L, s.K) for s in CFG.HEAX_SETS)
+    # the batch-size study spans 32 to 1024 ciphertexts per call and ends at the main batch
+    assert bench.HEAX_BATCH_SWEEP == CFG.HEAX_BATCH_SWEEP
+    assert CFG.HEAX_BATCH_SWEEP[0] == 32 and CFG.HEAX_BATCH_SWEEP[-1] == CFG.HEAX_BATCH
+    assert list(CFG.HEAX_BATCH_SWEEP) == sorted(set(CFG.HEAX_BATCH_SWEEP))
 
 
 def test_special_primes_exceed_every_slice():
