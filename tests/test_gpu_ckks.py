@@ -235,6 +235,31 @@ def test_hmult_heax_sets_bitexact(fhe, logn, L, K):
     ctx.close()
 
 
+@pytest.mark.parametrize("logn,L,K", [(12, 2, 2), (13, 4, 4), (14, 7, 8)])
+def test_hmult_heax_sets_benchmarked_batch(fhe, logn, L, K):
+    """The HEAX sets at the benchmark's 1024 ciphertexts per call: every stage on its full grid,
+    and at N = 2^13 and 2^14 the fused RESCALE tail's cross pass inside the local-pass launch (a
+    separate launch at batch 2, and at 2^12 with 1024 too): HMULT + relinearisation + rescale
+    bit-exact against the oracle on sampled pairs."""
+    import torch
+    from paper_2212_14191_gb300 import configs as CFG
+    n, batch = 1 << logn, CFG.HEAX_BATCH
+    allp = P.ntt_primes(L + K)
+    ps, qs = allp[:K], allp[K:]
+    prm = C.Params(n, qs, ps, alpha=L)
+    _, evk = make_key(prm, 350 + logn)
+    a, b = batch_cts(prm, L, batch, 360 + logn), batch_cts(prm, L, batch, 370 + logn)
+    ctx = fhe.Context(logn, qs, ps, alpha=L)
+    out = ctx.hmult(fhe.to_device(a), fhe.to_device(b), fhe.to_device(evk.astype(np.uint32)), logn)
+    torch.cuda.synchronize()
+    got = fhe.to_host(out)
+    for k in (0, batch // 2 - 1, batch - 1):
+        want = C.hmult(prm, L, a[:, :, k].astype(U64), b[:, :, k].astype(U64), evk)
+        assert (got[:, :, k] == want).all(), k
+    fhe.fhe_device_status(ctx.handle, 1)
+    ctx.close()
+
+
 def test_concurrent_streams_share_a_context(fhe):
     """HMULTs of one context on eight streams at once, with the two-pass NTT variants (whose
     chunk buffer each call takes from its own scratch): every result equals the result of the
