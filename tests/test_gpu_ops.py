@@ -176,33 +176,41 @@ def test_ops_bad_arguments(fhe, small):
 
 
 def test_hrotate_full_size_config(fhe):
-    """N = 2^16, 24 ciphertext limbs + 8 special primes, dnum = 3, 4 ciphertexts: sampled
-    (limb, ciphertext) rows of the GPU result against the oracle's rotation of that ciphertext."""
+    """The benchmarked configuration of the other operations: N = 2^16, 24 ciphertext limbs +
+    8 special primes, dnum = 3, 128 ciphertexts in one call, where the ModDown combine's cross
+    passes run inside the forward NTT's local-pass launch. The first, middle and last
+    ciphertexts of HROTATE, CMULT and HADD against the oracle, bit for bit."""
     import torch
-    logn, n, nl, K, batch = 16, 1 << 16, 24, 8, 4
+    logn, n, nl, K, batch = 16, 1 << 16, 24, 8, 128
     qs, ps = P.default_moduli(nl, K)
     prm = C.Params(n, qs, ps, alpha=8)
     s = I.ternary_secret(160, n, hamming_weight=64)
     k = C.galois_rotation(1, n)
     ksk = rot_key(prm, s, k, 161)
-    ct = batch_cts(prm, nl, batch, 162)
+    ct, ct2 = batch_cts(prm, nl, batch, 162), batch_cts(prm, nl, batch, 163)
+    pt = I.uniform_residues(164, qs[:nl], batch, n)
     ctx = fhe.Context(logn, qs, ps, alpha=8)
-    out = ctx.hrotate(fhe.to_device(ct), fhe.to_device(ksk.astype(np.uint32)), logn, k)
+    da, db, dp = fhe.to_device(ct), fhe.to_device(ct2), fhe.to_device(pt)
+    got = fhe.to_host(ctx.hrotate(da, fhe.to_device(ksk.astype(np.uint32)), logn, k))
+    cm = fhe.to_host(ctx.cmult(da, dp, logn))
+    ha = fhe.to_host(ctx.hadd(da, db, logn))
     torch.cuda.synchronize()
-    got = fhe.to_host(out)
-    for b in (0, batch - 1):
-        want = C.hrotate(prm, nl, ct[:, :, b].astype(U64), ksk, k)
-        assert (got[:, :, b] == want).all(), b
+    for b in (0, batch // 2 - 1, batch - 1):
+        a_b = ct[:, :, b].astype(U64)
+        assert (got[:, :, b] == C.hrotate(prm, nl, a_b, ksk, k)).all(), b
+        assert (cm[:, :, b] == C.cmult(prm, nl, a_b, pt[:, b].astype(U64))).all(), b
+        assert (ha[:, :, b] == C.hadd(prm, nl, a_b, ct2[:, :, b].astype(U64))).all(), b
     fhe.fhe_device_status(ctx.handle, 1)
     ctx.close()
 
 
 def test_hrotate_hoisted_full_size_config(fhe):
-    """N = 2^16, 24 ciphertext limbs + 8 special primes, dnum = 3, 4 ciphertexts, a rotation
-    and the conjugation sharing one ModUp: the first and last ciphertexts of the GPU result
-    against the oracle's hoisted rotation of that ciphertext, bit for bit."""
+    """N = 2^16, 24 ciphertext limbs + 8 special primes, dnum = 3, the benchmarked 128
+    ciphertexts, a rotation and the conjugation sharing one ModUp: the first, middle and last
+    ciphertexts of the GPU result against the oracle's hoisted rotation of that ciphertext,
+    bit for bit."""
     import torch
-    logn, n, nl, K, batch = 16, 1 << 16, 24, 8, 4
+    logn, n, nl, K, batch = 16, 1 << 16, 24, 8, 128
     qs, ps = P.default_moduli(nl, K)
     prm = C.Params(n, qs, ps, alpha=8)
     s = I.ternary_secret(160, n, hamming_weight=64)
@@ -213,7 +221,7 @@ def test_hrotate_hoisted_full_size_config(fhe):
     out = ctx.hrotate_hoisted(fhe.to_device(ct), [fhe.to_device(k.astype(np.uint32)) for k in keys], logn, ks)
     torch.cuda.synchronize()
     got = fhe.to_host(out)
-    for b in (0, batch - 1):
+    for b in (0, batch // 2 - 1, batch - 1):
         want = C.hrotate_hoisted(prm, nl, ct[:, :, b].astype(U64), keys, ks)
         for r in range(len(ks)):
             assert (got[r, :, :, b] == want[r]).all(), (b, r)
