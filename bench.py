@@ -787,10 +787,36 @@ def mixed_batch(args, fhe, ctx, qs, ps, st, barrier, max_over_ranks, ws):
     t_grouped = timed(lambda: fhe.fhe_batch_launch(gplan, sh), 3)
     t_ops = timed(per_op, 2)
     n_hm = sum(1 for d in desc if d[0] == fhe.FHE_OPK_HMULT)
+    # every operation of both plans against its single call, after the timed regions: the
+    # in-place NTT buffers are restored to one state before each run, the HMULT outputs cleared
+    ntt_t = [t for k, _, _, t in desc if k != fhe.FHE_OPK_HMULT]
+    hm_out = [t[2] for k, _, _, t in desc if k == fhe.FHE_OPK_HMULT]
+    start = [t.clone() for t in ntt_t]
+
+    def run_from_start(fn):
+        torch.cuda.synchronize()
+        for t, t0 in zip(ntt_t, start):
+            t.copy_(t0)
+        for o in hm_out:
+            o.zero_()
+        torch.cuda.synchronize()
+        fn()
+        torch.cuda.synchronize()
+        return [t.clone() for t in ntt_t + hm_out]
+
+    got_p = run_from_start(lambda: fhe.fhe_batch_launch(plan, sh))
+    got_g = run_from_start(lambda: fhe.fhe_batch_launch(gplan, sh))
+    want = run_from_start(per_op)
+    bad_p = sum(1 for x, y in zip(got_p, want) if not torch.equal(x, y))
+    bad_g = sum(1 for x, y in zip(got_g, want) if not torch.equal(x, y))
+    del start, got_p, got_g, want
+    assert bad_p == 0 and bad_g == 0, (bad_p, bad_g)
     res = {"ops": n_ops, "hmult_ops": n_hm, "ntt_ops": n_ops - n_hm, "ntt_limb_transforms": limb_transforms,
            "graph_ms": t_graph * 1e3, "grouped_graph_ms": t_grouped * 1e3, "per_op_ms": t_ops * 1e3,
            "graph_kops": n_ops * ws / t_graph / 1e3, "grouped_graph_kops": n_ops * ws / t_grouped / 1e3,
            "per_op_kops": n_ops * ws / t_ops / 1e3, "scratch_bytes": nbytes,
+           "checked": {"ops": n_ops, "persistent_mismatches": bad_p, "grouped_mismatches": bad_g,
+                       "against": "one library call per operation from the same inputs"},
            "config": "N in {2^14,2^15,2^16}, 3..44 limbs, batch 1 per op; graph replay of the persistent plan "
                      "(one launch, device work queue) vs the grouped plan vs one call per op",
            "ntt_variant_16": [fhe.fhe_ntt_get_variant(ctx.handle, 16, 0), fhe.fhe_ntt_get_variant(ctx.handle, 16, 1)]}
