@@ -260,6 +260,52 @@ def test_hmult_heax_sets_benchmarked_batch(fhe, logn, L, K):
     ctx.close()
 
 
+def _extreme(mods, count, n, kind):
+    """(len(mods), count, n) uint32 residues at the ends of each range: all q - 1 ("max") or
+    q - 1 at even and 0 at odd coefficients ("alt")."""
+    q = np.array(mods, dtype=np.uint64)[:, None, None]
+    x = np.broadcast_to(q - 1, (len(mods), count, n)).copy()
+    if kind == "alt":
+        x[:, :, 1::2] = 0
+    return x.astype(np.uint32)
+
+
+@pytest.mark.parametrize("logn,batch", [(12, 2), (15, 2), (16, 32)])
+def test_ckks_ops_extreme_residues(fhe, logn, batch):
+    """Ciphertexts, d2 and keys at the ends of every residue range (all q - 1, or q - 1 and 0
+    alternating), 6 + 2 limbs, dnum = 3: HMULT, HMULT + relinearisation, key switching, RESCALE
+    and HROTATE bit-exact against the oracle for every ciphertext of the batch. These are the
+    inputs that push the lazy reductions (Shoup, Montgomery, the fused tails' loads) to the top
+    of their ranges; at N = 2^16 with 32 ciphertexts the fused tails' cross passes run inside
+    the local-pass launch, at 2^15 in a separate one, at 2^12 on the one-CTA-per-row shape."""
+    import torch
+    nl, K, alpha = 6, 2, 2
+    n = 1 << logn
+    qs, ps = P.default_moduli(nl, K)
+    prm = C.Params(n, qs, ps, alpha=alpha)
+    dn = prm.dnum(nl)
+    a = np.stack([_extreme(qs, batch, n, "max"), _extreme(qs, batch, n, "alt")])
+    b = np.stack([_extreme(qs, batch, n, "alt"), _extreme(qs, batch, n, "max")])
+    evk = _extreme(qs + ps, 2 * dn, n, "max").reshape(nl + K, dn, 2, n).transpose(1, 2, 0, 3).copy()
+    k = C.galois_rotation(1, n)
+    ctx = fhe.Context(logn, qs, ps, alpha=alpha)
+    da, db, de = fhe.to_device(a), fhe.to_device(b), fhe.to_device(evk)
+    got = {"hmult": ctx.hmult(da, db, de, logn), "relin": ctx.hmult_relin(da, db, de, logn),
+           "ks": ctx.keyswitch(da[0].contiguous(), de, logn), "rescale": ctx.rescale(da, logn),
+           "hrotate": ctx.hrotate(da, de, logn, k)}
+    torch.cuda.synchronize()
+    got = {name: fhe.to_host(v) for name, v in got.items()}
+    a0, b0, e64 = a[:, :, 0].astype(U64), b[:, :, 0].astype(U64), evk.astype(U64)
+    want = {"hmult": C.hmult(prm, nl, a0, b0, e64), "relin": C.hmult_relin(prm, nl, a0, b0, e64),
+            "ks": np.stack(C.keyswitch(prm, nl, a0[0], e64)), "rescale": C.rescale(prm, a0),
+            "hrotate": C.hrotate(prm, nl, a0, e64, k)}
+    for name in want:
+        for j in range(batch):
+            assert (got[name][:, :, j] == want[name]).all(), (name, j)
+    fhe.fhe_device_status(ctx.handle, 1)
+    ctx.close()
+
+
 def test_concurrent_streams_share_a_context(fhe):
     """HMULTs of one context on eight streams at once, with the two-pass NTT variants (whose
     chunk buffer each call takes from its own scratch): every result equals the result of the
