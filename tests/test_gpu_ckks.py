@@ -273,11 +273,12 @@ def _extreme(mods, count, n, kind):
 @pytest.mark.parametrize("logn,batch", [(12, 2), (15, 2), (16, 32)])
 def test_ckks_ops_extreme_residues(fhe, logn, batch):
     """Ciphertexts, d2 and keys at the ends of every residue range (all q - 1, or q - 1 and 0
-    alternating), 6 + 2 limbs, dnum = 3: HMULT, HMULT + relinearisation, key switching, RESCALE
-    and HROTATE bit-exact against the oracle for every ciphertext of the batch. These are the
-    inputs that push the lazy reductions (Shoup, Montgomery, the fused tails' loads) to the top
-    of their ranges; at N = 2^16 with 32 ciphertexts the fused tails' cross passes run inside
-    the local-pass launch, at 2^15 in a separate one, at 2^12 on the one-CTA-per-row shape."""
+    alternating), 6 + 2 limbs, dnum = 3: HMULT, HMULT + relinearisation, key switching, RESCALE,
+    HROTATE and hoisted rotations (a rotation and the conjugation) bit-exact against the oracle
+    for every ciphertext of the batch. These are the inputs that push the lazy reductions
+    (Shoup, Montgomery, the fused tails' loads) to the top of their ranges; at N = 2^16 with 32
+    ciphertexts the fused tails' cross passes run inside the local-pass launch, at 2^15 in a
+    separate one, at 2^12 on the one-CTA-per-row shape."""
     import torch
     nl, K, alpha = 6, 2, 2
     n = 1 << logn
@@ -292,7 +293,8 @@ def test_ckks_ops_extreme_residues(fhe, logn, batch):
     da, db, de = fhe.to_device(a), fhe.to_device(b), fhe.to_device(evk)
     got = {"hmult": ctx.hmult(da, db, de, logn), "relin": ctx.hmult_relin(da, db, de, logn),
            "ks": ctx.keyswitch(da[0].contiguous(), de, logn), "rescale": ctx.rescale(da, logn),
-           "hrotate": ctx.hrotate(da, de, logn, k)}
+           "hrotate": ctx.hrotate(da, de, logn, k),
+           "hoisted": ctx.hrotate_hoisted(da, [de, de], logn, [k, C.galois_conjugation(n)])}
     torch.cuda.synchronize()
     got = {name: fhe.to_host(v) for name, v in got.items()}
     a0, b0, e64 = a[:, :, 0].astype(U64), b[:, :, 0].astype(U64), evk.astype(U64)
@@ -302,6 +304,10 @@ def test_ckks_ops_extreme_residues(fhe, logn, batch):
     for name in want:
         for j in range(batch):
             assert (got[name][:, :, j] == want[name]).all(), (name, j)
+    hw = C.hrotate_hoisted(prm, nl, a0, [e64, e64], [k, C.galois_conjugation(n)])
+    for r in range(2):
+        for j in range(batch):
+            assert (got["hoisted"][r, :, :, j] == hw[r]).all(), (r, j)
     fhe.fhe_device_status(ctx.handle, 1)
     ctx.close()
 
