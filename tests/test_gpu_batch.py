@@ -352,3 +352,65 @@ def test_persistent_queue_wait_expires(fhe):
     assert (fhe.to_host(d) == ref).all()
     fhe.fhe_batch_destroy(plan)
     ctx.close()
+
+
+def _extreme(mods, count, n, kind):
+    """(len(mods), count, n) uint32 residues: all q - 1 ("max") or q - 1 and 0 alternating."""
+    q = np.array(mods, dtype=np.uint64)[:, None, None]
+    x = np.broadcast_to(q - 1, (len(mods), count, n)).copy()
+    if kind == "alt":
+        x[:, :, 1::2] = 0
+    return x.astype(np.uint32)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_batch_extreme_residues(fhe, mode):
+    """A plan at N = 2^14..2^16 whose operands and keys sit at the ends of their residue ranges
+    (all q - 1, or q - 1 and 0 alternating): NTT and INTT rows and HMULTs through the persistent
+    engine's stage bodies (and the grouped launches) equal their single calls, and one HMULT
+    equals the oracle's."""
+    import torch
+    qs, ps = P.default_moduli(12, 4)
+    mods = qs + ps
+    ctx = fhe.Context(16, qs, ps, alpha=4)
+    dn = -(-len(qs) // 4)
+    evk_h = {lg: _extreme(mods, 2 * dn, 1 << lg, "max").reshape(len(mods), dn, 2, 1 << lg).transpose(1, 2, 0, 3).copy()
+             for lg in (15, 16)}
+    evks = {lg: fhe.to_device(e) for lg, e in evk_h.items()}
+    ops, keep = [], []
+    for lg, kind, first, nl, batch, pat in ((16, fhe.FHE_OPK_NTT_FWD, 0, 6, 2, "max"),
+                                            (15, fhe.FHE_OPK_NTT_INV, 2, 8, 1, "alt"),
+                                            (14, fhe.FHE_OPK_NTT_FWD, 10, 6, 3, "alt"),
+                                            (16, fhe.FHE_OPK_NTT_INV, 0, 16, 1, "max")):
+        x = _extreme(mods[first:first + nl], batch, 1 << lg, pat)
+        d = fhe.to_device(x)
+        ops.append(fhe.FheOp(kind=kind, logN=lg, first_limb=first, n_limbs=nl, batch=batch, data=d.data_ptr()))
+        keep.append(("ntt", lg, first, nl, batch, d, x, kind))
+    hm = []
+    for lg, nl, batch in ((16, 6, 2), (15, 9, 1)):
+        n = 1 << lg
+        a_h = np.stack([_extreme(qs[:nl], batch, n, "max"), _extreme(qs[:nl], batch, n, "alt")])
+        b_h = np.stack([_extreme(qs[:nl], batch, n, "alt"), _extreme(qs[:nl], batch, n, "max")])
+        a, b = fhe.to_device(a_h), fhe.to_device(b_h)
+        out = torch.empty((2, nl - 1, batch, n), dtype=torch.int32, device="cuda")
+        ops.append(fhe.FheOp(kind=fhe.FHE_OPK_HMULT, logN=lg, n_limbs=nl, batch=batch, a=a.data_ptr(),
+                             b=b.data_ptr(), evk=evks[lg].data_ptr(), out=out.data_ptr()))
+        keep.append(("hmult", lg, nl, batch, a, b, evks[lg], out))
+        hm.append((lg, nl, a_h, b_h))
+    want = reference_results(fhe, ctx, keep)
+    plan = create(fhe, ctx, ops, mode)
+    nbytes = fhe.fhe_batch_scratch_bytes(plan)
+    scratch = torch.empty(max(4, nbytes // 4 + 4), dtype=torch.int32, device="cuda")
+    fhe.fhe_batch_run(plan, scratch.data_ptr(), nbytes, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    got = batch_results(fhe, keep)
+    for i, (w, g) in enumerate(zip(want, got)):
+        assert (w == g).all(), i
+    lg, nl, a_h, b_h = hm[0]
+    prm = C.Params(1 << lg, qs, ps, alpha=4)
+    oracle = C.hmult(prm, nl, a_h[:, :, 0].astype(np.uint64), b_h[:, :, 0].astype(np.uint64),
+                     evk_h[lg].astype(np.uint64))
+    assert (got[len(keep) - 2][:, :, 0] == oracle).all()
+    fhe.fhe_device_status(ctx.handle, 1)
+    fhe.fhe_batch_destroy(plan)
+    ctx.close()
