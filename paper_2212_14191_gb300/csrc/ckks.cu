@@ -67,9 +67,26 @@ int run_conv(const fhe_ctx* ctx, const ConvArgs& ca, const ConvTable& ct, dim3 g
 }
 
 // ---- KS-4: inner product with the evaluation key (ip_range in ckks_kernels.cuh). It waits on
-// memory, so it is built for eight CTAs per SM (32 registers; 38 unbounded, six CTAs).
-__global__ void __launch_bounds__(256, 8) k_inner_product(const IpArgs a) {
-    ip_range<false>(a, blockIdx.y, blockIdx.x * (size_t)blockDim.x + threadIdx.x, a.L4, (size_t)gridDim.x * blockDim.x);
+// memory. With the slice count fixed at compile time (1 to 4) the slice loop unrolls, so every
+// slice's loads issue before the first product, at five CTAs per SM (at most 48 registers, no
+// spill). Larger counts spill when unrolled and take the loop as it is, at eight CTAs per SM
+// (32 registers).
+template <int DN>
+__global__ void __launch_bounds__(256, DN > 0 ? 5 : 8) k_inner_product(const IpArgs a) {
+    ip_range<false, DN>(a, blockIdx.y, blockIdx.x * (size_t)blockDim.x + threadIdx.x, a.L4,
+                        (size_t)gridDim.x * blockDim.x);
+}
+
+int launch_inner_product(const IpArgs& ia, dim3 g, cudaStream_t st) {
+    switch (ia.dnum) {
+        case 1: k_inner_product<1><<<g, 256, 0, st>>>(ia); break;
+        case 2: k_inner_product<2><<<g, 256, 0, st>>>(ia); break;
+        case 3: k_inner_product<3><<<g, 256, 0, st>>>(ia); break;
+        case 4: k_inner_product<4><<<g, 256, 0, st>>>(ia); break;
+        default: k_inner_product<0><<<g, 256, 0, st>>>(ia); break;
+    }
+    FHE_CUDA_TRY(cudaGetLastError());
+    return FHE_OK;
 }
 
 // ---- KS-5 tail + HM-2: out_c[i] (+)= (ks_c[i] - y_c[i]) * [P^-1]_{q_i}
@@ -346,8 +363,7 @@ int ks_finish(const fhe_ctx* ctx, uint32_t logN, int nl, int batch, const uint32
         ia.N4 = N / 4;
         ia.m = ext_m;
         ip_set_post(ctx, ia, nl, ext, ip_scale, !fuse_combine);
-        k_inner_product<<<stream_grid(ctx, L4, ext), 256, 0, st>>>(ia);
-        FHE_CUDA_TRY(cudaGetLastError());
+        if ((rc = launch_inner_product(ia, stream_grid(ctx, L4, ext), st))) return rc;
         if (galois && (rc = launch_automorph(ctx, ks_pre, ks, galois, logN, 2 * (size_t)ext * batch, st))) return rc;
     }
     // KS-5: ModDown of ks0, ks1

@@ -268,8 +268,9 @@ inline void ip_set_post(const fhe_ctx* ctx, IpArgs& ia, int nl, int ext, int sca
     }
 }
 
-template <bool COH>
+template <bool COH, int DN = 0>
 __device__ __forceinline__ void ip_range(const IpArgs& a, int t, size_t i, size_t end, size_t step) {
+    const int dnum = DN > 0 ? DN : a.dnum;
     const Red rd = red_of(a.m, t);
     const uint32_t q = a.m.q[t], qinv = a.m.qinv[t];
     const uint2 post = a.post[t];
@@ -281,7 +282,8 @@ __device__ __forceinline__ void ip_range(const IpArgs& a, int t, size_t i, size_
         const size_t n4 = i % a.N4;
         // products < 2^60: up to 15 of them accumulate exactly in 64 bits, then one reduction
         uint64_t r0[4] = {0, 0, 0, 0}, r1[4] = {0, 0, 0, 0};
-        for (int j = 0; j < a.dnum; ++j) {
+#pragma unroll
+        for (int j = 0; j < dnum; ++j) {
             if (j > 0 && j % 15 == 0) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {

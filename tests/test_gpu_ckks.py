@@ -66,6 +66,35 @@ def test_keyswitch_bitexact(fhe, small, nl):
         assert (got[0, :, b] == k0).all() and (got[1, :, b] == k1).all(), b
 
 
+@pytest.mark.parametrize("nl,alpha", [(3, 3), (4, 2), (8, 2), (5, 1)])
+def test_keyswitch_slice_counts(fhe, nl, alpha):
+    """Key switching with dnum = 1, 2, 4 and 5 slices at N = 2^12, 3 ciphertexts: the inner
+    product's unrolled kernels (1 to 4 slices) and its generic loop (5) bit-exact against the
+    oracle, in HMULT + relinearisation as well."""
+    import torch
+    logn = 12
+    n = 1 << logn
+    qs, ps = P.default_moduli(nl, alpha)
+    prm = C.Params(n, qs, ps, alpha=alpha)
+    dn = prm.dnum(nl)
+    evk = I.uniform_residues(60 + nl, qs + ps, 2 * dn, n).reshape(nl + alpha, dn, 2, n).transpose(1, 2, 0, 3).copy()
+    d2 = I.uniform_residues(70 + nl, qs, 3, n)
+    a, b = batch_cts(prm, nl, 3, 80 + nl), batch_cts(prm, nl, 3, 90 + nl)
+    ctx = fhe.Context(logn, qs, ps, alpha=alpha)
+    de = fhe.to_device(evk)
+    ks = fhe.to_host(ctx.keyswitch(fhe.to_device(d2), de, logn))
+    rel = fhe.to_host(ctx.hmult_relin(fhe.to_device(a), fhe.to_device(b), de, logn))
+    torch.cuda.synchronize()
+    e64 = evk.astype(U64)
+    for j in range(3):
+        k0, k1 = C.keyswitch(prm, nl, d2[:, j].astype(U64), e64)
+        assert (ks[0, :, j] == k0).all() and (ks[1, :, j] == k1).all(), j
+        want = C.hmult_relin(prm, nl, a[:, :, j].astype(U64), b[:, :, j].astype(U64), e64)
+        assert (rel[:, :, j] == want).all(), j
+    fhe.fhe_device_status(ctx.handle, 1)
+    ctx.close()
+
+
 @pytest.mark.parametrize("nl", [2, 3, 7, 12])
 def test_rescale_bitexact(fhe, small, nl):
     import torch
