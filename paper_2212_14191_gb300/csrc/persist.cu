@@ -197,7 +197,14 @@ __device__ void run_tile(const PParams& p, const PTile& t, TileArgs* sa, uint32_
             copy_args(&p.ip[t.desc], sa);
             __syncthreads();
             chunk_range(sa->ip.L4, t.y, &i0, &i1);
-            ip_range<true>(sa->ip, t.x, i0, i1, kPT);
+            // the slice loop unrolled where it fits without spilling (1 to 4 slices)
+            switch (sa->ip.dnum) {
+                case 1: ip_range<true, 1>(sa->ip, t.x, i0, i1, kPT); break;
+                case 2: ip_range<true, 2>(sa->ip, t.x, i0, i1, kPT); break;
+                case 3: ip_range<true, 3>(sa->ip, t.x, i0, i1, kPT); break;
+                case 4: ip_range<true, 4>(sa->ip, t.x, i0, i1, kPT); break;
+                default: ip_range<true>(sa->ip, t.x, i0, i1, kPT); break;
+            }
             break;
         case PK_RELIN_LAST:
             copy_args(&p.last[t.desc], sa);
