@@ -268,6 +268,8 @@ inline void ip_set_post(const fhe_ctx* ctx, IpArgs& ia, int nl, int ext, int sca
     }
 }
 
+// DN > 0: the slice count as a compile-time constant, so the slice loop unrolls and every
+// slice's loads can issue before the first product; 0: a.dnum, a runtime loop.
 template <bool COH, int DN = 0>
 __device__ __forceinline__ void ip_range(const IpArgs& a, int t, size_t i, size_t end, size_t step) {
     const int dnum = DN > 0 ? DN : a.dnum;
